@@ -1,0 +1,357 @@
+"""FP64 CPU oracle for trainable multiscale denoising (arXiv 1802.06130).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py``; never by the product package.  It is a
+thin ctypes layer over ``mdn_oracle.c`` (plain C, FP64) plus the level cascade
+written as plain Python loops in the paper's order:
+
+* ``pyramid``            -- Section 4 "Multiscale filtering": 2x downsampling
+* ``select``             -- Section 3 "Filter selection": colour structure
+                            tensor, eigen-features, bucket s(i)
+* ``filter_level``       -- Eq. 1 and the multiscale equation of Section 4
+* ``denoise_multiscale`` -- Section 4: base case u^L = z^L, levels L-1 .. 0
+* ``gram_accumulate`` / ``solve_bank`` -- Eqs. 5-6: per-bucket least squares
+* ``train_cascade``      -- Section 4: train level L-1 first, apply it, feed
+                            its output to the next finer level
+
+Precision: FP64 throughout, except ``mirror32=True`` which evaluates the
+pyramid and the structure tensor/features in the documented FP32 order (for
+bit-exact bucket comparison), and ``storage`` which rounds every stored
+plane (pyramid levels, level outputs) to FP32 or FP16 (RN-even).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mdn_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liborc.so")
+
+STORAGE = {"f64": 0, "f32": 1, "f16": 2}
+MAX_THR = 8
+
+
+def build(force: bool = False) -> str:
+    """Compile mdn_oracle.c into oracle/_build/liborc.so (gcc, OpenMP)."""
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
+        return _SO
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _SO + f".{os.getpid()}.tmp"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+                           "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _SO)
+    return _SO
+
+
+class _BParams(C.Structure):
+    _fields_ = [("n_angle", C.c_int32), ("n_strength", C.c_int32), ("n_coherence", C.c_int32),
+                ("strength_thr", C.c_float * MAX_THR), ("coherence_thr", C.c_float * MAX_THR),
+                ("coh_eps", C.c_float)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(build())
+        dp, u8p, i64p = C.POINTER(C.c_double), C.POINTER(C.c_uint8), C.POINTER(C.c_int64)
+        L.orc_round_f16.restype = C.c_double
+        L.orc_round_f16.argtypes = [C.c_double]
+        L.orc_round_storage.argtypes = [dp, C.c_long, C.c_int]
+        L.orc_pyramid_down.argtypes = [dp, C.c_int, C.c_int, C.c_int, dp, C.c_int]
+        L.orc_structure_tensor.argtypes = [dp, C.c_int, C.c_int, C.c_int, dp]
+        L.orc_features.argtypes = [dp, C.c_int, C.c_int, C.c_int, C.c_float, dp]
+        L.orc_buckets.argtypes = [dp, C.c_int, C.c_int, C.POINTER(_BParams), C.c_double, u8p, u8p]
+        L.orc_to_work.argtypes = [dp, C.c_long, C.c_int, dp]
+        L.orc_from_work.argtypes = [dp, C.c_long, C.c_int, dp]
+        L.orc_regressor_len.restype = C.c_int
+        L.orc_regressor_len.argtypes = [C.c_int, C.c_int, C.c_int]
+        L.orc_filter_level.argtypes = [dp, C.c_int, C.c_int, dp, C.c_int, C.c_int, u8p, dp, C.c_int,
+                                       C.c_int, C.c_int, C.c_int, C.c_int, dp]
+        L.orc_gram_accumulate.argtypes = [dp, C.c_int, C.c_int, dp, C.c_int, C.c_int, dp, u8p, C.c_int,
+                                          C.c_int, C.c_int, C.c_int, C.c_int, dp, i64p]
+        L.orc_cholesky_solve.restype = C.c_int
+        L.orc_cholesky_solve.argtypes = [dp, C.c_int, dp, C.c_int]
+        L.orc_solve_bank.restype = C.c_int
+        L.orc_solve_bank.argtypes = [dp, i64p, C.c_int, C.c_int, C.c_int, C.c_double, dp]
+        _lib = L
+    return _lib
+
+
+def _d(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _p(a, t=C.c_double):
+    return a.ctypes.data_as(C.POINTER(t))
+
+
+# ---------------------------------------------------------------- parameters
+
+@dataclass
+class Geometry:
+    """Filter footprint: fine radius, coarse radius (-1 = single level),
+    cross-channel regressors, colour space (0 = YCbCr BT.601, 1 = RGB)."""
+    r_fine: int = 3
+    r_coarse: int = 3
+    cross: int = 0
+    color: int = 0
+
+    def D(self) -> int:
+        return lib().orc_regressor_len(self.r_fine, self.r_coarse, self.cross)
+
+
+@dataclass
+class BucketParams:
+    """Bucket grid and thresholds for one level (Section 3; thresholds are
+    this implementation's reading, the paper gives none)."""
+    n_angle: int = 24
+    strength_thr: tuple = (0.135, 0.16)
+    coherence_thr: tuple = (0.10, 0.15)
+    coh_eps: float = 1e-8
+
+    @property
+    def K(self) -> int:
+        return self.n_angle * (len(self.strength_thr) + 1) * (len(self.coherence_thr) + 1)
+
+    def c(self) -> _BParams:
+        b = _BParams()
+        b.n_angle = self.n_angle
+        b.n_strength = len(self.strength_thr) + 1
+        b.n_coherence = len(self.coherence_thr) + 1
+        for i, t in enumerate(self.strength_thr):
+            b.strength_thr[i] = t
+        for i, t in enumerate(self.coherence_thr):
+            b.coherence_thr[i] = t
+        b.coh_eps = self.coh_eps
+        return b
+
+
+def default_bparams(level: int) -> BucketParams:
+    """Level-l defaults: strength thresholds halve per coarser level.
+
+    Level-0 values were fixed once from the feature histogram of the
+    256x256, sigma = 25/255 training set (seeds 1000-1007) so that none of
+    the 216 buckets is empty, then frozen."""
+    s = 0.5 ** level
+    return BucketParams(strength_thr=(0.135 * s, 0.16 * s), coherence_thr=(0.10, 0.15))
+
+
+# ---------------------------------------------------------------- primitives
+
+def round_storage(x, storage: str):
+    x = _d(x).copy()
+    lib().orc_round_storage(_p(x), x.size, STORAGE[storage])
+    return x
+
+
+def pyramid_down(img, mirror32: bool = False):
+    img = _d(img)
+    Cn, H, W = img.shape
+    out = np.empty((Cn, (H + 1) // 2, (W + 1) // 2))
+    lib().orc_pyramid_down(_p(img), Cn, H, W, _p(out), int(mirror32))
+    return out
+
+
+def pyramid(img, levels: int, storage: str = "f64", mirror32: bool = False):
+    """[z^0, ..., z^{L-1}]; z^0 is the input rounded to storage."""
+    z = [round_storage(img, storage)]
+    for _ in range(1, levels):
+        z.append(round_storage(pyramid_down(z[-1], mirror32), storage))
+    return z
+
+
+def structure_tensor(z, mirror32: bool = False):
+    z = _d(z)
+    _, H, W = z.shape
+    T = np.empty((3, H, W))
+    lib().orc_structure_tensor(_p(z), H, W, int(mirror32), _p(T))
+    return T
+
+
+def features(T, coh_eps: float = 1e-8, mirror32: bool = False):
+    T = _d(T)
+    _, H, W = T.shape
+    f = np.empty((3, H, W))
+    lib().orc_features(_p(T), H, W, int(mirror32), coh_eps, _p(f))
+    return f
+
+
+def buckets(feat, bp: BucketParams, band_eps: float = 1e-5):
+    feat = _d(feat)
+    _, H, W = feat.shape
+    b = np.empty((H, W), dtype=np.uint8)
+    band = np.empty((H, W), dtype=np.uint8)
+    cb = bp.c()
+    lib().orc_buckets(_p(feat), H, W, C.byref(cb), band_eps, _p(b, C.c_uint8), _p(band, C.c_uint8))
+    return b, band.astype(bool)
+
+
+def select(z, bp: BucketParams, mirror32: bool = False, band_eps: float = 1e-5):
+    """s(i) for one level: (bucket map u8 [H][W], band mask, features)."""
+    f = features(structure_tensor(z, mirror32), bp.coh_eps, mirror32)
+    b, band = buckets(f, bp, band_eps)
+    return b, band, f
+
+
+def to_work(rgb, color: int = 0):
+    rgb = _d(rgb)
+    out = np.empty_like(rgb)
+    lib().orc_to_work(_p(rgb), rgb.shape[1] * rgb.shape[2], color, _p(out))
+    return out
+
+
+def from_work(w, color: int = 0):
+    w = _d(w)
+    out = np.empty_like(w)
+    lib().orc_from_work(_p(w), w.shape[1] * w.shape[2], color, _p(out))
+    return out
+
+
+def filter_level(z, uc, bucket, bank, geom: Geometry):
+    """Level output (RGB, FP64) of the multiscale equation (Eq. 1 if uc is None)."""
+    z = _d(z)
+    _, H, W = z.shape
+    bank = _d(bank)
+    K = bank.shape[0]
+    assert bank.shape == (K, 3, geom.D()), (bank.shape, geom.D())
+    bucket = np.ascontiguousarray(bucket, dtype=np.uint8)
+    out = np.empty_like(z)
+    if geom.r_coarse >= 0:
+        uc = _d(uc)
+        Hc, Wc = uc.shape[1:]
+        ucp = _p(uc)
+    else:
+        Hc = Wc = 0
+        ucp = None
+    lib().orc_filter_level(_p(z), H, W, ucp, Hc, Wc, _p(bucket, C.c_uint8), _p(bank), K,
+                           geom.r_fine, geom.r_coarse, geom.cross, geom.color, _p(out))
+    return out
+
+
+@dataclass
+class DenoiseResult:
+    out: np.ndarray
+    buckets: list = field(default_factory=list)   # per filtered level
+    bands: list = field(default_factory=list)
+    pyramid: list = field(default_factory=list)
+    levels_out: list = field(default_factory=list)  # u-hat^l, l = 0..L-1
+
+
+def denoise_multiscale(noisy, banks, geom: Geometry, bparams=None, storage: str = "f64",
+                       mirror32: bool = False, bank_storage: str | None = None):
+    """Section 4 inference: pyramid, base u^{L-1} = z^{L-1}, then levels
+    L-2 .. 0 each filtered with its bank.  len(banks) = max(L-1, 1); L = 1 is
+    single-scale filtering (Eq. 1) and needs geom.r_coarse = -1."""
+    nb = len(banks)
+    L = 1 if geom.r_coarse < 0 else nb + 1
+    if bparams is None:
+        bparams = [default_bparams(l) for l in range(nb)]
+    if bank_storage is not None:
+        banks = [round_storage(b, bank_storage) for b in banks]
+    # the selector always sees the pyramid evaluated in the same precision as
+    # its own features (mirror32) -- a mirror32 pyramid differs from the FP64
+    # one only in FP32 rounding
+    zs = pyramid(noisy, L, storage, mirror32)
+    res = DenoiseResult(out=None, pyramid=zs)
+    u = [None] * L
+    u[L - 1] = zs[L - 1]
+    first = L - 2 if L > 1 else 0
+    bks, bds = [None] * nb, [None] * nb
+    for l in range(first, -1, -1):
+        b, band, _ = select(zs[l], bparams[l], mirror32)
+        uc = u[l + 1] if geom.r_coarse >= 0 else None
+        u[l] = round_storage(filter_level(zs[l], uc, b, banks[l], geom), storage)
+        bks[l], bds[l] = b, band
+    res.out = u[0]
+    res.buckets, res.bands, res.levels_out = bks, bds, u
+    return res
+
+
+# ---------------------------------------------------------------- training
+
+def gram_accumulate(z, uc, target, bucket, K: int, geom: Geometry, gram=None, counts=None):
+    """Adds one image's per-bucket Gram matrices of [x; y] (Eqs. 5-6)."""
+    z, target = _d(z), _d(target)
+    _, H, W = z.shape
+    D = geom.D()
+    G, T = (1, 3) if geom.cross else (3, 1)
+    if gram is None:
+        gram = np.zeros((K, G, D + T, D + T))
+        counts = np.zeros(K, dtype=np.int64)
+    bucket = np.ascontiguousarray(bucket, dtype=np.uint8)
+    if geom.r_coarse >= 0:
+        uc = _d(uc)
+        Hc, Wc = uc.shape[1:]
+        ucp = _p(uc)
+    else:
+        Hc = Wc = 0
+        ucp = None
+    lib().orc_gram_accumulate(_p(z), H, W, ucp, Hc, Wc, _p(target), _p(bucket, C.c_uint8), K,
+                              geom.r_fine, geom.r_coarse, geom.cross, geom.color,
+                              _p(gram), _p(counts, C.c_int64))
+    return gram, counts
+
+
+def solve_bank(gram, counts, geom: Geometry, lam: float = 1e-3):
+    """Ridge least squares per bucket, FP64 Cholesky; empty -> pooled."""
+    K = gram.shape[0]
+    D = geom.D()
+    gram = _d(gram)
+    counts = np.ascontiguousarray(counts, dtype=np.int64)
+    bank = np.zeros((K, 3, D))
+    fails = lib().orc_solve_bank(_p(gram), _p(counts, C.c_int64), K, D, geom.cross, lam, _p(bank))
+    if fails:
+        raise RuntimeError(f"{fails} Cholesky solves failed")
+    return bank
+
+
+def cholesky_solve(A, B):
+    A = _d(A).copy()
+    B = _d(B).copy()
+    squeeze = B.ndim == 1
+    if squeeze:
+        B = B[:, None].copy()
+    rc = lib().orc_cholesky_solve(_p(A), A.shape[0], _p(B), B.shape[1])
+    if rc:
+        raise np.linalg.LinAlgError("not positive definite")
+    return B[:, 0] if squeeze else B
+
+
+def train_cascade(noisy_list, clean_list, geom: Geometry, levels: int, bparams=None,
+                  lam: float = 1e-3, mirror32: bool = False, storage: str = "f64"):
+    """Section 4 training: level L-2 first (its coarse input is z^{L-1}), then
+    every finer level using the trained coarser levels' outputs."""
+    nb = max(levels - 1, 1)
+    L = 1 if geom.r_coarse < 0 else levels
+    if bparams is None:
+        bparams = [default_bparams(l) for l in range(nb)]
+    zp = [pyramid(z, L, storage, mirror32) for z in noisy_list]
+    up = [pyramid(u, L, storage, mirror32) for u in clean_list]
+    cur = [p[L - 1] for p in zp]           # u-hat at level l+1, per pair
+    banks = [None] * nb
+    stats = [None] * nb
+    first = L - 2 if L > 1 else 0
+    for l in range(first, -1, -1):
+        K = bparams[l].K
+        gram = counts = None
+        sel = []
+        for i in range(len(noisy_list)):
+            b, _, _ = select(zp[i][l], bparams[l], mirror32)
+            sel.append(b)
+            uc = cur[i] if geom.r_coarse >= 0 else None
+            gram, counts = gram_accumulate(zp[i][l], uc, up[i][l], b, K, geom, gram, counts)
+        banks[l] = solve_bank(gram, counts, geom, lam)
+        stats[l] = counts
+        cur = [round_storage(filter_level(zp[i][l], cur[i] if geom.r_coarse >= 0 else None,
+                                          sel[i], banks[l], geom), storage)
+               for i in range(len(noisy_list))]
+    return banks, stats

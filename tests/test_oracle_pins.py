@@ -1,0 +1,409 @@
+"""Pins the FP64 oracle to facts that do not come from the oracle itself:
+closed forms, library routines (numpy float16, LAPACK eigh/solve/lstsq),
+brute force through independently built matrices, invariants, and the
+hand-computed fixtures in tests/golden/ (each cites the passage it follows).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _clamp_matrix(n_out, n_in, taps, step, offset):
+    """Dense 1-D operator: out[i] = sum_t taps[t] * in[clamp(step*i + t - offset)]."""
+    M = np.zeros((n_out, n_in))
+    for i in range(n_out):
+        for t, w in enumerate(taps):
+            j = min(max(step * i + t - offset, 0), n_in - 1)
+            M[i, j] += w
+    return M
+
+
+# ------------------------------------------------------------ storage rounding
+
+def test_f16_rounding_matches_numpy():
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.standard_normal(20000) * 3, rng.uniform(-1e-4, 1e-4, 5000),
+                        np.array([0.0, -0.0, 65504.0, 65519.0, 1 + 2**-11, 1 + 3 * 2**-11,
+                                  2**-24, 2**-25, 3 * 2**-25, 6e-8, 1e-9])])
+    got = O.round_storage(x, "f16")
+    ref = x.astype(np.float16).astype(np.float64)
+    assert np.array_equal(got, ref)
+
+
+def test_f32_rounding_matches_numpy():
+    x = np.random.default_rng(1).standard_normal(1000)
+    assert np.array_equal(O.round_storage(x, "f32"), x.astype(np.float32).astype(np.float64))
+
+
+# ------------------------------------------------------------ A1 pyramid
+
+@pytest.mark.parametrize("H,W", [(1, 1), (2, 3), (7, 5), (33, 17), (16, 16)])
+def test_pyramid_equals_kronecker_operator(H, W):
+    """2x binomial downsampling with clamping == (Dy kron Dx) applied to the
+    flattened image, both 1-D operators built independently."""
+    rng = np.random.default_rng(H * 100 + W)
+    img = rng.standard_normal((3, H, W))
+    b = np.array([1, 4, 6, 4, 1]) / 16.0
+    Dy = _clamp_matrix((H + 1) // 2, H, b, 2, 2)
+    Dx = _clamp_matrix((W + 1) // 2, W, b, 2, 2)
+    ref = np.stack([Dy @ img[c] @ Dx.T for c in range(3)])
+    got = O.pyramid_down(img)
+    assert got.shape == ref.shape
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13)
+    got32 = O.pyramid_down(img, mirror32=True)
+    np.testing.assert_allclose(got32, ref, rtol=0, atol=5e-6)
+
+
+def test_pyramid_constant_and_ramp():
+    img = np.full((3, 20, 31), 0.37)
+    np.testing.assert_allclose(O.pyramid_down(img), 0.37, atol=1e-15)
+    # interior of a linear ramp maps to the ramp sampled at (2x, 2y)
+    yy, xx = np.mgrid[0:40, 0:40].astype(float)
+    ramp = np.stack([0.01 * xx - 0.02 * yy + 0.3] * 3)
+    d = O.pyramid_down(ramp)
+    Y, X = np.mgrid[0:20, 0:20].astype(float)
+    exp = 0.01 * 2 * X - 0.02 * 2 * Y + 0.3
+    np.testing.assert_allclose(d[0, 1:19, 1:19], exp[1:19, 1:19], atol=1e-14)
+
+
+def test_pyramid_storage_rounding_is_representable():
+    img = np.random.default_rng(2).uniform(0, 1, (3, 15, 9))
+    zs = O.pyramid(img, 3, storage="f16")
+    assert [z.shape for z in zs] == [(3, 15, 9), (3, 8, 5), (3, 4, 3)]
+    for z in zs:
+        assert np.array_equal(z, z.astype(np.float16).astype(np.float64))
+
+
+# ------------------------------------------------------------ A2/A3 selector
+
+def _ramp_image(H, W, grads, offs=(0.2, 0.4, 0.6)):
+    yy, xx = np.mgrid[0:H, 0:W].astype(float)
+    return np.stack([gx * xx + gy * yy + d for (gx, gy), d in zip(grads, offs)])
+
+
+@pytest.mark.parametrize("mirror32", [False, True])
+def test_ramp_closed_form(mirror32):
+    """Parallel colour gradients g_c = k_c (gx, gy): T = sum_c g_c g_c^T away
+    from the border, l2 = 0, coherence 1, strength = sqrt(sum |g_c|^2),
+    orientation = angle(g) + pi/2 (mod pi)."""
+    with open(os.path.join(GOLDEN, "ramp_features.json")) as f:
+        cases = json.load(f)["cases"]
+    for case in cases:
+        g = case["grads"]
+        img = _ramp_image(24, 24, g)
+        T = O.structure_tensor(img, mirror32)
+        Txx = sum(a * a for a, _ in g)
+        Txy = sum(a * b for a, b in g)
+        Tyy = sum(b * b for _, b in g)
+        tol = 1e-12 if not mirror32 else 1e-6
+        np.testing.assert_allclose(T[0, 3:-3, 3:-3], Txx, atol=tol)
+        np.testing.assert_allclose(T[1, 3:-3, 3:-3], Txy, atol=tol)
+        np.testing.assert_allclose(T[2, 3:-3, 3:-3], Tyy, atol=tol)
+        f = O.features(T, mirror32=mirror32)
+        np.testing.assert_allclose(f[1, 3:-3, 3:-3], case["strength"], rtol=1e-6)
+        np.testing.assert_allclose(f[2, 3:-3, 3:-3], 1.0, atol=2e-3 if mirror32 else 1e-6)
+        np.testing.assert_allclose(f[0, 3:-3, 3:-3], case["theta_over_pi"], atol=1e-6)
+        b, _ = O.buckets(f, O.default_bparams(0))
+        assert np.all(b[3:-3, 3:-3] == case["bucket"]), (case, np.unique(b[3:-3, 3:-3]))
+
+
+def test_orientation_rotates_with_image():
+    for alpha in np.linspace(0.05, 3.0, 9):
+        g = (math.cos(alpha) * 0.05, math.sin(alpha) * 0.05)
+        img = _ramp_image(20, 20, [g, g, g])
+        f = O.features(O.structure_tensor(img))
+        th = ((alpha + math.pi / 2) % math.pi) / math.pi
+        np.testing.assert_allclose(f[0, 3:-3, 3:-3], th, atol=1e-9)
+
+
+def test_edges_and_constant_buckets():
+    bp = O.default_bparams(0)
+    H = W = 16
+    vert = np.zeros((3, H, W)); vert[:, :, 8:] = 1.0      # vertical edge: gradient along x
+    horz = np.zeros((3, H, W)); horz[:, 8:, :] = 1.0      # horizontal edge: gradient along y
+    bv, _, fv = O.select(vert, bp)
+    bh, _, fh = O.select(horz, bp)
+    assert np.all(bv[:, 7:9] // 9 == 12)        # theta = pi/2 -> angle bin 12
+    assert np.all(bh[7:9, :] // 9 == 0)          # theta = 0    -> angle bin 0
+    const = np.full((3, H, W), 0.5)
+    bc, _, fc = O.select(const, bp)
+    assert np.all(fc[1] == 0) and np.all(fc[2] == 0)
+    assert np.all(bc == (12 * 3 + 0) * 3 + 0)
+
+
+def test_features_match_lapack_eigh():
+    z, _ = synth.noisy_pair(40, 40, 7)
+    T = O.structure_tensor(z)
+    f = O.features(T)
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        y, x = rng.integers(0, 40, 2)
+        M = np.array([[T[0, y, x], T[1, y, x]], [T[1, y, x], T[2, y, x]]])
+        w, V = np.linalg.eigh(M)
+        l2, l1 = max(w[0], 0), w[1]
+        assert abs(f[1, y, x] - math.sqrt(l1)) < 1e-12
+        coh = (math.sqrt(l1) - math.sqrt(l2)) / (math.sqrt(l1) + math.sqrt(l2))
+        assert abs(f[2, y, x] - coh) < 1e-9
+        v = V[:, 0]                                 # minor eigenvector (x, y)
+        th = math.atan2(v[1], v[0]) % math.pi
+        d = abs(f[0, y, x] * math.pi - th)
+        assert min(d, math.pi - d) < 1e-7
+
+
+def test_tensor_symmetries():
+    """Transposing the image swaps Txx/Tyy; mirroring x negates Txy;
+    adding a constant leaves T unchanged; scaling by a multiplies T by a^2."""
+    z = synth.noisy_pair(24, 30, 11)[0].astype(np.float64)
+    T = O.structure_tensor(z)
+    Tt = O.structure_tensor(np.ascontiguousarray(z.transpose(0, 2, 1)))
+    np.testing.assert_allclose(Tt[0], T[2].T, atol=1e-14)
+    np.testing.assert_allclose(Tt[2], T[0].T, atol=1e-14)
+    np.testing.assert_allclose(Tt[1], T[1].T, atol=1e-14)
+    Tm = O.structure_tensor(np.ascontiguousarray(z[:, :, ::-1]))
+    np.testing.assert_allclose(Tm[1], -T[1][:, ::-1], atol=1e-14)
+    np.testing.assert_allclose(O.structure_tensor(z + 0.25), T, atol=1e-13)
+    np.testing.assert_allclose(O.structure_tensor(3 * z), 9 * T, rtol=1e-12, atol=1e-14)
+
+
+def test_coherence_range_and_fp32_path_agrees_outside_band():
+    z, _ = synth.noisy_pair(64, 64, 13)
+    bp = O.default_bparams(0)
+    b64, band64, f64 = O.select(z, bp, mirror32=False)
+    b32, band32, f32 = O.select(z, bp, mirror32=True)
+    assert f64[2].min() >= 0 and f64[2].max() <= 1
+    assert f32[2].min() >= 0 and f32[2].max() <= 1 + 1e-7
+    mism = (b64 != b32) & ~band64 & ~band32
+    assert mism.sum() == 0
+
+
+# ------------------------------------------------------------ colour transform
+
+def test_ycbcr_golden_and_roundtrip():
+    with open(os.path.join(GOLDEN, "ycbcr_bt601.json")) as f:
+        g = json.load(f)
+    for case in g["cases"]:
+        rgb = np.array(case["rgb"], dtype=float).reshape(3, 1, 1)
+        w = O.to_work(rgb, 0)[:, 0, 0]
+        np.testing.assert_allclose(w, case["ycbcr"], atol=1e-12)
+    x = np.random.default_rng(5).uniform(-1, 2, (3, 8, 9))
+    np.testing.assert_allclose(O.from_work(O.to_work(x, 0), 0), x, atol=1e-13)
+    np.testing.assert_array_equal(O.to_work(x, 1), x)
+
+
+# ------------------------------------------------------------ A4 filtering
+
+def _delta_bank(K, geom, coarse_center=0.0, fine_center=1.0):
+    D = geom.D()
+    bank = np.zeros((K, 3, D))
+    pf = (2 * geom.r_fine + 1) ** 2
+    pc = (2 * geom.r_coarse + 1) ** 2 if geom.r_coarse >= 0 else 0
+    for c in range(3):
+        cc = c if geom.cross else 0
+        if pc:
+            bank[:, c, cc * pc + pc // 2] = coarse_center
+        off = (3 if geom.cross else 1) * pc
+        bank[:, c, off + cc * pf + pf // 2] = fine_center
+    return bank
+
+
+@pytest.mark.parametrize("geom", [O.Geometry(2, -1), O.Geometry(3, 3), O.Geometry(3, 2, cross=1),
+                                  O.Geometry(3, 3, color=1)])
+def test_delta_filter_is_identity(geom):
+    z, _ = synth.noisy_pair(21, 18, 3)
+    uc = O.pyramid_down(z)
+    bk = np.random.default_rng(0).integers(0, 216, (21, 18)).astype(np.uint8)
+    out = O.filter_level(z, uc, bk, _delta_bank(216, geom), geom)
+    np.testing.assert_allclose(out, z, atol=1e-13)
+
+
+def test_coarse_delta_is_nearest_upsampling():
+    """f = delta at the coarse centre, g = 0: out_i = u^{l+1}_{floor(i/2)}."""
+    geom = O.Geometry(3, 3)
+    z = np.zeros((3, 13, 10))
+    uc = np.random.default_rng(1).uniform(0, 1, (3, 7, 5))
+    bank = _delta_bank(216, geom, coarse_center=1.0, fine_center=0.0)
+    out = O.filter_level(z, uc, np.zeros((13, 10), np.uint8), bank, geom)
+    ref = uc[:, np.arange(13) // 2][:, :, np.arange(10) // 2]
+    np.testing.assert_allclose(out, ref, atol=1e-13)
+
+
+def test_normalised_bank_preserves_constant():
+    geom = O.Geometry(3, 3)
+    rng = np.random.default_rng(2)
+    bank = rng.standard_normal((216, 3, geom.D()))
+    bank /= bank.sum(axis=2, keepdims=True)
+    z = np.empty((3, 11, 12)); z[0], z[1], z[2] = 0.2, 0.5, 0.9
+    uc = O.pyramid_down(z)
+    bk = rng.integers(0, 216, (11, 12)).astype(np.uint8)
+    out = O.filter_level(z, uc, bk, bank, geom)
+    np.testing.assert_allclose(out, z, atol=1e-10)
+
+
+def test_one_pixel_image_by_hand():
+    """1x1 image: every clamped tap reads the single pixel, so the output in
+    working space is (sum of taps) x value."""
+    geom = O.Geometry(2, 2)
+    rgb = np.array([0.3, 0.6, 0.1]).reshape(3, 1, 1)
+    bank = np.zeros((216, 3, geom.D()))
+    bank[5, 0, :] = 0.01      # Y: 50 taps x 0.01 = 0.5
+    bank[5, 1, :25] = 0.04    # Cb: coarse taps only, 25 x 0.04 = 1.0
+    bank[5, 2, 25:] = -0.02   # Cr: fine taps only, 25 x -0.02 = -0.5
+    out = O.filter_level(rgb, rgb, np.array([[5]], np.uint8), bank, geom)
+    Y = 0.299 * 0.3 + 0.587 * 0.6 + 0.114 * 0.1
+    Cb, Cr = (0.1 - Y) / 1.772, (0.3 - Y) / 1.402
+    y, cb, cr = 0.5 * Y, 1.0 * Cb, -0.5 * Cr
+    R, B = y + 1.402 * cr, y + 1.772 * cb
+    G = (y - 0.299 * R - 0.114 * B) / 0.587
+    np.testing.assert_allclose(out[:, 0, 0], [R, G, B], atol=1e-14)
+
+
+def _patches_numpy(img, r):
+    """[C][H][W] -> [H][W][C][(2r+1)^2] clamped patches via edge padding."""
+    p = np.pad(img, ((0, 0), (r, r), (r, r)), mode="edge")
+    H, W = img.shape[1:]
+    out = np.empty((H, W, img.shape[0], (2 * r + 1) ** 2))
+    k = 0
+    for dy in range(2 * r + 1):
+        for dx in range(2 * r + 1):
+            out[..., k] = p[:, dy:dy + H, dx:dx + W].transpose(1, 2, 0)
+            k += 1
+    return out
+
+
+def _ycc(rgb):
+    M = np.array([[0.299, 0.587, 0.114],
+                  [-0.299 / 1.772, -0.587 / 1.772, (1 - 0.114) / 1.772],
+                  [(1 - 0.299) / 1.402, -0.587 / 1.402, -0.114 / 1.402]])
+    return np.einsum("ij,jhw->ihw", M, rgb), np.linalg.inv(M)
+
+
+def test_filter_brute_force_multiscale():
+    """Brute force of the multiscale equation on a 9x8 image: explicit patch
+    tensors from edge padding, YCbCr by the BT.601 matrix and its inverse."""
+    rng = np.random.default_rng(4)
+    geom = O.Geometry(3, 2)
+    z = rng.uniform(0, 1, (3, 9, 8))
+    uc = rng.uniform(0, 1, (3, 5, 4))
+    bk = rng.integers(0, 216, (9, 8)).astype(np.uint8)
+    bank = rng.standard_normal((216, 3, geom.D())) * 0.05
+    zw, Minv = _ycc(z)
+    uw, _ = _ycc(uc)
+    Pz = _patches_numpy(zw, 3)                     # [9][8][3][49]
+    Pu = _patches_numpy(uw, 2)                     # [5][4][3][25]
+    ow = np.zeros((3, 9, 8))
+    for y in range(9):
+        for x in range(8):
+            h = bank[bk[y, x]]
+            for c in range(3):
+                ow[c, y, x] = h[c, :25] @ Pu[y // 2, x // 2, c] + h[c, 25:] @ Pz[y, x, c]
+    ref = np.einsum("ij,jhw->ihw", Minv, ow)
+    out = O.filter_level(z, uc, bk, bank, geom)
+    np.testing.assert_allclose(out, ref, atol=1e-12)
+
+
+def test_filter_brute_force_single_scale_cross_channel():
+    rng = np.random.default_rng(6)
+    geom = O.Geometry(2, -1, cross=1, color=1)
+    z = rng.uniform(0, 1, (3, 8, 8))
+    bk = rng.integers(0, 216, (8, 8)).astype(np.uint8)
+    bank = rng.standard_normal((216, 3, geom.D()))
+    Pz = _patches_numpy(z, 2).reshape(8, 8, 75)    # channel-major (c, dy, dx)
+    ref = np.einsum("hwcd,hwd->chw", bank[bk], Pz)
+    np.testing.assert_allclose(O.filter_level(z, None, bk, bank, geom), ref, atol=1e-12)
+
+
+# ------------------------------------------------------------ A5/A6 training
+
+def test_cholesky_matches_lapack():
+    rng = np.random.default_rng(8)
+    for n in (1, 5, 49, 147):
+        A = rng.standard_normal((n, n + 3))
+        A = A @ A.T + 1e-3 * np.eye(n)
+        B = rng.standard_normal((n, 3))
+        np.testing.assert_allclose(O.cholesky_solve(A, B), np.linalg.solve(A, B),
+                                   rtol=1e-9, atol=1e-9 * np.abs(np.linalg.solve(A, B)).max())
+
+
+def test_gram_path_equals_lstsq():
+    """Per bucket, the ridge solution from the accumulated Gram equals the
+    LAPACK least-squares solution of the stacked system [X; sqrt(n lam) I] h
+    = [y; 0], X built from numpy patch tensors."""
+    rng = np.random.default_rng(9)
+    geom = O.Geometry(2, -1)
+    z, u = synth.noisy_pair(32, 32, 21)
+    bk = rng.integers(0, 4, (32, 32)).astype(np.uint8)
+    lam = 1e-3
+    gram, counts = O.gram_accumulate(z, None, u, bk, 4, geom)
+    bank = O.solve_bank(gram, counts, geom, lam)
+    zw, _ = _ycc(z)
+    uw, _ = _ycc(u)
+    P = _patches_numpy(zw, 2)
+    for k in range(4):
+        m = bk == k
+        n = m.sum()
+        assert counts[k] == n
+        for c in range(3):
+            X = P[m][:, c, :]
+            y = uw[c][m]
+            A = np.vstack([X, math.sqrt(n * lam) * np.eye(25)])
+            rhs = np.concatenate([y, np.zeros(25)])
+            h = np.linalg.lstsq(A, rhs, rcond=None)[0]
+            np.testing.assert_allclose(bank[k, c], h, rtol=1e-8, atol=1e-10)
+
+
+@pytest.mark.parametrize("geom", [O.Geometry(2, -1), O.Geometry(3, 3), O.Geometry(3, -1, cross=1)])
+def test_planted_bank_recovered(geom):
+    """Noise-free targets made by a planted bank (selector computed on z) are
+    fitted exactly by least squares with lambda = 0 (Eqs. 5-6)."""
+    rng = np.random.default_rng(10)
+    z, _ = synth.noisy_pair(160, 160, 31)
+    uc = O.pyramid_down(z) if geom.r_coarse >= 0 else None
+    bp = O.default_bparams(0)
+    bk, _, _ = O.select(z, bp)
+    planted = rng.standard_normal((216, 3, geom.D())) * 0.05
+    target = O.filter_level(z, uc, bk, planted, geom)
+    gram, counts = O.gram_accumulate(z, uc, target, bk, 216, geom)
+    D = geom.D()
+    checked = 0
+    Gn = gram.shape[1]
+    for k in range(216):
+        if counts[k] < 4 * D:
+            continue
+        for g in range(Gn):
+            A = gram[k, g, :D, :D]
+            if np.linalg.cond(A) > 1e8:
+                continue
+            B = gram[k, g, :D, D:]
+            h = O.cholesky_solve(A, B)
+            ref = planted[k].T[:, :] if geom.cross else planted[k, g][:, None]
+            err = np.linalg.norm(h - ref) / np.linalg.norm(ref)
+            assert err < 1e-10, (k, g, err)
+            checked += 1
+    assert checked >= 5
+
+
+def test_cascade_with_identity_banks_returns_input():
+    geom = O.Geometry(3, 3)
+    z, _ = synth.noisy_pair(30, 26, 41)
+    banks = [_delta_bank(216, geom), _delta_bank(216, geom)]
+    r = O.denoise_multiscale(z, banks, geom)
+    np.testing.assert_allclose(r.out, z, atol=1e-13)
+    assert len(r.pyramid) == 3 and r.pyramid[2].shape == (3, 8, 7)
+
+
+def test_training_reduces_error_single_level():
+    """Sanity: a bank trained on 4 pairs denoises a held-out image."""
+    geom = O.Geometry(2, -1)
+    pairs = [synth.noisy_pair(64, 64, 1000 + i) for i in range(4)]
+    banks, _ = O.train_cascade([p[0] for p in pairs], [p[1] for p in pairs], geom, 1)
+    z, u = synth.noisy_pair(64, 64, 2000)
+    out = O.denoise_multiscale(z, banks, geom).out
+    assert np.mean((out - u) ** 2) < 0.3 * np.mean((z - u) ** 2)
