@@ -1,0 +1,340 @@
+"""Throughput benchmark: 3-level multiscale denoise of 12 MP frames.
+
+Workload (default): 8 frames of 4032x3024 RGB, FP16 storage / FP32
+arithmetic, camera-like noise (variance 0.01 x + (10/255)^2 with a smooth
+gain field in [0.5, 2]), 3 pyramid levels, 7x7 fine + 7x7 coarse per-channel
+filters (D = 98), 216 buckets per level, FP16 banks resident in shared memory.
+One step = pyramid (2 launches) + level-1 filter + level-0 filter, all through
+the C ABI, inputs resident in HBM (585 MB per step, larger than L2).
+
+Metric: Mpix/s of finest-level input pixels (whole job, all ranks).
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+H, W, LEVELS = 3024, 4032, 3
+METRIC = "Mpix/s 3-level denoise at 12MP"
+
+
+def _gen_frame(seed):
+    import synth
+    return synth.noisy_pair(H, W, seed, model="camera")[0]
+
+
+def make_frames(n, seed0):
+    """n distinct seeded frames, generated in a spawn pool (before any CUDA use)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    with cf.ProcessPoolExecutor(max_workers=min(n, os.cpu_count() or 1),
+                                mp_context=mp.get_context("spawn")) as ex:
+        return np.stack(list(ex.map(_gen_frame, [seed0 + i for i in range(n)])))
+
+
+def random_banks(seed, D=98, K=216, nb=LEVELS - 1):
+    """Random FP16 banks with taps summing to ~1 (values keep the output in range)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(nb):
+        b = rng.standard_normal((K, 3, D)).astype(np.float32) * 0.03
+        b += (1.0 - b.sum(axis=2, keepdims=True)) / D
+        out.append(b)
+    return out
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def cpu_oracle_run(steps, warmup, sample_hw=(768, 1024)):
+    """Times the FP64 oracle (as it stands) on 3-level denoises of crops of the
+    benchmark frame; returns Mpix/s, cores, sample description."""
+    import oracle as O
+    import synth
+    h, w = sample_hw
+    z = synth.noisy_pair(h, w, 40000, model="camera")[0]
+    z16 = O.round_storage(z, "f16")
+    geom = O.Geometry(3, 3)
+    banks = [b.astype(np.float64) for b in random_banks(7)]
+    for _ in range(warmup):
+        O.denoise_multiscale(z16, banks, geom, storage="f16")
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        O.denoise_multiscale(z16, banks, geom, storage="f16")
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    mpix = h * w * steps / 1e6
+    return mpix / tot, tot, f"{steps} x 3-level denoise of a {w}x{h} crop (FP16-rounded input, FP64 arithmetic)"
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    v, tot, sample = cpu_oracle_run(args.steps, args.warmup)
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "Mpix/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000 * tot / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "3-level denoise, 7x7+7x7 per-channel YCbCr filters, 216 buckets, "
+                                   "FP16 inputs, crop of a 4032x3024 camera-noise frame"},
+            "cpu_baseline": {"value": round(v, 3), "unit": "Mpix/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(v, 3), "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_gpu(args, rank, world, frames):
+    import torch
+    import paper_1802_06130_gb300 as mdn
+
+    torch.cuda.set_device(args.local_rank)
+    dev = torch.device("cuda", args.local_rank)
+    mdn.build()
+    L = mdn.lib()
+    n = frames.shape[0]
+    geom = mdn.Geometry(3, 3)
+    bps = [mdn.default_bparams(0), mdn.default_bparams(1)]
+    banks = [torch.tensor(b, dtype=torch.float16, device=dev) for b in random_banks(7)]
+    x = torch.tensor(frames, dtype=torch.float16, device=dev)
+    hl = [H, (H + 1) // 2, (H + 3) // 4]
+    wl = [W, (W + 1) // 2, (W + 3) // 4]
+    z1 = torch.empty((n, 3, hl[1], wl[1]), dtype=torch.float16, device=dev)
+    z2 = torch.empty((n, 3, hl[2], wl[2]), dtype=torch.float16, device=dev)
+    u1 = torch.empty_like(z1)
+    out = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    import ctypes as C
+    sp = C.c_void_p(stream.cuda_stream)
+    lv = (C.c_void_p * 2)(z1.data_ptr(), z2.data_ptr())
+
+    ev = None
+
+    def step(record):
+        if record:
+            ev[0].record(stream)
+        mdn._check(L.mdn_build_pyramid(C.c_void_p(x.data_ptr()), mdn.F16, n, H, W, LEVELS, lv, sp))
+        if record:
+            ev[1].record(stream)
+        mdn._check(L.mdn_filter_level(C.c_void_p(z1.data_ptr()), C.c_void_p(z2.data_ptr()), mdn.F16, n, hl[1],
+                                      wl[1], C.c_void_p(banks[1].data_ptr()), mdn.F16, C.byref(geom),
+                                      C.byref(bps[1]), C.c_void_p(u1.data_ptr()), None, sp))
+        if record:
+            ev[2].record(stream)
+        mdn._check(L.mdn_filter_level(C.c_void_p(x.data_ptr()), C.c_void_p(u1.data_ptr()), mdn.F16, n, H, W,
+                                      C.c_void_p(banks[0].data_ptr()), mdn.F16, C.byref(geom), C.byref(bps[0]),
+                                      C.c_void_p(out.data_ptr()), None, sp))
+        if record:
+            ev[3].record(stream)
+
+    # the level-wise sequence is exactly what mdn_denoise_multiscale launches
+    ref = mdn.denoise_multiscale(x, banks, geom, bps)
+    step(False)
+    torch.cuda.synchronize()
+    assert torch.equal(ref, out), "level-wise step differs from mdn_denoise_multiscale"
+
+    for _ in range(args.warmup):
+        step(False)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(args.local_rank) as clk:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for k in range(args.steps):
+            ev = evs[k]
+            step(True)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    if dist is not None:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+        dist.barrier()
+    pyr = [e[0].elapsed_time(e[1]) for e in evs]
+    lv1 = [e[1].elapsed_time(e[2]) for e in evs]
+    lv0 = [e[2].elapsed_time(e[3]) for e in evs]
+
+    # ---- end to end: pinned host frames -> device -> denoise -> host ----
+    host_in = torch.empty((n, 3, H, W), dtype=torch.float16, pin_memory=True)
+    host_in.copy_(torch.from_numpy(frames.astype(np.float16)))
+    host_out = torch.empty_like(host_in, pin_memory=True)
+    xin = torch.empty_like(x)
+    ws = torch.empty(mdn.denoise_workspace_bytes(n, H, W, LEVELS, mdn.F16), dtype=torch.uint8, device=dev)
+
+    def e2e_step():
+        xin.copy_(host_in, non_blocking=True)
+        mdn.denoise_multiscale(xin, banks, geom, bps, out=out, ws=ws)
+        host_out.copy_(out, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    e2e_steps = max(2, args.steps // 2)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ems = e0.elapsed_time(e1)
+    if dist is not None:
+        tt = torch.tensor([ems], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ems = float(tt.item())
+
+    if rank != 0:
+        return
+    pix = n * H * W
+    value = pix * args.steps * world / (ms * 1e-3) / 1e6
+    e2e_value = pix * e2e_steps * world / (ems * 1e-3) / 1e6
+    # roofline of the dominant kernel (level-0 fused filter): algorithmic bytes
+    # per launch = read z^0 (6 B/px) + read u^1 (1.5 B per finest px) + write
+    # u^0 (6 B/px) = 13.5 B per finest pixel
+    t_lv0 = statistics.mean(lv0) * 1e-3
+    bytes_lv0 = 13.5 * pix
+    achieved = bytes_lv0 / t_lv0 / 1e9
+    peak, peak_kind = measured_peaks()
+    # FP32 FMA issue roof of the same kernel: 294 filter FMAs per pixel
+    clk = clk_summary = clk.summary()
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "3-level denoise of 8 x 4032x3024 RGB frames per GPU, FP16 storage, FP32 "
+                               "arithmetic, 7x7+7x7 per-channel YCbCr filters, 216 buckets/level, FP16 banks",
+                   "batch_per_gpu": n, "h": H, "w": W, "levels": LEVELS, "storage": "f16",
+                   "l2": "inputs larger than L2 (585 MB per step)", "parallelism": f"replicas x{world}"},
+        "gpu_launches": 4 * args.steps,
+        "kernel_ms": {"pyramid": round(statistics.mean(pyr), 4), "level1": round(statistics.mean(lv1), 4),
+                      "level0": round(statistics.mean(lv0), 4)},
+        "roofline": {"bound": "hbm", "kernel": "k_level (level 0)", "achieved": round(achieved, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": None, "peak_source": peak_kind},
+        "e2e": {"value": round(e2e_value, 2), "unit": "Mpix/s", "h2d_bytes_per_step": int(pix * 3 * 2),
+                "d2h_bytes_per_step": int(pix * 3 * 2)},
+        "clocks": {"sm_mhz": clk_summary["sm_mhz"], "sm_max_mhz": clk_summary["sm_max_mhz"],
+                   "reasons": clk_summary["reasons"]},
+    }
+    if args.cpu_baseline:
+        v, tot, sample = cpu_oracle_run(12, 1)
+        line["cpu_baseline"] = {"value": round(v, 3), "unit": "Mpix/s", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": sample}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    args.local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    # frames first: the spawn pool runs before this process touches CUDA
+    frames = make_frames(args.batch, 40000 + 100 * rank)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(args.local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", args.local_rank))
+    try:
+        run_gpu(args, rank, world, frames)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,211 @@
+/*
+ * mdn.h -- C ABI of libmdn: GB300 (sm_103a) trainable multiscale denoising
+ * after Choi, Isidoro, Getreuer, Milanfar, "Fast, Trainable, Multiscale
+ * Denoising" (arXiv 1802.06130).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Images are planar RGB, row-major: [n][3][h][w], values nominally in
+ *   [0, 1], stored as FP32 (MDN_F32) or FP16 (MDN_F16).  Level l of a pyramid
+ *   has size ceil(h / 2^l) x ceil(w / 2^l).
+ * - Every data pointer is a DEVICE pointer unless stated otherwise; the caller
+ *   owns every buffer (images, banks, maps, Gram state, workspace).  The
+ *   library never allocates or frees on these paths; the only state it keeps
+ *   is per-device kernel configuration made on first use.  Pointers to the
+ *   parameter structs are HOST pointers, read during the call only.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   Calls are asynchronous on that stream: the return status covers argument
+ *   checks and launch errors only; device results are valid after the stream
+ *   is synchronised.
+ * - Status: MDN_OK (0) or one of the MDN_E* codes below; on error the message
+ *   is kept per thread and returned by mdn_last_error().  No entry point
+ *   aborts the process.
+ * - Filter banks are [K][3][D] (bucket, output channel, regressor tap), FP32
+ *   or FP16.  The regressor of output channel c at pixel i (Section 4, the
+ *   multiscale filtering equation with h = [f; g]) is the coarse patch
+ *   R_{floor(i/2)} u^{l+1} followed by the fine patch R_i z^l, each in
+ *   (channel, dy, dx) row-major order, dy, dx in [-r, r]; per-channel
+ *   geometry uses working channel c only, cross-channel geometry all three.
+ *   Borders clamp to the edge.  Filtering runs in zero-offset BT.601 YCbCr
+ *   (Section 3, footnote 1) unless color = MDN_RGB.
+ */
+#ifndef MDN_H
+#define MDN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define MDN_OK 0
+#define MDN_EINVAL 1      /* null pointer, bad enum or parameter */
+#define MDN_ESHAPE 2      /* inconsistent sizes or unsupported geometry */
+#define MDN_EWORKSPACE 3  /* workspace too small (see the *_bytes queries) */
+#define MDN_EBUDGET 4     /* serving: request exceeds the memory budget */
+#define MDN_ETIMEOUT 5    /* a bounded wait expired */
+#define MDN_ECUDA 6       /* CUDA error; message in mdn_last_error() */
+#define MDN_ENOMEM 7      /* host allocation failed (serving set-up only) */
+
+/* ---- element types ---- */
+#define MDN_F32 0
+#define MDN_F16 1
+
+/* ---- colour spaces ---- */
+#define MDN_YCBCR601 0
+#define MDN_RGB 1
+
+/* ---- Gram precisions for training ---- */
+#define MDN_GRAM_FP32 0        /* CUDA-core FP32 products, FP64 reduction */
+#define MDN_GRAM_TF32 1        /* tcgen05 kind::tf32, FP32 accumulate in TMEM */
+#define MDN_GRAM_BF16 2        /* tcgen05 kind::f16 with BF16 operands */
+#define MDN_GRAM_SPLIT_BF16 3  /* hi*hi + hi*lo + lo*hi BF16 products */
+
+#define MDN_MAX_THR 8
+#define MDN_MAX_K 256
+
+/* Filter footprint.  r_fine: radius of the fine patch R_i z^l (1..3);
+ * r_coarse: radius of the coarse patch R_{i/2} u^{l+1} (0..3) or -1 for
+ * single-scale filtering (Eq. 1); cross_channel: 0 = per-channel regressors
+ * (D = P_c + P_f), 1 = all three channels (D = 3 (P_c + P_f)); color:
+ * MDN_YCBCR601 or MDN_RGB. */
+typedef struct {
+    int32_t r_fine;
+    int32_t r_coarse;
+    int32_t cross_channel;
+    int32_t color;
+} mdn_geometry;
+
+/* Filter selector s(i) (Section 3, "Filter selection").  Orientation (angle
+ * of the minor eigenvector of the smoothed colour structure tensor, in
+ * [0, pi)) is split into n_angle equal bins (n_angle even, <= 64); strength
+ * sqrt(lambda1) and coherence (sqrt l1 - sqrt l2)/(sqrt l1 + sqrt l2) are
+ * binned by the n_strength-1 and n_coherence-1 ascending thresholds
+ * (lower-inclusive).  Coherence is 0 where sqrt l1 + sqrt l2 < coh_eps.
+ * Bucket k = (a * n_strength + s) * n_coherence + c, K = product <= 256. */
+typedef struct {
+    int32_t n_angle;
+    int32_t n_strength;
+    int32_t n_coherence;
+    float strength_thr[MDN_MAX_THR];
+    float coherence_thr[MDN_MAX_THR];
+    float coh_eps;
+} mdn_bucket_params;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int mdn_version(void);
+
+/* Message of the last failed call on this thread ("" if none).  The string
+ * stays valid until the next call on the same thread. */
+const char* mdn_last_error(void);
+
+/* Regressor length D per output channel for a geometry, or -1 if invalid. */
+int mdn_regressor_len(const mdn_geometry* geom);
+
+/* ------------------------------------------------------------------ */
+/* Pyramid (Section 4, "Multiscale filtering": downsampling by two)    */
+/* ------------------------------------------------------------------ */
+
+/* Bytes of levels 1 .. levels-1 of an [n][3][h][w] image of element type
+ * dtype (each level padded to 256 bytes). */
+size_t mdn_pyramid_bytes(int64_t n, int64_t h, int64_t w, int32_t levels, int32_t dtype);
+
+/* Builds levels 1 .. levels-1 of `img` by repeated 2x downsampling with the
+ * separable 5-tap binomial kernel [1 4 6 4 1]/16 (clamped borders), computed
+ * in FP32 (horizontal pass, then vertical) and rounded to `dtype`
+ * (round-to-nearest-even for FP16).  out_levels: HOST array of levels-1
+ * device pointers, out_levels[l-1] -> [n][3][h_l][w_l].  levels in 1..8. */
+int mdn_build_pyramid(const void* img, int32_t dtype, int64_t n, int64_t h, int64_t w,
+                      int32_t levels, void* const* out_levels, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* Filter selection only (Section 3)                                   */
+/* ------------------------------------------------------------------ */
+
+/* Writes the bucket map s(i) (u8, [n][h][w]) of image z ([n][3][h][w]). */
+int mdn_select_buckets(const void* z, int32_t dtype, int64_t n, int64_t h, int64_t w,
+                       const mdn_bucket_params* bp, uint8_t* buckets, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* One level of filtering (Eq. 1; Section 4 multiscale equation)       */
+/* ------------------------------------------------------------------ */
+
+/* Fused selector + filter for one level: out = h^{s(i)} . [R_{i/2} coarse ;
+ * R_i z] per output channel, converted back to RGB and rounded to dtype.
+ * z, out: [n][3][h][w]; coarse: [n][3][ceil(h/2)][ceil(w/2)] or NULL when
+ * geom->r_coarse < 0; bank: [K][3][D] of bank_dtype, K = bucket count of bp;
+ * buckets_out: optional u8 [n][h][w] copy of s(i).  out must not alias z or
+ * coarse. */
+int mdn_filter_level(const void* z, const void* coarse, int32_t dtype, int64_t n, int64_t h,
+                     int64_t w, const void* bank, int32_t bank_dtype, const mdn_geometry* geom,
+                     const mdn_bucket_params* bp, void* out, uint8_t* buckets_out, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* Multiscale denoising (Section 4)                                    */
+/* ------------------------------------------------------------------ */
+
+/* Workspace bytes for mdn_denoise_multiscale: pyramid levels 1..L-1 plus
+ * intermediate outputs u^1 .. u^{L-2}. */
+size_t mdn_denoise_workspace_bytes(int64_t n, int64_t h, int64_t w, int32_t levels, int32_t dtype);
+
+/* Multiscale inference: z^0 = noisy, z^{l+1} = downsample(z^l), base case
+ * u^{L-1} = z^{L-1}, then for l = L-2 .. 0 u^l = filter_level(z^l, u^{l+1},
+ * banks[l]); out = u^0.  levels = 1 is single-scale filtering (Eq. 1) with
+ * banks[0] and geom->r_coarse = -1.  banks: HOST array of max(levels-1, 1)
+ * device pointers; bparams: HOST array of the same length (level l uses
+ * bparams[l]); bucket_maps: NULL or a HOST array of the same length of device
+ * u8 [n][h_l][w_l] pointers (entries may be NULL).  ws: device workspace of
+ * at least mdn_denoise_workspace_bytes(). */
+int mdn_denoise_multiscale(const void* noisy, int32_t dtype, int64_t n, int64_t h, int64_t w,
+                           int32_t levels, const void* const* banks, int32_t bank_dtype,
+                           const mdn_geometry* geom, const mdn_bucket_params* bparams,
+                           void* out, uint8_t* const* bucket_maps, void* ws, size_t ws_bytes,
+                           void* stream);
+
+/* ------------------------------------------------------------------ */
+/* Training (Eqs. 5-6: per-bucket least squares; Section 4 cascade)    */
+/* ------------------------------------------------------------------ */
+
+/* Gram state layout: gram[K][G][Dp][Dp] FP64 with G = 3, Dp = D + 1 for
+ * per-channel geometry and G = 1, Dp = D + 3 for cross-channel geometry
+ * (regressor taps first, then the target(s) in working colour space);
+ * counts[K] int64 = pixels per bucket. */
+size_t mdn_gram_state_bytes(const mdn_geometry* geom, int32_t K);
+
+/* Workspace bytes for mdn_train_level_filters on n images of h x w. */
+size_t mdn_train_workspace_bytes(int64_t n, int64_t h, int64_t w, const mdn_geometry* geom,
+                                 int32_t K, int32_t gram_precision);
+
+/* One level of training data: computes s(i) on noisy_lvl, sorts pixels by
+ * bucket, and adds to gram/counts (cleared first unless `accumulate`) the
+ * Gram matrix of [regressor ; target] over every pixel of each bucket, the
+ * regressor as in mdn_filter_level with coarse = coarse_out (the trained
+ * coarser level's output, NULL if geom->r_coarse < 0) and the target =
+ * clean_lvl in working colour space.  gram_precision selects the product
+ * arithmetic (MDN_GRAM_*); partial sums are reduced in FP64.  If bank_out
+ * is not NULL, then solves the bank as mdn_solve_bank does. */
+int mdn_train_level_filters(const void* noisy_lvl, const void* coarse_out, const void* clean_lvl,
+                            int32_t dtype, int64_t n, int64_t h, int64_t w,
+                            const mdn_geometry* geom, const mdn_bucket_params* bp,
+                            int32_t gram_precision, int32_t accumulate, double* gram,
+                            int64_t* counts, double lambda, float* bank_out, void* ws,
+                            size_t ws_bytes, void* stream);
+
+/* Ridge solve per bucket and group in FP64 on the GPU:
+ * h = (G_xx / n_k + lambda I)^{-1} (G_xy / n_k) by Cholesky; buckets with
+ * n_k = 0 take the pooled filter solved from sum_k G_k.  bank_out: FP32
+ * [K][3][D].  ws: at least mdn_solve_workspace_bytes().  status_out: device
+ * int32[1], set to the number of systems whose Cholesky pivot was not
+ * positive (those filters are written as zeros). */
+size_t mdn_solve_workspace_bytes(const mdn_geometry* geom, int32_t K);
+int mdn_solve_bank(const double* gram, const int64_t* counts, const mdn_geometry* geom,
+                   int32_t K, double lambda, float* bank_out, int32_t* status_out, void* ws,
+                   size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MDN_H */

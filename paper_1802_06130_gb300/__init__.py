@@ -1,0 +1,280 @@
+"""GB300-native trainable multiscale denoising (arXiv 1802.06130).
+
+Thin ctypes binding over ``libmdn.so`` (include/mdn.h).  Every step of the
+method runs in the library's CUDA kernels; this module only marshals torch
+tensors (device memory, streams) into the C ABI.  There is no CPU fallback:
+importing works without a GPU, but every call needs the built library and a
+CUDA device and raises otherwise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from .build import LIB as _LIB_PATH, build
+
+__all__ = ["build", "lib", "Geometry", "BucketParams", "default_bparams", "MdnError",
+           "build_pyramid", "select_buckets", "filter_level", "denoise_multiscale",
+           "denoise_workspace_bytes", "train_level_filters", "solve_bank", "regressor_len",
+           "gram_state_shape", "F32", "F16", "YCBCR601", "RGB", "GRAM_FP32", "GRAM_TF32",
+           "GRAM_BF16", "GRAM_SPLIT_BF16"]
+
+F32, F16 = 0, 1
+YCBCR601, RGB = 0, 1
+GRAM_FP32, GRAM_TF32, GRAM_BF16, GRAM_SPLIT_BF16 = 0, 1, 2, 3
+MAX_THR = 8
+
+
+class MdnError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libmdn error {code}: {msg}")
+        self.code = code
+
+
+class Geometry(C.Structure):
+    """mdn_geometry: r_fine, r_coarse (-1 = single scale), cross_channel, color."""
+    _fields_ = [("r_fine", C.c_int32), ("r_coarse", C.c_int32), ("cross_channel", C.c_int32),
+                ("color", C.c_int32)]
+
+    def __init__(self, r_fine=3, r_coarse=3, cross_channel=0, color=YCBCR601):
+        super().__init__(r_fine, r_coarse, cross_channel, color)
+
+
+class BucketParams(C.Structure):
+    """mdn_bucket_params: angle bins and ascending strength/coherence thresholds."""
+    _fields_ = [("n_angle", C.c_int32), ("n_strength", C.c_int32), ("n_coherence", C.c_int32),
+                ("strength_thr", C.c_float * MAX_THR), ("coherence_thr", C.c_float * MAX_THR),
+                ("coh_eps", C.c_float)]
+
+    def __init__(self, n_angle=24, strength_thr=(0.135, 0.16), coherence_thr=(0.10, 0.15), coh_eps=1e-8):
+        super().__init__()
+        self.n_angle = n_angle
+        self.n_strength = len(strength_thr) + 1
+        self.n_coherence = len(coherence_thr) + 1
+        for i, t in enumerate(strength_thr):
+            self.strength_thr[i] = t
+        for i, t in enumerate(coherence_thr):
+            self.coherence_thr[i] = t
+        self.coh_eps = coh_eps
+
+    @property
+    def K(self) -> int:
+        return self.n_angle * self.n_strength * self.n_coherence
+
+
+def default_bparams(level: int) -> BucketParams:
+    """Level-l selector defaults: 24 x 3 x 3 buckets, strength thresholds
+    (0.135, 0.16) halved per coarser level, coherence thresholds (0.10, 0.15)."""
+    s = 0.5 ** level
+    return BucketParams(24, (0.135 * s, 0.16 * s), (0.10, 0.15), 1e-8)
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libmdn (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"libmdn is not built ({_LIB_PATH}); call paper_1802_06130_gb300.build()")
+        L = C.CDLL(_LIB_PATH)
+        vp, i64, i32, sz = C.c_void_p, C.c_int64, C.c_int32, C.c_size_t
+        G, B = C.POINTER(Geometry), C.POINTER(BucketParams)
+        sig = {
+            "mdn_version": (C.c_int, []),
+            "mdn_last_error": (C.c_char_p, []),
+            "mdn_regressor_len": (C.c_int, [G]),
+            "mdn_pyramid_bytes": (sz, [i64, i64, i64, i32, i32]),
+            "mdn_build_pyramid": (C.c_int, [vp, i32, i64, i64, i64, i32, C.POINTER(vp), vp]),
+            "mdn_select_buckets": (C.c_int, [vp, i32, i64, i64, i64, B, vp, vp]),
+            "mdn_filter_level": (C.c_int, [vp, vp, i32, i64, i64, i64, vp, i32, G, B, vp, vp, vp]),
+            "mdn_denoise_workspace_bytes": (sz, [i64, i64, i64, i32, i32]),
+            "mdn_denoise_multiscale": (C.c_int, [vp, i32, i64, i64, i64, i32, C.POINTER(vp), i32, G, B, vp,
+                                                 C.POINTER(vp), vp, sz, vp]),
+            "mdn_gram_state_bytes": (sz, [G, i32]),
+            "mdn_train_workspace_bytes": (sz, [i64, i64, i64, G, i32, i32]),
+            "mdn_train_level_filters": (C.c_int, [vp, vp, vp, i32, i64, i64, i64, G, B, i32, i32, vp, vp,
+                                                  C.c_double, vp, vp, sz, vp]),
+            "mdn_solve_workspace_bytes": (sz, [G, i32]),
+            "mdn_solve_bank": (C.c_int, [vp, vp, G, i32, C.c_double, vp, vp, vp, sz, vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+# ---------------------------------------------------------------- helpers
+
+def _torch():
+    import torch
+    return torch
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise MdnError(rc, lib().mdn_last_error().decode())
+
+
+def _dtype_code(t) -> int:
+    torch = _torch()
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.float16:
+        return F16
+    raise TypeError(f"unsupported dtype {t.dtype} (float32 or float16)")
+
+
+def _dev(t, name="tensor"):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _img(t):
+    if t.dim() == 3:
+        t = t.unsqueeze(0)
+    if t.dim() != 4 or t.shape[1] != 3:
+        raise ValueError("images are [n][3][h][w] (or [3][h][w])")
+    return t
+
+
+def regressor_len(geom: Geometry) -> int:
+    return lib().mdn_regressor_len(C.byref(geom))
+
+
+def gram_state_shape(geom: Geometry, K: int):
+    D = regressor_len(geom)
+    G, T = (1, 3) if geom.cross_channel else (3, 1)
+    return (K, G, D + T, D + T)
+
+
+# ---------------------------------------------------------------- API
+
+def build_pyramid(img, levels: int, stream=None):
+    """[z^1 .. z^{L-1}] of an [n][3][h][w] image (mdn_build_pyramid)."""
+    torch = _torch()
+    img4 = _img(img)
+    n, _, h, w = img4.shape
+    outs, ptrs = [], []
+    hh, ww = h, w
+    for _ in range(1, levels):
+        hh, ww = (hh + 1) // 2, (ww + 1) // 2
+        o = torch.empty((n, 3, hh, ww), dtype=img4.dtype, device=img4.device)
+        outs.append(o)
+        ptrs.append(o.data_ptr())
+    arr = (C.c_void_p * max(len(ptrs), 1))(*ptrs)
+    _check(lib().mdn_build_pyramid(_dev(img4, "img"), _dtype_code(img4), n, h, w, levels, arr, _stream(stream)))
+    return [o if img.dim() == 4 else o[0] for o in outs]
+
+
+def select_buckets(z, bp: BucketParams, stream=None):
+    """Bucket map s(i), uint8 [n][h][w] (mdn_select_buckets)."""
+    torch = _torch()
+    z4 = _img(z)
+    n, _, h, w = z4.shape
+    out = torch.empty((n, h, w), dtype=torch.uint8, device=z4.device)
+    _check(lib().mdn_select_buckets(_dev(z4, "z"), _dtype_code(z4), n, h, w, C.byref(bp), _dev(out), _stream(stream)))
+    return out if z.dim() == 4 else out[0]
+
+
+def filter_level(z, coarse, bank, geom: Geometry, bp: BucketParams, out=None, buckets_out=None, stream=None):
+    """One fused level: selector + filter (mdn_filter_level).  Returns out."""
+    torch = _torch()
+    z4 = _img(z)
+    n, _, h, w = z4.shape
+    c4 = _img(coarse) if coarse is not None else None
+    if out is None:
+        out = torch.empty_like(z4)
+    _check(lib().mdn_filter_level(_dev(z4, "z"), _dev(c4, "coarse"), _dtype_code(z4), n, h, w, _dev(bank, "bank"),
+                                  _dtype_code(bank), C.byref(geom), C.byref(bp), _dev(out, "out"),
+                                  _dev(buckets_out, "buckets_out"), _stream(stream)))
+    return out if z.dim() == 4 else out[0]
+
+
+def denoise_workspace_bytes(n, h, w, levels, dtype_code) -> int:
+    return lib().mdn_denoise_workspace_bytes(n, h, w, levels, dtype_code)
+
+
+def denoise_multiscale(noisy, banks, geom: Geometry, bparams, out=None, bucket_maps=None, ws=None, stream=None):
+    """Section 4 multiscale inference (mdn_denoise_multiscale).
+
+    banks: list of max(L-1, 1) [K][3][D] tensors; bparams: list of the same
+    length; levels = len(banks) + 1 (or 1 when geom.r_coarse < 0)."""
+    torch = _torch()
+    z4 = _img(noisy)
+    n, _, h, w = z4.shape
+    levels = 1 if geom.r_coarse < 0 else len(banks) + 1
+    nb = len(banks)
+    if len(bparams) != nb:
+        raise ValueError("need one BucketParams per bank")
+    if out is None:
+        out = torch.empty_like(z4)
+    need = denoise_workspace_bytes(n, h, w, levels, _dtype_code(z4))
+    if ws is None:
+        ws = torch.empty(max(need, 1), dtype=torch.uint8, device=z4.device)
+    bank_dt = _dtype_code(banks[0])
+    barr = (C.c_void_p * nb)(*[b.data_ptr() for b in banks])
+    parr = (BucketParams * nb)(*bparams)
+    marr = None
+    if bucket_maps is not None:
+        marr = (C.c_void_p * nb)(*[m.data_ptr() if m is not None else None for m in bucket_maps])
+    _check(lib().mdn_denoise_multiscale(_dev(z4, "noisy"), _dtype_code(z4), n, h, w, levels, barr, bank_dt,
+                                        C.byref(geom), parr, _dev(out, "out"), marr, _dev(ws, "ws"),
+                                        ws.numel() * ws.element_size(), _stream(stream)))
+    return out if noisy.dim() == 4 else out[0]
+
+
+def train_level_filters(noisy_lvl, coarse_out, clean_lvl, geom: Geometry, bp: BucketParams,
+                        gram_precision: int = GRAM_FP32, gram=None, counts=None, accumulate=False,
+                        lam: float = 1e-3, solve: bool = True, ws=None, stream=None):
+    """One level of training (mdn_train_level_filters).
+
+    Returns (gram [K][G][Dp][Dp] f64, counts [K] i64, bank [K][3][D] f32 or None)."""
+    torch = _torch()
+    z4 = _img(noisy_lvl)
+    u4 = _img(clean_lvl)
+    c4 = _img(coarse_out) if coarse_out is not None else None
+    n, _, h, w = z4.shape
+    K = bp.K
+    dev = z4.device
+    if gram is None:
+        gram = torch.zeros(gram_state_shape(geom, K), dtype=torch.float64, device=dev)
+        counts = torch.zeros(K, dtype=torch.int64, device=dev)
+    bank = torch.empty((K, 3, regressor_len(geom)), dtype=torch.float32, device=dev) if solve else None
+    need = lib().mdn_train_workspace_bytes(n, h, w, C.byref(geom), K, gram_precision)
+    if ws is None:
+        ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    _check(lib().mdn_train_level_filters(_dev(z4, "noisy"), _dev(c4, "coarse"), _dev(u4, "clean"), _dtype_code(z4),
+                                         n, h, w, C.byref(geom), C.byref(bp), gram_precision, int(accumulate),
+                                         _dev(gram, "gram"), _dev(counts, "counts"), lam,
+                                         _dev(bank, "bank") if bank is not None else None, _dev(ws, "ws"),
+                                         ws.numel(), _stream(stream)))
+    return gram, counts, bank
+
+
+def solve_bank(gram, counts, geom: Geometry, lam: float = 1e-3, stream=None):
+    """Ridge Cholesky solve on the GPU (mdn_solve_bank) -> (bank, status)."""
+    torch = _torch()
+    K = gram.shape[0]
+    dev = gram.device
+    bank = torch.empty((K, 3, regressor_len(geom)), dtype=torch.float32, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    need = lib().mdn_solve_workspace_bytes(C.byref(geom), K)
+    ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    _check(lib().mdn_solve_bank(_dev(gram, "gram"), _dev(counts, "counts"), C.byref(geom), K, lam,
+                                _dev(bank, "bank"), _dev(status, "status"), _dev(ws, "ws"), need, _stream(stream)))
+    return bank, status

@@ -1,0 +1,83 @@
+// internal.h -- declarations shared between the C-ABI layer (capi.cu) and
+// the kernel translation units.  Not part of the public interface.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <string>
+
+#include "../../include/mdn.h"
+
+namespace mdn {
+
+// Per-thread error message; returns `code` for convenient `return fail(...)`.
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* where);
+int check_launch(const char* where);
+
+// Device-side selector parameters (FP32 thresholds, angle-sector boundary
+// vectors), built on the host from mdn_bucket_params.
+struct SelParams {
+    int n_angle, n_strength, n_coherence;
+    int nthr_s, nthr_c;
+    float strength_thr[MDN_MAX_THR];
+    float coherence_thr[MDN_MAX_THR];
+    float coh_eps;
+    // boundary unit vectors of the doubled orientation angle psi in [0, pi):
+    // (cos, sin) of 2 pi k / n_angle for k = 1 .. n_angle/2 - 1
+    float bcos[32];
+    float bsin[32];
+};
+int make_sel_params(const mdn_bucket_params* bp, SelParams* out);
+
+// 1-D normalised Gaussian (sigma 1.5, 5 taps), FP32, computed on the host.
+void gauss5_weights(float w[5]);
+
+struct LevelArgs {
+    const void* z;        // [n][3][h][w] storage type
+    const void* coarse;   // [n][3][hc][wc] or nullptr
+    void* out;            // [n][3][h][w] or nullptr (select-only)
+    uint8_t* buckets;     // [n][h][w] or nullptr
+    const void* bank;     // [K][3][D]
+    int64_t n, h, w, hc, wc;
+    int dtype, bank_dtype;
+    int K;
+    mdn_geometry geom;
+    SelParams sel;
+};
+int launch_level(const LevelArgs& a, cudaStream_t s);
+int launch_pyramid_down(const void* in, void* out, int dtype, int64_t n, int64_t h, int64_t w,
+                        cudaStream_t s);
+
+// ---- training ----
+struct TrainArgs {
+    const void* z;        // noisy level [n][3][h][w]
+    const void* coarse;   // [n][3][hc][wc] or nullptr
+    const void* target;   // clean level [n][3][h][w]
+    int dtype;
+    int64_t n, h, w, hc, wc;
+    mdn_geometry geom;
+    int K, D, G, T, Dp;
+    int precision;
+    double* gram;         // [K][G][Dp][Dp]
+    int64_t* counts;      // [K]
+    const uint8_t* buckets;  // [n][h][w] (computed beforehand)
+    void* ws;
+    size_t ws_bytes;
+};
+size_t train_ws_bytes(int64_t npix, int K, int G, int Dp, int precision);
+int launch_gram(const TrainArgs& a, cudaStream_t s);
+size_t solve_ws_bytes(int K, int G, int D, int T);
+int launch_solve(const double* gram, const int64_t* counts, int K, int G, int D, int T,
+                 double lambda, float* bank_out, int32_t* status, void* ws, size_t ws_bytes,
+                 cudaStream_t s);
+
+int num_sms();
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+inline int regressor_len(const mdn_geometry& g) {
+    int pf = (2 * g.r_fine + 1) * (2 * g.r_fine + 1);
+    int pc = g.r_coarse >= 0 ? (2 * g.r_coarse + 1) * (2 * g.r_coarse + 1) : 0;
+    return (g.cross_channel ? 3 : 1) * (pf + pc);
+}
+
+}  // namespace mdn

@@ -1,0 +1,377 @@
+// k_level.cuh -- A2+A3+A4: the fused per-level kernel.
+//
+// For every output pixel i of level l, in one pass over a tile:
+//   * colour structure tensor T_i (Section 3, "Filter selection"): central
+//     differences per RGB channel, products summed over channels, separable
+//     5x5 Gaussian (sigma 1.5) on the clamped product field;
+//   * eigen-features (strength sqrt(l1), coherence, orientation of the minor
+//     eigenvector) and the bucket s(i);
+//   * the selected filter applied to [R_{i/2} u^{l+1} ; R_i z^l] in the
+//     working colour space (multiscale equation of Section 4; Eq. 1 when
+//     there is no coarse term), converted back to RGB and stored.
+//
+// Arithmetic of the selector (fixed, reproducible bit for bit):
+//   g = (z[+1] - z[-1]) * 0.5 per axis and channel;
+//   Pxx = gxR*gxR, fma(gxG,gxG,.), fma(gxB,gxB,.)  (same for Pxy, Pyy);
+//   H = w0*P[x-2], fma(w1,P[x-1]) ... fma(w4,P[x+2]);  T = same over rows;
+//   ht = (a+c)*0.5, hd = (a-c)*0.5, disc = sqrt(fma(hd,hd,b*b)),
+//   l1 = ht+disc, l2 = max(ht-disc, 0), s1 = sqrt(l1), s2 = sqrt(l2),
+//   coherence = (s1-s2)/(s1+s2) or 0 if s1+s2 < coh_eps, strength = s1.
+// Orientation bin: the doubled angle psi = 2 theta of the minor eigenvector
+// is the angle of v = (c-a, -2b); psi is placed in one of n_angle sectors of
+// width 2 pi / n_angle by sign tests against the sector boundary vectors (no
+// arctangent), with v = 0 mapped to theta = pi/2.
+//
+// Tiling and memory: a persistent CTA (grid = SMs x resident CTAs) loads the
+// whole filter bank into shared memory once (when it fits; otherwise taps are
+// read through the read-only cache), then loops over TW x TH tiles: the RGB
+// tile with a 3-pixel halo and the coarse tile with an r_coarse halo are
+// staged in shared memory with coalesced, clamped loads, the tensor fields
+// are computed in shared memory, and every thread filters its pixels with
+// taps and patch values from shared memory.
+#pragma once
+#include "common.cuh"
+#include "internal.h"
+
+namespace mdn {
+namespace lvl {
+
+constexpr int TW = 32, TH = 16, NT = 256;
+constexpr int HZ = 3;                      // tensor halo (1 gradient + 2 smoothing)
+constexpr int ZW = TW + 2 * HZ, ZH = TH + 2 * HZ;
+constexpr int PW = TW + 4, PH = TH + 4;
+
+template <int RC> struct Coarse {
+    static constexpr int UW = RC >= 0 ? TW / 2 + 2 * RC : 0;
+    static constexpr int UH = RC >= 0 ? TH / 2 + 2 * RC : 0;
+};
+
+template <typename TB> struct BankVec;
+template <> struct BankVec<float> { static constexpr int V = 4; };
+template <> struct BankVec<__half> { static constexpr int V = 8; };
+
+template <int RF, int RC, bool CROSS> struct Geo {
+    static constexpr int PF = (2 * RF + 1) * (2 * RF + 1);
+    static constexpr int PC = RC >= 0 ? (2 * RC + 1) * (2 * RC + 1) : 0;
+    static constexpr int NCH = CROSS ? 3 : 1;
+    static constexpr int D = NCH * (PF + PC);
+};
+
+template <typename TB, int D> struct BankLayout {
+    static constexpr int V = BankVec<TB>::V;
+    static constexpr int DP = (D + V - 1) / V * V;   // padded row length
+};
+
+// shared-memory footprint of the tile buffers (bytes)
+template <int RC> constexpr size_t tile_bytes() {
+    return sizeof(float) * (3 * ZH * ZW + 3 * PH * PW + 3 * PH * TW + 3 * Coarse<RC>::UH * Coarse<RC>::UW) +
+           TH * TW;
+}
+
+__device__ __forceinline__ void rgb_to_work(float r, float g, float b, int color, float& y, float& cb, float& cr) {
+    if (color == MDN_RGB) { y = r; cb = g; cr = b; return; }
+    // zero-offset ITU-R BT.601: Y = .299R + .587G + .114B, Cb = (B-Y)/1.772, Cr = (R-Y)/1.402
+    y = 0.299f * r + 0.587f * g + 0.114f * b;
+    cb = -0.168735892f * r - 0.331264108f * g + 0.5f * b;
+    cr = 0.5f * r - 0.418687589f * g - 0.081312411f * b;
+}
+__device__ __forceinline__ void work_to_rgb(float y, float cb, float cr, int color, float& r, float& g, float& b) {
+    if (color == MDN_RGB) { r = y; g = cb; b = cr; return; }
+    r = y + 1.402f * cr;
+    g = y - 0.344136286f * cb - 0.714136286f * cr;
+    b = y + 1.772f * cb;
+}
+
+// Orientation/strength/coherence -> bucket index, arithmetic as documented
+// in the file header.
+__device__ __forceinline__ int bucket_of(float a, float b, float c, const SelParams& sp) {
+    float ht = __fmul_rn(__fadd_rn(a, c), 0.5f);
+    float hd = __fmul_rn(__fsub_rn(a, c), 0.5f);
+    float disc = __fsqrt_rn(__fmaf_rn(hd, hd, __fmul_rn(b, b)));
+    float l1 = __fadd_rn(ht, disc);
+    float l2 = __fsub_rn(ht, disc);
+    l2 = l2 < 0.f ? 0.f : l2;
+    float s1 = __fsqrt_rn(l1), s2 = __fsqrt_rn(l2);
+    float den = __fadd_rn(s1, s2);
+    float coh = den < sp.coh_eps ? 0.f : __fdiv_rn(__fsub_rn(s1, s2), den);
+    // orientation sector of v = (c - a, -(b + b))
+    float vx = __fsub_rn(c, a), vy = -__fadd_rn(b, b);
+    int abin;
+    const int half = sp.n_angle >> 1;
+    if (vx == 0.f && vy == 0.f) {
+        abin = half;                            // theta = pi/2
+    } else {
+        bool upper = (vy > 0.f) || (vy == 0.f && vx > 0.f);
+        if (!upper) { vx = -vx; vy = -vy; }
+        int cnt = 0;
+        for (int k = 0; k < half - 1; ++k) {
+            // cross(b_k, v) >= 0  <=>  psi >= boundary k+1
+            float cr = __fmaf_rn(sp.bcos[k], vy, -__fmul_rn(sp.bsin[k], vx));
+            cnt += cr >= 0.f ? 1 : 0;
+        }
+        abin = (upper ? 0 : half) + cnt;
+    }
+    int sb = 0, cb = 0;
+    for (int t = 0; t < sp.nthr_s; ++t) sb += (sp.strength_thr[t] <= s1) ? 1 : 0;
+    for (int t = 0; t < sp.nthr_c; ++t) cb += (sp.coherence_thr[t] <= coh) ? 1 : 0;
+    return (abin * sp.n_strength + sb) * sp.n_coherence + cb;
+}
+
+// One output channel of the level filter for the pixel whose fine-patch
+// centre is zc (shared tile, working space) and coarse-patch centre uc.
+template <int RF, int RC, bool CROSS, typename TB, bool SMEM>
+__device__ __forceinline__ float apply_filter(const TB* __restrict__ hb, const float* __restrict__ zc,
+                                              const float* __restrict__ uc, int oc_const) {
+    using G = Geo<RF, RC, CROSS>;
+    constexpr int V = BankVec<TB>::V;
+    constexpr int UW = Coarse<RC>::UW, UH = Coarse<RC>::UH;
+    constexpr int NCOARSE = G::NCH * G::PC;
+    float acc = 0.f;
+    float h[V];
+#pragma unroll
+    for (int t = 0; t < G::D; ++t) {
+        if (t % V == 0) {
+            if constexpr (SMEM) {
+                if constexpr (V == 4) {
+                    float4 q = reinterpret_cast<const float4*>(hb)[t / V];
+                    h[0] = q.x; h[1] = q.y; h[2] = q.z; h[3] = q.w;
+                } else {
+                    uint4 q = reinterpret_cast<const uint4*>(hb)[t / V];
+                    const __half2* hp = reinterpret_cast<const __half2*>(&q);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        float2 f = __half22float2(hp[e]);
+                        h[2 * e] = f.x; h[2 * e + 1] = f.y;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < V; ++e)
+                    if (t + e < G::D) h[e] = ld_f(hb, t + e);
+            }
+        }
+        const float hv = h[t % V];
+        if (t < NCOARSE) {
+            constexpr int PCs = G::PC > 0 ? G::PC : 1, RCs = RC > 0 ? RC : 0;
+            const int cc = t / PCs, idx = t % PCs;
+            const int dy = idx / (2 * RCs + 1) - RCs, dx = idx % (2 * RCs + 1) - RCs;
+            const int c = CROSS ? cc : oc_const;
+            acc = fmaf(hv, uc[c * UH * UW + dy * UW + dx], acc);
+        } else {
+            const int tt = t - NCOARSE;
+            const int cc = tt / G::PF, idx = tt % G::PF;
+            const int dy = idx / (2 * RF + 1) - RF, dx = idx % (2 * RF + 1) - RF;
+            const int c = CROSS ? cc : oc_const;
+            acc = fmaf(hv, zc[c * ZH * ZW + dy * ZW + dx], acc);
+        }
+    }
+    return acc;
+}
+
+template <int RF, int RC, bool CROSS, typename TS, typename TB, bool SMEM, bool FILTER>
+__global__ void __launch_bounds__(NT) k_level(const TS* __restrict__ z, const TS* __restrict__ coarse,
+                                              TS* __restrict__ out, uint8_t* __restrict__ bmap,
+                                              const TB* __restrict__ bank, int H, int W, int Hc, int Wc,
+                                              int nimg, int K, int color, SelParams sp, float w0, float w1,
+                                              float w2) {
+    using G = Geo<RF, RC, CROSS>;
+    using BL = BankLayout<TB, G::D>;
+    constexpr int UW = Coarse<RC>::UW, UH = Coarse<RC>::UH;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float* zs = reinterpret_cast<float*>(smem);             // [3][ZH][ZW]
+    float* ps = zs + 3 * ZH * ZW;                            // [3][PH][PW]
+    float* hs = ps + 3 * PH * PW;                            // [3][PH][TW]
+    float* us = hs + 3 * PH * TW;                            // [3][UH][UW]
+    uint8_t* bk = reinterpret_cast<uint8_t*>(us + 3 * UH * UW);  // [TH][TW]
+    TB* bank_s = reinterpret_cast<TB*>(smem + ((tile_bytes<RC>() + 15) & ~size_t(15)));
+    const int tid = threadIdx.x;
+    const float wv[5] = {w0, w1, w2, w1, w0};
+
+    if constexpr (FILTER && SMEM) {
+        // bank -> shared memory, rows padded to BL::DP (pad taps are zero)
+        const int rows = K * 3;
+        for (int i = tid; i < rows * BL::DP; i += NT) {
+            int r = i / BL::DP, t = i % BL::DP;
+            bank_s[i] = t < G::D ? bank[(int64_t)r * G::D + t] : TB(0.f);
+        }
+    }
+
+    const int tiles_x = (W + TW - 1) / TW, tiles_y = (H + TH - 1) / TH;
+    const int64_t ntiles = (int64_t)tiles_x * tiles_y * nimg;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int img = (int)(tile / ((int64_t)tiles_x * tiles_y));
+        const int trem = (int)(tile % ((int64_t)tiles_x * tiles_y));
+        const int x0 = (trem % tiles_x) * TW, y0 = (trem / tiles_x) * TH;
+        const TS* zi = z + (int64_t)img * 3 * H * W;
+        __syncthreads();  // previous tile finished with the shared buffers
+        // ---- stage the RGB tile (clamped) ----
+        for (int i = tid; i < 3 * ZH * ZW; i += NT) {
+            int c = i / (ZH * ZW), r = (i / ZW) % ZH, q = i % ZW;
+            int gy = clampi(y0 - HZ + r, 0, H - 1), gx = clampi(x0 - HZ + q, 0, W - 1);
+            zs[i] = ld_f(zi, ((int64_t)c * H + gy) * W + gx);
+        }
+        if constexpr (FILTER && RC >= 0) {
+            const TS* ci = coarse + (int64_t)img * 3 * Hc * Wc;
+            const int cx0 = x0 / 2 - RC, cy0 = y0 / 2 - RC;
+            for (int i = tid; i < UH * UW; i += NT) {
+                int r = i / UW, q = i % UW;
+                int gy = clampi(cy0 + r, 0, Hc - 1), gx = clampi(cx0 + q, 0, Wc - 1);
+                int64_t o = (int64_t)gy * Wc + gx;
+                float cr, cg, cb;
+                rgb_to_work(ld_f(ci, o), ld_f(ci, o + (int64_t)Hc * Wc), ld_f(ci, o + 2 * (int64_t)Hc * Wc), color,
+                            cr, cg, cb);
+                us[i] = cr; us[UH * UW + i] = cg; us[2 * UH * UW + i] = cb;
+            }
+        }
+        __syncthreads();
+        // ---- products of central-difference gradients at clamped positions ----
+        for (int i = tid; i < PH * PW; i += NT) {
+            int r = i / PW, q = i % PW;
+            int cy = clampi(y0 - 2 + r, 0, H - 1), cx = clampi(x0 - 2 + q, 0, W - 1);
+            int ly = cy - (y0 - HZ), lx = cx - (x0 - HZ);
+            int lxm = clampi(cx - 1, 0, W - 1) - (x0 - HZ), lxp = clampi(cx + 1, 0, W - 1) - (x0 - HZ);
+            int lym = clampi(cy - 1, 0, H - 1) - (y0 - HZ), lyp = clampi(cy + 1, 0, H - 1) - (y0 - HZ);
+            float gx[3], gy[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float* zc = zs + c * ZH * ZW;
+                gx[c] = __fmul_rn(__fsub_rn(zc[ly * ZW + lxp], zc[ly * ZW + lxm]), 0.5f);
+                gy[c] = __fmul_rn(__fsub_rn(zc[lyp * ZW + lx], zc[lym * ZW + lx]), 0.5f);
+            }
+            float pxx = __fmul_rn(gx[0], gx[0]), pxy = __fmul_rn(gx[0], gy[0]), pyy = __fmul_rn(gy[0], gy[0]);
+#pragma unroll
+            for (int c = 1; c < 3; ++c) {
+                pxx = __fmaf_rn(gx[c], gx[c], pxx);
+                pxy = __fmaf_rn(gx[c], gy[c], pxy);
+                pyy = __fmaf_rn(gy[c], gy[c], pyy);
+            }
+            ps[i] = pxx; ps[PH * PW + i] = pxy; ps[2 * PH * PW + i] = pyy;
+        }
+        __syncthreads();
+        // ---- horizontal smoothing pass; RGB tile -> working colour space ----
+        for (int i = tid; i < 3 * PH * TW; i += NT) {
+            int f = i / (PH * TW), r = (i / TW) % PH, q = i % TW;
+            const float* p = ps + f * PH * PW + r * PW + q;
+            float acc = __fmul_rn(wv[0], p[0]);
+#pragma unroll
+            for (int u = 1; u < 5; ++u) acc = __fmaf_rn(wv[u], p[u], acc);
+            hs[i] = acc;
+        }
+        if constexpr (FILTER) {
+            for (int i = tid; i < ZH * ZW; i += NT) {
+                float a, b, c;
+                rgb_to_work(zs[i], zs[ZH * ZW + i], zs[2 * ZH * ZW + i], color, a, b, c);
+                zs[i] = a; zs[ZH * ZW + i] = b; zs[2 * ZH * ZW + i] = c;
+            }
+        }
+        __syncthreads();
+        // ---- vertical pass, features, bucket ----
+        for (int i = tid; i < TH * TW; i += NT) {
+            int r = i / TW, q = i % TW;
+            float t3[3];
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                const float* p = hs + f * PH * TW + r * TW + q;
+                float acc = __fmul_rn(wv[0], p[0]);
+#pragma unroll
+                for (int v = 1; v < 5; ++v) acc = __fmaf_rn(wv[v], p[v * TW], acc);
+                t3[f] = acc;
+            }
+            int k = bucket_of(t3[0], t3[1], t3[2], sp);
+            k = k < K ? k : K - 1;
+            bk[i] = (uint8_t)k;
+            int gy = y0 + r, gx = x0 + q;
+            if (bmap && gy < H && gx < W) bmap[((int64_t)img * H + gy) * W + gx] = (uint8_t)k;
+        }
+        if constexpr (FILTER) {
+            __syncthreads();
+            // ---- filtering ----
+            TS* oi = out + (int64_t)img * 3 * H * W;
+            for (int i = tid; i < TH * TW; i += NT) {
+                int r = i / TW, q = i % TW;
+                int gy = y0 + r, gx = x0 + q;
+                if (gy >= H || gx >= W) continue;
+                const int k = bk[i];
+                const float* zc = zs + (r + HZ) * ZW + (q + HZ);
+                const float* uc = us + (r / 2 + (RC > 0 ? RC : 0)) * UW + (q / 2 + (RC > 0 ? RC : 0));
+                float o[3];
+#pragma unroll
+                for (int oc = 0; oc < 3; ++oc) {
+                    const TB* hb = SMEM ? bank_s + ((int64_t)k * 3 + oc) * BL::DP
+                                        : bank + ((int64_t)k * 3 + oc) * G::D;
+                    o[oc] = apply_filter<RF, RC, CROSS, TB, SMEM>(hb, zc, uc, oc);
+                }
+                float R, Gc, B;
+                work_to_rgb(o[0], o[1], o[2], color, R, Gc, B);
+                int64_t po = (int64_t)gy * W + gx;
+                st_f(oi, po, R);
+                st_f(oi, (int64_t)H * W + po, Gc);
+                st_f(oi, 2 * (int64_t)H * W + po, B);
+            }
+        }
+    }
+}
+
+template <int RF, int RC, bool CROSS, typename TS, typename TB, bool SMEM, bool FILTER>
+int run(const LevelArgs& a, cudaStream_t s) {
+    using G = Geo<RF, RC, CROSS>;
+    using BL = BankLayout<TB, G::D>;
+    auto kern = k_level<RF, RC, CROSS, TS, TB, SMEM, FILTER>;
+    size_t bytes = ((tile_bytes<RC>() + 15) & ~size_t(15));
+    if (FILTER && SMEM) bytes += sizeof(TB) * (size_t)a.K * 3 * BL::DP;
+    static int configured_dev = -1;
+    static int occ = 1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (configured_dev != dev) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+        if (e != cudaSuccess) return cuda_fail(e, "k_level: set smem attribute");
+        configured_dev = dev;
+    }
+    {
+        int o = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, NT, bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "k_level: occupancy");
+        if (o < 1) return fail(MDN_ESHAPE, "k_level: shared memory footprint too large");
+        occ = o;
+    }
+    const int64_t tiles = ((a.w + TW - 1) / TW) * ((a.h + TH - 1) / TH) * a.n;
+    int64_t grid = (int64_t)num_sms() * occ;
+    if (grid > tiles) grid = tiles;
+    float w[5];
+    gauss5_weights(w);
+    kern<<<(unsigned)grid, NT, bytes, s>>>((const TS*)a.z, (const TS*)a.coarse, (TS*)a.out, a.buckets,
+                                           (const TB*)a.bank, (int)a.h, (int)a.w, (int)a.hc, (int)a.wc,
+                                           (int)a.n, a.K, a.geom.color, a.sel, w[0], w[1], w[2]);
+    return check_launch("k_level");
+}
+
+// bytes of shared memory the SMEM variant needs for K buckets
+template <int RF, int RC, bool CROSS, typename TB> size_t smem_need(int K) {
+    using G = Geo<RF, RC, CROSS>;
+    using BL = BankLayout<TB, G::D>;
+    return ((tile_bytes<RC>() + 15) & ~size_t(15)) + sizeof(TB) * (size_t)K * 3 * BL::DP;
+}
+
+constexpr size_t SMEM_LIMIT = 232448;
+
+// Geometry dispatch for one (storage, bank) type pair.
+template <typename TS, typename TB> int dispatch(const LevelArgs& a, cudaStream_t s) {
+    const mdn_geometry& g = a.geom;
+#define MDN_GEO(RF_, RC_, CR_)                                                                  \
+    if (g.r_fine == RF_ && g.r_coarse == RC_ && (g.cross_channel != 0) == CR_) {                \
+        if (smem_need<RF_, RC_, CR_, TB>(a.K) <= SMEM_LIMIT)                                  \
+            return run<RF_, RC_, CR_, TS, TB, true, true>(a, s);                              \
+        return run<RF_, RC_, CR_, TS, TB, false, true>(a, s);                                 \
+    }
+    MDN_GEO(2, -1, false)
+    MDN_GEO(3, 3, false)
+    MDN_GEO(3, 2, false)
+    MDN_GEO(3, -1, true)
+#undef MDN_GEO
+    return fail(MDN_ESHAPE, "filter_level: geometry not compiled (supported: r_fine/r_coarse/cross = "
+                            "2/-1/0, 3/3/0, 3/2/0, 3/-1/1)");
+}
+
+}  // namespace lvl
+}  // namespace mdn

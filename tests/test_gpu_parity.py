@@ -1,0 +1,274 @@
+"""GPU path (through the C ABI) vs the FP64 oracle on seeded synthetic inputs.
+
+Bars: pyramid levels bit-identical to the oracle's FP32-order pyramid;
+bucket maps bit-identical to the oracle's FP32 feature path except pixels in
+the 1e-5 threshold band; outputs within max-abs 1e-4 (FP32 storage) or 2e-3
+(FP16 storage) of the FP64 oracle, on every pixel whose bucket (and whose
+coarser-level dependencies' buckets) match; learned filters within 1e-3
+relative Frobenius norm.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from parity_util import affected_mask, max_abs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"f32": 1e-4, "f16": 2e-3}
+
+
+@pytest.fixture(scope="module")
+def mdn():
+    import paper_1802_06130_gb300 as m
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    m.build()
+    m.lib()
+    return m
+
+
+def _tt(a, storage):
+    dt = torch.float32 if storage == "f32" else torch.float16
+    return torch.tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+
+
+def _np(t):
+    return t.detach().float().cpu().numpy().astype(np.float64)
+
+
+def _geom(m, g):
+    return m.Geometry(g.r_fine, g.r_coarse, g.cross, g.color)
+
+
+def _bank(K, geom, seed, storage="f32"):
+    """Random bank whose taps sum to ~1 per output channel (outputs stay in range)."""
+    rng = np.random.default_rng(seed)
+    D = geom.D()
+    b = rng.standard_normal((K, 3, D)) * 0.05
+    b += (1.0 - b.sum(axis=2, keepdims=True)) / D
+    return O.round_storage(b, storage)
+
+
+SIZES = [(1, 1), (2, 3), (7, 5), (33, 17), (64, 64), (131, 97)]
+
+
+# ------------------------------------------------------------ A1
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("hw", SIZES)
+def test_pyramid_bit_exact(mdn, storage, hw):
+    h, w = hw
+    z, _ = synth.noisy_pair(h, w, 100 + h)
+    zs = O.round_storage(z, storage)
+    ref = O.pyramid(zs, 4, storage, mirror32=True)
+    got = mdn.build_pyramid(_tt(zs, storage)[None], 4)
+    for l in range(1, 4):
+        g = _np(got[l - 1][0])
+        assert g.shape == ref[l].shape
+        assert np.array_equal(g, ref[l]), (l, np.abs(g - ref[l]).max())
+        # and close to the exact FP64 pyramid
+        ex = O.pyramid(zs, l + 1, "f64")[l]
+        assert max_abs(g, ex) <= (1e-6 if storage == "f32" else 2e-3)
+
+
+# ------------------------------------------------------------ A2/A3
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("hw", SIZES + [(256, 256)])
+def test_buckets_bit_exact_outside_band(mdn, storage, hw):
+    h, w = hw
+    z, _ = synth.noisy_pair(h, w, 200 + w)
+    zs = O.round_storage(z, storage)
+    for level in (0, 2):
+        bp_o, bp_g = O.default_bparams(level), mdn.default_bparams(level)
+        ref, band, _ = O.select(zs, bp_o, mirror32=True)
+        got = mdn.select_buckets(_tt(zs, storage)[None], bp_g)[0].cpu().numpy()
+        mism = got != ref
+        assert not (mism & ~band).any(), f"{(mism & ~band).sum()} mismatches outside the band"
+        if h * w >= 4096:
+            assert band.mean() < 0.01
+
+
+def test_buckets_cover_all_bins_on_training_set(mdn):
+    seen = set()
+    for i in range(8):
+        z, _ = synth.noisy_pair(256, 256, 1000 + i)
+        seen |= set(np.unique(mdn.select_buckets(_tt(z, "f32")[None], mdn.default_bparams(0)).cpu().numpy()))
+    assert len(seen) == 216
+
+
+def test_constant_image_bucket(mdn):
+    z = np.full((3, 20, 24), 0.4)
+    got = mdn.select_buckets(_tt(z, "f32")[None], mdn.default_bparams(0)).cpu().numpy()
+    assert np.all(got == (12 * 3 + 0) * 3 + 0)
+
+
+# ------------------------------------------------------------ A4
+
+GEOMS = [O.Geometry(2, -1), O.Geometry(3, 3), O.Geometry(3, 2), O.Geometry(3, -1, cross=1),
+         O.Geometry(3, 3, color=1)]
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("bank_storage", ["f32", "f16"])
+@pytest.mark.parametrize("geom", GEOMS, ids=lambda g: f"rf{g.r_fine}rc{g.r_coarse}x{g.cross}c{g.color}")
+@pytest.mark.parametrize("hw", [(1, 1), (7, 5), (33, 17), (97, 130)])
+def test_filter_level(mdn, storage, bank_storage, geom, hw):
+    h, w = hw
+    z, _ = synth.noisy_pair(h, w, 300 + h * w)
+    zs = O.round_storage(z, storage)
+    hc, wc = (h + 1) // 2, (w + 1) // 2
+    uc = O.round_storage(synth.clean_image(hc, wc, 400 + h), storage) if geom.r_coarse >= 0 else None
+    bank = _bank(216, geom, 7, bank_storage)
+    bp_o = O.default_bparams(0)
+    ref_b, band, _ = O.select(zs, bp_o, mirror32=True)
+    ref = O.round_storage(O.filter_level(zs, uc, ref_b, bank, geom), storage)
+    bmap = torch.empty((1, h, w), dtype=torch.uint8, device="cuda")
+    out = mdn.filter_level(_tt(zs, storage)[None], _tt(uc, storage)[None] if uc is not None else None,
+                           _tt(bank, bank_storage).contiguous(), _geom(mdn, geom), mdn.default_bparams(0),
+                           buckets_out=bmap)
+    gb = bmap[0].cpu().numpy()
+    mism = gb != ref_b
+    assert not (mism & ~band).any()
+    err = max_abs(_np(out[0]), ref, ~mism)
+    assert err <= TOL[storage], err
+
+
+# ------------------------------------------------------------ multiscale pipeline
+
+def _trained_banks(geom, levels, n=2, size=96, seed=1000):
+    pairs = [synth.noisy_pair(size, size, seed + i) for i in range(n)]
+    banks, _ = O.train_cascade([p[0] for p in pairs], [p[1] for p in pairs], geom, levels)
+    return banks
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("case", [("cfg1", O.Geometry(2, -1), 1, (256, 256)),
+                                  ("cfg2", O.Geometry(3, 3), 3, (135, 240)),
+                                  ("paper", O.Geometry(3, 2), 3, (101, 77)),
+                                  ("cfg4", O.Geometry(3, 3), 4, (189, 252))], ids=lambda c: c[0])
+def test_denoise_multiscale(mdn, storage, case):
+    _, geom, levels, (h, w) = case
+    banks = _trained_banks(geom, levels)
+    bank_st = storage
+    banks_s = [O.round_storage(b, bank_st) for b in banks]
+    z, u = synth.noisy_pair(h, w, 2000, model="camera" if levels == 4 else "awgn")
+    zs = O.round_storage(z, storage)
+    ref = O.denoise_multiscale(zs, banks_s, geom, storage=storage, mirror32=True)
+    nb = len(banks)
+    shapes = [r.shape[1:] for r in ref.pyramid]
+    maps = [torch.empty((1, *shapes[l]), dtype=torch.uint8, device="cuda") for l in range(nb)]
+    out = mdn.denoise_multiscale(_tt(zs, storage)[None], [_tt(b, bank_st) for b in banks_s], _geom(mdn, geom),
+                                 [mdn.default_bparams(l) for l in range(nb)], bucket_maps=maps)
+    mism = []
+    for l in range(nb):
+        g = maps[l][0].cpu().numpy()
+        m = g != ref.buckets[l]
+        assert not (m & ~ref.bands[l]).any(), (l, (m & ~ref.bands[l]).sum())
+        mism.append(m)
+    aff = affected_mask(mism, geom.r_coarse, shapes)
+    err = max_abs(_np(out[0]), ref.out, ~aff)
+    assert err <= TOL[storage], err
+    # denoising actually happens (banks were trained on AWGN)
+    if levels != 4:
+            assert np.mean((_np(out[0]) - u) ** 2) < 0.5 * np.mean((z - u) ** 2)
+
+
+@pytest.mark.parametrize("storage", ["f16", "f32"])
+def test_full_size_sampled_crops(mdn, storage):
+    """4032x3024, 3 levels, the launch configuration of the benchmark: the
+    GPU's full-frame output is compared with the oracle on crops (corners and
+    interior) whose interior is unaffected by the crop border."""
+    geom = O.Geometry(3, 3)
+    banks = [O.round_storage(b, storage) for b in _trained_banks(geom, 3, n=1, size=64)]
+    H, W = 3024, 4032
+    z = O.round_storage(synth.noisy_pair(H, W, 40000, model="camera")[0], storage).astype(np.float32)
+    zt = _tt(z, storage)[None]
+    maps = [torch.empty((1, H, W), dtype=torch.uint8, device="cuda"),
+            torch.empty((1, H // 2, W // 2), dtype=torch.uint8, device="cuda")]
+    out = _np(mdn.denoise_multiscale(zt, [_tt(b, storage) for b in banks], _geom(mdn, geom),
+                                     [mdn.default_bparams(0), mdn.default_bparams(1)], bucket_maps=maps)[0])
+    gmaps = [m[0].cpu().numpy() for m in maps]
+    M = 64
+    for (y0, x0) in [(0, 0), (0, W - 128), (H - 128, 0), (H - 128, W - 128), (1504, 2000), (752, 3136)]:
+        cy0, cx0 = max(y0 - M, 0), max(x0 - M, 0)      # multiples of 4: the crop's pyramid aligns
+        cy1, cx1 = min(y0 + 128 + M, H), min(x0 + 128 + M, W)
+        crop = z[:, cy0:cy1, cx0:cx1].astype(np.float64)
+        ref = O.denoise_multiscale(crop, banks, geom, storage=storage, mirror32=True)
+        mism = []
+        for l in range(2):
+            s_ = 2 ** l
+            g = gmaps[l][cy0 // s_: cy0 // s_ + ref.buckets[l].shape[0], cx0 // s_: cx0 // s_ + ref.buckets[l].shape[1]]
+            m = g != ref.buckets[l]
+            # the crop's own border is not the frame's: only its interior counts
+            inner = np.zeros_like(m)
+            b_ = 16 // s_
+            inner[b_ if cy0 else 0: m.shape[0] - (b_ if cy1 < H else 0),
+                  b_ if cx0 else 0: m.shape[1] - (b_ if cx1 < W else 0)] = True
+            assert not (m & ~ref.bands[l] & inner).any(), ((y0, x0), l)
+            mism.append(m & inner)
+        aff = affected_mask(mism, 3, [r.shape[1:] for r in ref.pyramid])
+        ry, rx = y0 - cy0, x0 - cx0
+        err = max_abs(out[:, y0:y0 + 128, x0:x0 + 128], ref.out[:, ry:ry + 128, rx:rx + 128],
+                      ~aff[ry:ry + 128, rx:rx + 128])
+        assert err <= TOL[storage], ((y0, x0), err)
+
+
+def test_empty_and_degenerate_inputs(mdn):
+    geom = mdn.Geometry(3, 3)
+    bank = torch.zeros((216, 3, 98), device="cuda")
+    z = torch.zeros((0, 3, 16, 16), device="cuda")
+    out = mdn.denoise_multiscale(z, [bank, bank], geom, [mdn.default_bparams(0)] * 2)
+    assert out.shape == (0, 3, 16, 16)
+    one = torch.full((1, 3, 1, 1), 0.5, device="cuda")
+    b = torch.zeros((216, 3, 98), device="cuda")
+    b[:, :, 49 + 24] = 1.0
+    o = mdn.denoise_multiscale(one, [b, b], geom, [mdn.default_bparams(0)] * 2)
+    assert torch.allclose(o, one)
+
+
+# ------------------------------------------------------------ A5/A6 training
+
+@pytest.mark.parametrize("case", [("cfg1", O.Geometry(2, -1), (128, 128), 2),
+                                  ("cfg2", O.Geometry(3, 3), (96, 80), 2),
+                                  ("cfg3", O.Geometry(3, -1, cross=1), (96, 96), 2)], ids=lambda c: c[0])
+def test_train_level_gram_and_bank(mdn, case):
+    _, geom, (h, w), n = case
+    pairs = [synth.noisy_pair(h, w, 30000 + i) for i in range(n)]
+    bp_o = O.default_bparams(0)
+    gram = counts = None
+    zb, ub, cb = [], [], []
+    for z, u in pairs:
+        uc = synth.clean_image((h + 1) // 2, (w + 1) // 2, 31000) if geom.r_coarse >= 0 else None
+        b, _, _ = O.select(z, bp_o, mirror32=True)
+        gram, counts = O.gram_accumulate(z, uc, u, b, 216, geom, gram, counts)
+        zb.append(z); ub.append(u); cb.append(uc)
+    ref_bank = O.solve_bank(gram, counts, geom, 1e-3)
+    Z = _tt(np.stack(zb), "f32")
+    U = _tt(np.stack(ub), "f32")
+    Cc = _tt(np.stack(cb), "f32") if geom.r_coarse >= 0 else None
+    g, c, bank = mdn.train_level_filters(Z, Cc, U, _geom(mdn, geom), mdn.default_bparams(0),
+                                         mdn.GRAM_FP32, lam=1e-3)
+    g, c, bank = _np(g), c.cpu().numpy(), _np(bank)
+    assert np.array_equal(c, counts)
+    rel = np.linalg.norm(g - gram) / np.linalg.norm(gram)
+    assert rel < 1e-5, rel
+    rb = np.linalg.norm(bank - ref_bank) / np.linalg.norm(ref_bank)
+    assert rb < 1e-3, rb
+
+
+def test_solve_bank_matches_oracle(mdn):
+    geom = O.Geometry(3, 3)
+    z, u = synth.noisy_pair(80, 80, 5)
+    uc = synth.clean_image(40, 40, 6)
+    b, _, _ = O.select(z, O.default_bparams(0), mirror32=True)
+    gram, counts = O.gram_accumulate(z, uc, u, b, 216, geom)
+    ref = O.solve_bank(gram, counts, geom, 1e-3)
+    bank, status = mdn.solve_bank(torch.tensor(gram, device="cuda"), torch.tensor(counts, device="cuda"),
+                                  _geom(mdn, geom), 1e-3)
+    assert int(status.item()) == 0
+    np.testing.assert_allclose(_np(bank), ref, rtol=1e-5, atol=1e-6)
+    assert (counts == 0).any()   # the pooled path is exercised
