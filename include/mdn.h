@@ -164,6 +164,29 @@ int mdn_denoise_multiscale(const void* noisy, int32_t dtype, int64_t n, int64_t 
                            void* out, uint8_t* const* bucket_maps, void* ws, size_t ws_bytes,
                            void* stream);
 
+/* Same as mdn_denoise_multiscale, for callers that cannot allocate device
+ * memory: a plug-in inside a host application that owns every device
+ * allocation, or a real-time pipeline where an allocation (which may
+ * synchronise the device) is not allowed on the frame path.  The paper has
+ * no counterpart; this is a deployment convenience.  The caller still owns
+ * noisy, out, banks and bucket maps; the scratch (pyramid levels and
+ * intermediate outputs) comes from one static device array of
+ * MDN_STATIC_SCRATCH_BYTES (48 MiB) that every device loading the library
+ * holds until the process exits.  No cudaMalloc/cudaFree or other allocating
+ * call is made.  Images whose mdn_denoise_workspace_bytes() exceeds the array
+ * are rejected with MDN_EWORKSPACE (e.g. one 12 MP FP16 frame at 3 levels
+ * fits, eight do not).  The first call on a device, with that device
+ * current, looks up the array's address and caches it: make that first call
+ * before any stream capture.  All calls on a device share the array and it
+ * keeps the previous call's contents (nothing needs clearing: each call
+ * writes every scratch element before reading it), so calls whose GPU work
+ * overlaps (different streams or host threads) race: serialise them. */
+#define MDN_STATIC_SCRATCH_BYTES ((size_t)48 << 20)
+int mdn_denoise_multiscale_static(const void* noisy, int32_t dtype, int64_t n, int64_t h, int64_t w,
+                                  int32_t levels, const void* const* banks, int32_t bank_dtype,
+                                  const mdn_geometry* geom, const mdn_bucket_params* bparams,
+                                  void* out, uint8_t* const* bucket_maps, void* stream);
+
 /* ------------------------------------------------------------------ */
 /* Training (Eqs. 5-6: per-bucket least squares; Section 4 cascade)    */
 /* ------------------------------------------------------------------ */
