@@ -355,11 +355,636 @@ template <int RF, int RC, bool CROSS, typename TB> size_t smem_need(int K) {
 
 constexpr size_t SMEM_LIMIT = 232448;
 
+// ==========================================================================
+// Strip variant (v2): same selector stage; the filter stage gives every
+// thread a vertical strip of PY pixels of one column, so that each loaded
+// column of patch values (PY + 2r values) serves PY pixels and 2r+1 taps.
+// Shared-memory bank layout: for bucket k, output channel oc, block b (the
+// coarse then the fine patch of each input channel) and column dx, one
+// 8-element slot holding the 2r+1 taps of that column (dy = -r..r, zero
+// padded).  A slot is one 16-byte (FP16) or two 16-byte (FP32) loads; the
+// per-bucket stride is an odd number of 16-byte units so that lanes with
+// different buckets hit different bank groups.
+// ==========================================================================
+namespace v2 {
+
+#ifndef MDN_V2_NT
+#define MDN_V2_NT 384
+#endif
+#ifndef MDN_V2_PY
+#define MDN_V2_PY 4
+#endif
+constexpr int TW = 32, NT = MDN_V2_NT, PY = MDN_V2_PY, NW = NT / 32, TH = NW * PY;
+constexpr int HZ = 3;
+constexpr int ZW = TW + 2 * HZ, ZH = TH + 2 * HZ;
+constexpr int PW = TW + 4, PH = TH + 4;
+
+template <int RC> struct Coarse {
+    static constexpr int UW = RC >= 0 ? TW / 2 + 2 * RC : 0;
+    static constexpr int UH = RC >= 0 ? TH / 2 + 2 * RC : 0;
+};
+
+template <int RF, int RC, bool CROSS> struct Slots {
+    static constexpr int NCH = CROSS ? 3 : 1;
+    static constexpr int PER_OC = NCH * ((RC >= 0 ? 2 * RC + 1 : 0) + (2 * RF + 1));
+    static constexpr int S = 3 * PER_OC;    // slots per bucket
+};
+
+template <typename TB> struct SlotBytes;
+template <> struct SlotBytes<float> { static constexpr int B = 32; };
+template <> struct SlotBytes<__half> { static constexpr int B = 16; };
+
+// per-bucket stride in 16-byte units: odd
+template <int RF, int RC, bool CROSS, typename TB> constexpr int bucket_units() {
+    int u = Slots<RF, RC, CROSS>::S * SlotBytes<TB>::B / 16;
+    return (u % 2 == 1) ? u : u + 1;
+}
+
+template <int RC> constexpr size_t tile_bytes() {
+    return sizeof(float) * (3 * ZH * ZW + 3 * PH * PW + 3 * PH * TW + 3 * Coarse<RC>::UH * Coarse<RC>::UW) +
+           TH * TW;
+}
+
+template <int RF, int RC, bool CROSS, typename TB> size_t smem_need(int K) {
+    return ((tile_bytes<RC>() + 15) & ~size_t(15)) + (size_t)K * bucket_units<RF, RC, CROSS, TB>() * 16;
+}
+
+// 8 taps of one slot as floats
+template <typename TB> __device__ __forceinline__ void load_slot(const unsigned char* p, float h[8]);
+template <> __device__ __forceinline__ void load_slot<__half>(const unsigned char* p, float h[8]) {
+    uint4 q = *reinterpret_cast<const uint4*>(p);
+    const __half2* hp = reinterpret_cast<const __half2*>(&q);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        float2 f = __half22float2(hp[e]);
+        h[2 * e] = f.x; h[2 * e + 1] = f.y;
+    }
+}
+template <> __device__ __forceinline__ void load_slot<float>(const unsigned char* p, float h[8]) {
+    float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 16);
+    h[0] = a.x; h[1] = a.y; h[2] = a.z; h[3] = a.w; h[4] = b.x; h[5] = b.y; h[6] = b.z; h[7] = b.w;
+}
+
+template <int RF, int RC, bool CROSS, typename TS, typename TB>
+__global__ void __launch_bounds__(NT, 1) k_level2(const TS* __restrict__ z, const TS* __restrict__ coarse,
+                                                  TS* __restrict__ out, uint8_t* __restrict__ bmap,
+                                                  const TB* __restrict__ bank, int H, int W, int Hc, int Wc,
+                                                  int nimg, int K, int color, SelParams sp, float w0, float w1,
+                                                  float w2) {
+    using G = Geo<RF, RC, CROSS>;
+    using SL = Slots<RF, RC, CROSS>;
+    constexpr int UW = Coarse<RC>::UW, UH = Coarse<RC>::UH;
+    constexpr int SB = SlotBytes<TB>::B;
+    constexpr int BSTRIDE = bucket_units<RF, RC, CROSS, TB>() * 16;   // bytes per bucket
+    constexpr int NCX = RC >= 0 ? 2 * RC + 1 : 0;                       // coarse columns per channel
+    constexpr int NFX = 2 * RF + 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float* zs = reinterpret_cast<float*>(smem);             // [3][ZH][ZW]
+    float* ps = zs + 3 * ZH * ZW;                            // [3][PH][PW]
+    float* hs = ps + 3 * PH * PW;                            // [3][PH][TW]
+    float* us = hs + 3 * PH * TW;                            // [3][UH][UW]
+    uint8_t* bk = reinterpret_cast<uint8_t*>(us + 3 * UH * UW);  // [TH][TW]
+    unsigned char* bank_s = smem + ((tile_bytes<RC>() + 15) & ~size_t(15));
+    const int tid = threadIdx.x;
+    const float wv[5] = {w0, w1, w2, w1, w0};
+
+    // ---- bank -> slots (once per persistent CTA) ----
+    {
+        constexpr int E = SB / (int)sizeof(TB);   // 8 elements per slot
+        const int total = K * SL::S * E;
+        for (int i = tid; i < total; i += NT) {
+            const int e = i % E, slot = (i / E) % SL::S, k = i / (E * SL::S);
+            const int oc = slot / SL::PER_OC, sr = slot % SL::PER_OC;
+            int src = -1;
+            if (sr < G::NCH * NCX) {                    // coarse block of channel cc
+                const int cc = sr / (NCX > 0 ? NCX : 1), dx = sr % (NCX > 0 ? NCX : 1);
+                if (e < NCX) src = cc * G::PC + e * NCX + dx;
+            } else {
+                const int t = sr - G::NCH * NCX;
+                const int cc = t / NFX, dx = t % NFX;
+                if (e < NFX) src = G::NCH * G::PC + cc * G::PF + e * NFX + dx;
+            }
+            TB v = src >= 0 ? bank[((int64_t)k * 3 + oc) * G::D + src] : TB(0.f);
+            reinterpret_cast<TB*>(bank_s + (size_t)k * BSTRIDE + slot * SB)[e] = v;
+        }
+    }
+
+    const int tiles_x = (W + TW - 1) / TW, tiles_y = (H + TH - 1) / TH;
+    const int64_t ntiles = (int64_t)tiles_x * tiles_y * nimg;
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int img = (int)(tile / ((int64_t)tiles_x * tiles_y));
+        const int trem = (int)(tile % ((int64_t)tiles_x * tiles_y));
+        const int x0 = (trem % tiles_x) * TW, y0 = (trem / tiles_x) * TH;
+        const TS* zi = z + (int64_t)img * 3 * H * W;
+        __syncthreads();
+        for (int i = tid; i < 3 * ZH * ZW; i += NT) {
+            int c = i / (ZH * ZW), r = (i / ZW) % ZH, q = i % ZW;
+            int gy = clampi(y0 - HZ + r, 0, H - 1), gx = clampi(x0 - HZ + q, 0, W - 1);
+            zs[i] = ld_f(zi, ((int64_t)c * H + gy) * W + gx);
+        }
+        if constexpr (RC >= 0) {
+            const TS* ci = coarse + (int64_t)img * 3 * Hc * Wc;
+            const int cx0 = x0 / 2 - RC, cy0 = y0 / 2 - RC;
+            for (int i = tid; i < UH * UW; i += NT) {
+                int r = i / UW, q = i % UW;
+                int gy = clampi(cy0 + r, 0, Hc - 1), gx = clampi(cx0 + q, 0, Wc - 1);
+                int64_t o = (int64_t)gy * Wc + gx;
+                float a, b, c;
+                rgb_to_work(ld_f(ci, o), ld_f(ci, o + (int64_t)Hc * Wc), ld_f(ci, o + 2 * (int64_t)Hc * Wc), color,
+                            a, b, c);
+                us[i] = a; us[UH * UW + i] = b; us[2 * UH * UW + i] = c;
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < PH * PW; i += NT) {
+            int r = i / PW, q = i % PW;
+            int cy = clampi(y0 - 2 + r, 0, H - 1), cx = clampi(x0 - 2 + q, 0, W - 1);
+            int ly = cy - (y0 - HZ), lx = cx - (x0 - HZ);
+            int lxm = clampi(cx - 1, 0, W - 1) - (x0 - HZ), lxp = clampi(cx + 1, 0, W - 1) - (x0 - HZ);
+            int lym = clampi(cy - 1, 0, H - 1) - (y0 - HZ), lyp = clampi(cy + 1, 0, H - 1) - (y0 - HZ);
+            float gx[3], gy[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float* zc = zs + c * ZH * ZW;
+                gx[c] = __fmul_rn(__fsub_rn(zc[ly * ZW + lxp], zc[ly * ZW + lxm]), 0.5f);
+                gy[c] = __fmul_rn(__fsub_rn(zc[lyp * ZW + lx], zc[lym * ZW + lx]), 0.5f);
+            }
+            float pxx = __fmul_rn(gx[0], gx[0]), pxy = __fmul_rn(gx[0], gy[0]), pyy = __fmul_rn(gy[0], gy[0]);
+#pragma unroll
+            for (int c = 1; c < 3; ++c) {
+                pxx = __fmaf_rn(gx[c], gx[c], pxx);
+                pxy = __fmaf_rn(gx[c], gy[c], pxy);
+                pyy = __fmaf_rn(gy[c], gy[c], pyy);
+            }
+            ps[i] = pxx; ps[PH * PW + i] = pxy; ps[2 * PH * PW + i] = pyy;
+        }
+        __syncthreads();
+        for (int i = tid; i < 3 * PH * TW; i += NT) {
+            int f = i / (PH * TW), r = (i / TW) % PH, q = i % TW;
+            const float* p = ps + f * PH * PW + r * PW + q;
+            float acc = __fmul_rn(wv[0], p[0]);
+#pragma unroll
+            for (int u = 1; u < 5; ++u) acc = __fmaf_rn(wv[u], p[u], acc);
+            hs[i] = acc;
+        }
+        for (int i = tid; i < ZH * ZW; i += NT) {
+            float a, b, c;
+            rgb_to_work(zs[i], zs[ZH * ZW + i], zs[2 * ZH * ZW + i], color, a, b, c);
+            zs[i] = a; zs[ZH * ZW + i] = b; zs[2 * ZH * ZW + i] = c;
+        }
+        __syncthreads();
+        for (int i = tid; i < TH * TW; i += NT) {
+            int r = i / TW, q = i % TW;
+            float t3[3];
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                const float* p = hs + f * PH * TW + r * TW + q;
+                float acc = __fmul_rn(wv[0], p[0]);
+#pragma unroll
+                for (int v = 1; v < 5; ++v) acc = __fmaf_rn(wv[v], p[v * TW], acc);
+                t3[f] = acc;
+            }
+            int k = bucket_of(t3[0], t3[1], t3[2], sp);
+            k = k < K ? k : K - 1;
+            bk[i] = (uint8_t)k;
+            int gy = y0 + r, gx = x0 + q;
+            if (bmap && gy < H && gx < W) bmap[((int64_t)img * H + gy) * W + gx] = (uint8_t)k;
+        }
+        __syncthreads();
+        // ---- filtering: lane = column, warp = strip of PY rows ----
+        const int q = lane, r0 = warp * PY;
+        const unsigned char* hb[PY];
+#pragma unroll
+        for (int p = 0; p < PY; ++p) hb[p] = bank_s + (size_t)bk[(r0 + p) * TW + q] * BSTRIDE;
+        float o[3][PY];
+#pragma unroll
+        for (int oc = 0; oc < 3; ++oc) {
+            float acc[PY];
+#pragma unroll
+            for (int p = 0; p < PY; ++p) acc[p] = 0.f;
+            int slot = oc * SL::PER_OC;
+            if constexpr (RC >= 0) {
+                constexpr int NCR = PY / 2 + 2 * RC;     // coarse rows touched by the strip
+#pragma unroll
+                for (int cc = 0; cc < G::NCH; ++cc) {
+                    const int c = CROSS ? cc : oc;
+                    const float* ub = us + c * UH * UW + (r0 / 2) * UW + (q / 2) + RC;
+#pragma unroll
+                    for (int dx = -RC; dx <= RC; ++dx, ++slot) {
+                        float col[NCR];
+#pragma unroll
+                        for (int j = 0; j < NCR; ++j) col[j] = ub[j * UW + dx];
+#pragma unroll
+                        for (int p = 0; p < PY; ++p) {
+                            float h[8];
+                            load_slot<TB>(hb[p] + slot * SB, h);
+#pragma unroll
+                            for (int dy = 0; dy < 2 * RC + 1; ++dy) acc[p] = fmaf(h[dy], col[p / 2 + dy], acc[p]);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int cc = 0; cc < G::NCH; ++cc) {
+                const int c = CROSS ? cc : oc;
+                const float* zb = zs + c * ZH * ZW + (r0 + HZ - RF) * ZW + q + HZ;
+#pragma unroll
+                for (int dx = -RF; dx <= RF; ++dx, ++slot) {
+                    float col[PY + 2 * RF];
+#pragma unroll
+                    for (int j = 0; j < PY + 2 * RF; ++j) col[j] = zb[j * ZW + dx];
+#pragma unroll
+                    for (int p = 0; p < PY; ++p) {
+                        float h[8];
+                        load_slot<TB>(hb[p] + slot * SB, h);
+#pragma unroll
+                        for (int dy = 0; dy < 2 * RF + 1; ++dy) acc[p] = fmaf(h[dy], col[p + dy], acc[p]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < PY; ++p) o[oc][p] = acc[p];
+        }
+        TS* oi = out + (int64_t)img * 3 * H * W;
+        const int gx = x0 + q;
+#pragma unroll
+        for (int p = 0; p < PY; ++p) {
+            const int gy = y0 + r0 + p;
+            if (gy < H && gx < W) {
+                float R, Gc, B;
+                work_to_rgb(o[0][p], o[1][p], o[2][p], color, R, Gc, B);
+                int64_t po = (int64_t)gy * W + gx;
+                st_f(oi, po, R);
+                st_f(oi, (int64_t)H * W + po, Gc);
+                st_f(oi, 2 * (int64_t)H * W + po, B);
+            }
+        }
+    }
+}
+
+template <int RF, int RC, bool CROSS, typename TS, typename TB>
+int run2(const LevelArgs& a, cudaStream_t s) {
+    auto kern = k_level2<RF, RC, CROSS, TS, TB>;
+    const size_t bytes = smem_need<RF, RC, CROSS, TB>(a.K);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "k_level2: set smem attribute");
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "k_level2: occupancy");
+    if (occ < 1) return fail(MDN_ESHAPE, "k_level2: shared memory footprint too large");
+    const int64_t tiles = ((a.w + TW - 1) / TW) * ((a.h + TH - 1) / TH) * a.n;
+    int64_t grid = (int64_t)num_sms() * occ;
+    if (grid > tiles) grid = tiles;
+    float w[5];
+    gauss5_weights(w);
+    kern<<<(unsigned)grid, NT, bytes, s>>>((const TS*)a.z, (const TS*)a.coarse, (TS*)a.out, a.buckets,
+                                           (const TB*)a.bank, (int)a.h, (int)a.w, (int)a.hc, (int)a.wc,
+                                           (int)a.n, a.K, a.geom.color, a.sel, w[0], w[1], w[2]);
+    return check_launch("k_level2");
+}
+
+}  // namespace v2
+
+// ==========================================================================
+// Warp-specialised variant (v3).  Producer warps (4) stage tile t+1 (global
+// loads, tensor, features, buckets, RGB -> working space) into one of two
+// shared-memory stages while consumer warps (8) filter tile t from the other
+// stage, exactly as in v2.  Hand-off uses named barriers:
+//   FULL[s]  : producers bar.arrive, consumers bar.sync   (128 + 256 threads)
+//   EMPTY[s] : consumers bar.arrive, producers bar.sync   (256 + 128 threads)
+//   PROD     : producer-internal bar.sync (128 threads)
+// Every CTA computes the same tile count T for both roles; producers wait on
+// EMPTY[i%2] only for i >= 2 and consumers arrive on EMPTY[i%2] only when
+// i + 2 < T, so every barrier generation receives exactly 384 threads and
+// generations are ordered (a consumer reaches tile i's arrival only after
+// tile i's FULL, which follows the producer's EMPTY wait for tile i).
+// ==========================================================================
+namespace v3 {
+
+constexpr int TW = 32, TH = 32, PY = 4;
+constexpr int NCW = 8, NPW = 8;                 // consumer / producer warps
+constexpr int NC = NCW * 32, NP = NPW * 32, NT = NC + NP;
+constexpr int HZ = 3;
+constexpr int ZW = TW + 2 * HZ, ZH = TH + 2 * HZ;
+constexpr int PW = TW + 4, PH = TH + 4;
+static_assert(NCW * PY == TH, "consumer strips must cover the tile");
+
+enum { BAR_FULL0 = 1, BAR_EMPTY0 = 3, BAR_PROD = 5 };
+
+__device__ __forceinline__ void bar_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+__device__ __forceinline__ void bar_arrive(int id, int n) { asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+
+template <int RC> struct Coarse {
+    static constexpr int UW = RC >= 0 ? TW / 2 + 2 * RC : 0;
+    static constexpr int UH = RC >= 0 ? TH / 2 + 2 * RC : 0;
+};
+
+template <int RC> constexpr size_t stage_bytes() {
+    return sizeof(float) * (3 * ZH * ZW + 3 * Coarse<RC>::UH * Coarse<RC>::UW) + TH * TW;
+}
+constexpr size_t scratch_bytes() { return sizeof(float) * (3 * PH * PW + 3 * PH * TW); }
+template <int RC> constexpr size_t front_bytes() {
+    return ((2 * stage_bytes<RC>() + scratch_bytes()) + 15) & ~size_t(15);
+}
+template <int RF, int RC, bool CROSS, typename TB> size_t smem_need(int K) {
+    return front_bytes<RC>() + (size_t)K * v2::bucket_units<RF, RC, CROSS, TB>() * 16;
+}
+
+template <int RF, int RC, bool CROSS, typename TS, typename TB>
+__global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, const TS* __restrict__ coarse,
+                                                  TS* __restrict__ out, uint8_t* __restrict__ bmap,
+                                                  const TB* __restrict__ bank, int H, int W, int Hc, int Wc,
+                                                  int nimg, int K, int color, SelParams sp, float w0, float w1,
+                                                  float w2) {
+    using G = Geo<RF, RC, CROSS>;
+    using SL = v2::Slots<RF, RC, CROSS>;
+    constexpr int UW = Coarse<RC>::UW, UH = Coarse<RC>::UH;
+    constexpr int SB = v2::SlotBytes<TB>::B;
+    constexpr int BSTRIDE = v2::bucket_units<RF, RC, CROSS, TB>() * 16;
+    constexpr int NCX = RC >= 0 ? 2 * RC + 1 : 0;
+    constexpr int NFX = 2 * RF + 1;
+    constexpr size_t SBY = stage_bytes<RC>();
+    extern __shared__ __align__(16) unsigned char smem[];
+    float* ps = reinterpret_cast<float*>(smem + 2 * SBY);   // producer scratch [3][PH][PW]
+    float* hs = ps + 3 * PH * PW;                             // [3][PH][TW]
+    unsigned char* bank_s = smem + front_bytes<RC>();
+    const int tid = threadIdx.x;
+
+    {   // bank -> slots, all threads, once per persistent CTA
+        constexpr int E = SB / (int)sizeof(TB);
+        const int total = K * SL::S * E;
+        for (int i = tid; i < total; i += NT) {
+            const int e = i % E, slot = (i / E) % SL::S, k = i / (E * SL::S);
+            const int oc = slot / SL::PER_OC, sr = slot % SL::PER_OC;
+            int src = -1;
+            if (sr < G::NCH * NCX) {
+                const int cc = sr / (NCX > 0 ? NCX : 1), dx = sr % (NCX > 0 ? NCX : 1);
+                if (e < NCX) src = cc * G::PC + e * NCX + dx;
+            } else {
+                const int t = sr - G::NCH * NCX;
+                const int cc = t / NFX, dx = t % NFX;
+                if (e < NFX) src = G::NCH * G::PC + cc * G::PF + e * NFX + dx;
+            }
+            TB v = src >= 0 ? bank[((int64_t)k * 3 + oc) * G::D + src] : TB(0.f);
+            reinterpret_cast<TB*>(bank_s + (size_t)k * BSTRIDE + slot * SB)[e] = v;
+        }
+    }
+    __syncthreads();
+
+    const int tiles_x = (W + TW - 1) / TW, tiles_y = (H + TH - 1) / TH;
+    const int64_t ntiles = (int64_t)tiles_x * tiles_y * nimg;
+    const int64_t T = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int warp = tid >> 5, lane = tid & 31;
+
+    if (warp >= NCW) {
+        // =============================== producer ===============================
+        const int pt = tid - NC;
+        const float wv[5] = {w0, w1, w2, w1, w0};
+        // Register prefetch: the inputs of tile i+1 are loaded while tile i's
+        // selector runs, so global latency overlaps shared-memory work.
+        constexpr int NZ = (3 * ZH * ZW + NP - 1) / NP;
+        constexpr int NU = RC >= 0 ? (UH * UW + NP - 1) / NP : 0;
+        float zreg[NZ];
+        float ureg[NU > 0 ? NU : 1][3];
+        auto fetch = [&](int64_t tile) {
+            const int img = (int)(tile / ((int64_t)tiles_x * tiles_y));
+            const int trem = (int)(tile % ((int64_t)tiles_x * tiles_y));
+            const int x0 = (trem % tiles_x) * TW, y0 = (trem / tiles_x) * TH;
+            const TS* zi = z + (int64_t)img * 3 * H * W;
+#pragma unroll
+            for (int j = 0; j < NZ; ++j) {
+                const int e = pt + j * NP;
+                if (e < 3 * ZH * ZW) {
+                    int c = e / (ZH * ZW), r = (e / ZW) % ZH, q = e % ZW;
+                    int gy = clampi(y0 - HZ + r, 0, H - 1), gx = clampi(x0 - HZ + q, 0, W - 1);
+                    zreg[j] = ld_f(zi, ((int64_t)c * H + gy) * W + gx);
+                }
+            }
+            if constexpr (RC >= 0) {
+                const TS* ci = coarse + (int64_t)img * 3 * Hc * Wc;
+                const int cx0 = x0 / 2 - RC, cy0 = y0 / 2 - RC;
+#pragma unroll
+                for (int j = 0; j < NU; ++j) {
+                    const int e = pt + j * NP;
+                    if (e < UH * UW) {
+                        int r = e / UW, q = e % UW;
+                        int gy = clampi(cy0 + r, 0, Hc - 1), gx = clampi(cx0 + q, 0, Wc - 1);
+                        int64_t o = (int64_t)gy * Wc + gx;
+                        ureg[j][0] = ld_f(ci, o);
+                        ureg[j][1] = ld_f(ci, o + (int64_t)Hc * Wc);
+                        ureg[j][2] = ld_f(ci, o + 2 * (int64_t)Hc * Wc);
+                    }
+                }
+            }
+        };
+        if (T > 0) fetch(blockIdx.x);
+        for (int64_t i = 0; i < T; ++i) {
+            const int s = (int)(i & 1);
+            if (i >= 2) bar_sync(BAR_EMPTY0 + s, NT);
+            float* zs = reinterpret_cast<float*>(smem + s * SBY);
+            float* us = zs + 3 * ZH * ZW;
+            uint8_t* bk = reinterpret_cast<uint8_t*>(us + 3 * UH * UW);
+            const int64_t tile = blockIdx.x + i * gridDim.x;
+            const int img = (int)(tile / ((int64_t)tiles_x * tiles_y));
+            const int trem = (int)(tile % ((int64_t)tiles_x * tiles_y));
+            const int x0 = (trem % tiles_x) * TW, y0 = (trem / tiles_x) * TH;
+#pragma unroll
+            for (int j = 0; j < NZ; ++j) {
+                const int e = pt + j * NP;
+                if (e < 3 * ZH * ZW) zs[e] = zreg[j];
+            }
+            if constexpr (RC >= 0) {
+#pragma unroll
+                for (int j = 0; j < NU; ++j) {
+                    const int e = pt + j * NP;
+                    if (e < UH * UW) {
+                        float a, b, c;
+                        rgb_to_work(ureg[j][0], ureg[j][1], ureg[j][2], color, a, b, c);
+                        us[e] = a; us[UH * UW + e] = b; us[2 * UH * UW + e] = c;
+                    }
+                }
+            }
+            if (i + 1 < T) fetch(tile + gridDim.x);
+            bar_sync(BAR_PROD, NP);
+            for (int e = pt; e < PH * PW; e += NP) {
+                int r = e / PW, q = e % PW;
+                int cy = clampi(y0 - 2 + r, 0, H - 1), cx = clampi(x0 - 2 + q, 0, W - 1);
+                int ly = cy - (y0 - HZ), lx = cx - (x0 - HZ);
+                int lxm = clampi(cx - 1, 0, W - 1) - (x0 - HZ), lxp = clampi(cx + 1, 0, W - 1) - (x0 - HZ);
+                int lym = clampi(cy - 1, 0, H - 1) - (y0 - HZ), lyp = clampi(cy + 1, 0, H - 1) - (y0 - HZ);
+                float gx[3], gy[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float* zc = zs + c * ZH * ZW;
+                    gx[c] = __fmul_rn(__fsub_rn(zc[ly * ZW + lxp], zc[ly * ZW + lxm]), 0.5f);
+                    gy[c] = __fmul_rn(__fsub_rn(zc[lyp * ZW + lx], zc[lym * ZW + lx]), 0.5f);
+                }
+                float pxx = __fmul_rn(gx[0], gx[0]), pxy = __fmul_rn(gx[0], gy[0]), pyy = __fmul_rn(gy[0], gy[0]);
+#pragma unroll
+                for (int c = 1; c < 3; ++c) {
+                    pxx = __fmaf_rn(gx[c], gx[c], pxx);
+                    pxy = __fmaf_rn(gx[c], gy[c], pxy);
+                    pyy = __fmaf_rn(gy[c], gy[c], pyy);
+                }
+                ps[e] = pxx; ps[PH * PW + e] = pxy; ps[2 * PH * PW + e] = pyy;
+            }
+            bar_sync(BAR_PROD, NP);
+            for (int e = pt; e < 3 * PH * TW; e += NP) {
+                int f = e / (PH * TW), r = (e / TW) % PH, q = e % TW;
+                const float* p = ps + f * PH * PW + r * PW + q;
+                float acc = __fmul_rn(wv[0], p[0]);
+#pragma unroll
+                for (int u = 1; u < 5; ++u) acc = __fmaf_rn(wv[u], p[u], acc);
+                hs[e] = acc;
+            }
+            for (int e = pt; e < ZH * ZW; e += NP) {
+                float a, b, c;
+                rgb_to_work(zs[e], zs[ZH * ZW + e], zs[2 * ZH * ZW + e], color, a, b, c);
+                zs[e] = a; zs[ZH * ZW + e] = b; zs[2 * ZH * ZW + e] = c;
+            }
+            bar_sync(BAR_PROD, NP);
+            for (int e = pt; e < TH * TW; e += NP) {
+                int r = e / TW, q = e % TW;
+                float t3[3];
+#pragma unroll
+                for (int f = 0; f < 3; ++f) {
+                    const float* p = hs + f * PH * TW + r * TW + q;
+                    float acc = __fmul_rn(wv[0], p[0]);
+#pragma unroll
+                    for (int v = 1; v < 5; ++v) acc = __fmaf_rn(wv[v], p[v * TW], acc);
+                    t3[f] = acc;
+                }
+                int k = bucket_of(t3[0], t3[1], t3[2], sp);
+                k = k < K ? k : K - 1;
+                bk[e] = (uint8_t)k;
+                int gy = y0 + r, gx = x0 + q;
+                if (bmap && gy < H && gx < W) bmap[((int64_t)img * H + gy) * W + gx] = (uint8_t)k;
+            }
+            bar_arrive(BAR_FULL0 + s, NT);
+        }
+    } else {
+        // =============================== consumer ===============================
+        const int q = lane, r0 = warp * PY;
+        for (int64_t i = 0; i < T; ++i) {
+            const int s = (int)(i & 1);
+            bar_sync(BAR_FULL0 + s, NT);
+            const float* zs = reinterpret_cast<const float*>(smem + s * SBY);
+            const float* us = zs + 3 * ZH * ZW;
+            const uint8_t* bk = reinterpret_cast<const uint8_t*>(us + 3 * UH * UW);
+            const int64_t tile = blockIdx.x + i * gridDim.x;
+            const int img = (int)(tile / ((int64_t)tiles_x * tiles_y));
+            const int trem = (int)(tile % ((int64_t)tiles_x * tiles_y));
+            const int x0 = (trem % tiles_x) * TW, y0 = (trem / tiles_x) * TH;
+            const unsigned char* hb[PY];
+#pragma unroll
+            for (int p = 0; p < PY; ++p) hb[p] = bank_s + (size_t)bk[(r0 + p) * TW + q] * BSTRIDE;
+            float o[3][PY];
+#pragma unroll
+            for (int oc = 0; oc < 3; ++oc) {
+                float acc[PY];
+#pragma unroll
+                for (int p = 0; p < PY; ++p) acc[p] = 0.f;
+                int slot = oc * SL::PER_OC;
+                if constexpr (RC >= 0) {
+                    constexpr int NCR = PY / 2 + 2 * RC;
+#pragma unroll
+                    for (int cc = 0; cc < G::NCH; ++cc) {
+                        const int c = CROSS ? cc : oc;
+                        const float* ub = us + c * UH * UW + (r0 / 2) * UW + (q / 2) + RC;
+#pragma unroll
+                        for (int dx = -RC; dx <= RC; ++dx, ++slot) {
+                            float col[NCR];
+#pragma unroll
+                            for (int j = 0; j < NCR; ++j) col[j] = ub[j * UW + dx];
+#pragma unroll
+                            for (int p = 0; p < PY; ++p) {
+                                float h[8];
+                                v2::load_slot<TB>(hb[p] + slot * SB, h);
+#pragma unroll
+                                for (int dy = 0; dy < 2 * RC + 1; ++dy) acc[p] = fmaf(h[dy], col[p / 2 + dy], acc[p]);
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int cc = 0; cc < G::NCH; ++cc) {
+                    const int c = CROSS ? cc : oc;
+                    const float* zb = zs + c * ZH * ZW + (r0 + HZ - RF) * ZW + q + HZ;
+#pragma unroll
+                    for (int dx = -RF; dx <= RF; ++dx, ++slot) {
+                        float col[PY + 2 * RF];
+#pragma unroll
+                        for (int j = 0; j < PY + 2 * RF; ++j) col[j] = zb[j * ZW + dx];
+#pragma unroll
+                        for (int p = 0; p < PY; ++p) {
+                            float h[8];
+                            v2::load_slot<TB>(hb[p] + slot * SB, h);
+#pragma unroll
+                            for (int dy = 0; dy < 2 * RF + 1; ++dy) acc[p] = fmaf(h[dy], col[p + dy], acc[p]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int p = 0; p < PY; ++p) o[oc][p] = acc[p];
+            }
+            // stage s is no longer read: hand it back (only if the producer will reuse it)
+            if (i + 2 < T) bar_arrive(BAR_EMPTY0 + s, NT);
+            TS* oi = out + (int64_t)img * 3 * H * W;
+            const int gx = x0 + q;
+#pragma unroll
+            for (int p = 0; p < PY; ++p) {
+                const int gy = y0 + r0 + p;
+                if (gy < H && gx < W) {
+                    float R, Gc, B;
+                    work_to_rgb(o[0][p], o[1][p], o[2][p], color, R, Gc, B);
+                    int64_t po = (int64_t)gy * W + gx;
+                    st_f(oi, po, R);
+                    st_f(oi, (int64_t)H * W + po, Gc);
+                    st_f(oi, 2 * (int64_t)H * W + po, B);
+                }
+            }
+        }
+    }
+}
+
+template <int RF, int RC, bool CROSS, typename TS, typename TB>
+int run3(const LevelArgs& a, cudaStream_t s) {
+    auto kern = k_level3<RF, RC, CROSS, TS, TB>;
+    const size_t bytes = smem_need<RF, RC, CROSS, TB>(a.K);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "k_level3: set smem attribute");
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "k_level3: occupancy");
+    if (occ < 1) return fail(MDN_ESHAPE, "k_level3: shared memory footprint too large");
+    const int64_t tiles = ((a.w + TW - 1) / TW) * ((a.h + TH - 1) / TH) * a.n;
+    int64_t grid = (int64_t)num_sms() * occ;
+    if (grid > tiles) grid = tiles;
+    float w[5];
+    gauss5_weights(w);
+    kern<<<(unsigned)grid, NT, bytes, s>>>((const TS*)a.z, (const TS*)a.coarse, (TS*)a.out, a.buckets,
+                                           (const TB*)a.bank, (int)a.h, (int)a.w, (int)a.hc, (int)a.wc,
+                                           (int)a.n, a.K, a.geom.color, a.sel, w[0], w[1], w[2]);
+    return check_launch("k_level3");
+}
+
+}  // namespace v3
+
+
+#ifndef MDN_USE_V3
+#define MDN_USE_V3 1
+#endif
+
 // Geometry dispatch for one (storage, bank) type pair.
 template <typename TS, typename TB> int dispatch(const LevelArgs& a, cudaStream_t s) {
     const mdn_geometry& g = a.geom;
 #define MDN_GEO(RF_, RC_, CR_)                                                                  \
     if (g.r_fine == RF_ && g.r_coarse == RC_ && (g.cross_channel != 0) == CR_) {                \
+        if (MDN_USE_V3 && v3::smem_need<RF_, RC_, CR_, TB>(a.K) <= SMEM_LIMIT)                \
+            return v3::run3<RF_, RC_, CR_, TS, TB>(a, s);                                      \
+        if (v2::smem_need<RF_, RC_, CR_, TB>(a.K) <= SMEM_LIMIT)                              \
+            return v2::run2<RF_, RC_, CR_, TS, TB>(a, s);                                      \
         if (smem_need<RF_, RC_, CR_, TB>(a.K) <= SMEM_LIMIT)                                  \
             return run<RF_, RC_, CR_, TS, TB, true, true>(a, s);                              \
         return run<RF_, RC_, CR_, TS, TB, false, true>(a, s);                                 \
