@@ -216,6 +216,12 @@ int mdn_train_level_filters(const void* noisy_lvl, const void* coarse_out, const
                             int64_t* counts, double lambda, float* bank_out, void* ws,
                             size_t ws_bytes, void* stream);
 
+/* Reads and clears the device-side error flag of the tensor-core Gram
+ * kernels (synchronous, host pointer): *flag = 1 if a bounded wait inside a
+ * Gram kernel expired since the last call (its partial sums were not
+ * written and the result must be discarded), else 0. */
+int mdn_train_status(int32_t* flag);
+
 /* Ridge solve per bucket and group in FP64 on the GPU:
  * h = (G_xx / n_k + lambda I)^{-1} (G_xy / n_k) by Cholesky; buckets with
  * n_k = 0 take the pooled filter solved from sum_k G_k.  bank_out: FP32

@@ -16,7 +16,7 @@ from .build import LIB as _LIB_PATH, build
 __all__ = ["build", "lib", "Geometry", "BucketParams", "default_bparams", "MdnError",
            "build_pyramid", "select_buckets", "filter_level", "denoise_multiscale",
            "denoise_workspace_bytes", "train_level_filters", "solve_bank", "regressor_len",
-           "gram_state_shape", "F32", "F16", "YCBCR601", "RGB", "GRAM_FP32", "GRAM_TF32",
+           "gram_state_shape", "train_status", "F32", "F16", "YCBCR601", "RGB", "GRAM_FP32", "GRAM_TF32",
            "GRAM_BF16", "GRAM_SPLIT_BF16"]
 
 F32, F16 = 0, 1
@@ -97,6 +97,7 @@ def lib():
             "mdn_train_level_filters": (C.c_int, [vp, vp, vp, i32, i64, i64, i64, G, B, i32, i32, vp, vp,
                                                   C.c_double, vp, vp, sz, vp]),
             "mdn_solve_workspace_bytes": (sz, [G, i32]),
+            "mdn_train_status": (C.c_int, [C.POINTER(C.c_int32)]),
             "mdn_solve_bank": (C.c_int, [vp, vp, G, i32, C.c_double, vp, vp, vp, sz, vp]),
         }
         for name, (res, args) in sig.items():
@@ -264,6 +265,13 @@ def train_level_filters(noisy_lvl, coarse_out, clean_lvl, geom: Geometry, bp: Bu
                                          _dev(bank, "bank") if bank is not None else None, _dev(ws, "ws"),
                                          ws.numel(), _stream(stream)))
     return gram, counts, bank
+
+
+def train_status() -> int:
+    """Reads and clears the tensor-core Gram error flag (1 = a bounded wait expired)."""
+    v = C.c_int32(0)
+    _check(lib().mdn_train_status(C.byref(v)))
+    return v.value
 
 
 def solve_bank(gram, counts, geom: Geometry, lam: float = 1e-3, stream=None):

@@ -8,6 +8,7 @@
 #include <string>
 
 #include "internal.h"
+#include "train_common.cuh"
 
 namespace mdn {
 
@@ -345,6 +346,15 @@ int mdn_solve_bank(const double* gram, const int64_t* counts, const mdn_geometry
     int G = geom->cross_channel ? 1 : 3, T = geom->cross_channel ? 3 : 1;
     if (ws_bytes < solve_ws_bytes(K, G, D, T) || !ws) return fail(MDN_EWORKSPACE, "solve_bank: workspace too small");
     return launch_solve(gram, counts, K, G, D, T, lambda, bank_out, status_out, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int mdn_train_status(int32_t* flag) {
+    if (!flag) return fail(MDN_EINVAL, "train_status: null");
+    int v = 0;
+    int rc = gram_tc_error(&v);
+    if (rc) return rc;
+    *flag = v;
+    return MDN_OK;
 }
 
 }  // extern "C"

@@ -6,11 +6,12 @@
 //   k_scan         bucket-major exclusive scan -> stable scatter offsets and
 //                  the chunk table (bucket, begin, end), chunks <= CHUNK rows
 //   k_scatter      stable counting-sort scatter of pixel indices by bucket
-//   Gram           per chunk: A^T A of the gathered rows A = [regressor|target]
-//                  (SIMT FP32 here, tcgen05 variants in k_gram_tc.cu),
-//                  written as FP32 partials
-//   k_reduce       FP64 sum of a bucket's partials in chunk order (determin-
-//                  istic), added into gram[k][g]; counts[k] += n_k
+//   Gram           per chunk: A^T A of the gathered rows A = [regressor|target
+//                  shifted by a per-channel constant | 1] (SIMT FP32 here,
+//                  tcgen05 variants in k_gram_tc.cu), written as FP32 partials
+//   k_reduce_centered  FP64 sum of a bucket's partials in chunk order
+//                  (deterministic) with the exact centring correction, added
+//                  into gram[k][g]; counts[k] += n_k
 //   k_pool/k_chol  ridge solve (G_xx/n + lambda I) h = G_xy/n by Cholesky in
 //                  FP64 shared memory, one CTA per (bucket, group); empty
 //                  buckets copy the pooled solution
@@ -138,11 +139,11 @@ __global__ void __launch_bounds__(256) k_gram_simt(GatherArgs ga, const int4* __
     extern __shared__ __align__(16) unsigned char smem[];
     const int4 ch = chunks[blockIdx.x];
     if (ch.x < 0) return;
-    const int Dp = ga.Dp, G = ga.G, DPs = ga.Dp4;   // Dp4: row stride, multiple of 4
+    const int Dq = ga.Dp + 1, G = ga.G, DPs = ga.Dp4;   // Dq: features + ones column
     float* As = reinterpret_cast<float*>(smem);        // [G][RB][DPs]
-    int* coltab = reinterpret_cast<int*>(As + (size_t)G * GRAM_RB * DPs);   // [G][Dp]
+    int* coltab = reinterpret_cast<int*>(As + (size_t)G * GRAM_RB * DPs);   // [G][Dq]
     build_coltab(ga, coltab);
-    const int nb = (Dp + 3) / 4;
+    const int nb = (Dq + 3) / 4;
     const int nblk_g = nb * (nb + 1) / 2;
     const int total = G * nblk_g;
     constexpr int MB = 8;   // max blocks per thread
@@ -185,26 +186,29 @@ __global__ void __launch_bounds__(256) k_gram_simt(GatherArgs ga, const int4* __
             }
         }
     }
-    float* out = partial + (size_t)blockIdx.x * G * Dp * Dp;
+    float* out = partial + (size_t)blockIdx.x * G * Dq * Dq;
 #pragma unroll
     for (int m = 0; m < MB; ++m) {
         if (bg[m] < 0) continue;
         for (int p = 0; p < 4; ++p)
             for (int q = 0; q < 4; ++q) {
                 int i = bi[m] * 4 + p, j = bj[m] * 4 + q;
-                if (i < Dp && j < Dp && i <= j) out[((size_t)bg[m] * Dp + i) * Dp + j] = acc[m][p * 4 + q];
+                if (i < Dq && j < Dq && i <= j) out[((size_t)bg[m] * Dq + i) * Dq + j] = acc[m][p * 4 + q];
             }
     }
 }
 
-// FP64 reduction of a bucket's chunk partials (upper triangle), in chunk
-// order; result added into gram and mirrored to the lower triangle.
-__global__ void k_reduce(const float* __restrict__ partial, const int4* __restrict__ chunks,
-                         const int* __restrict__ nchunks, const int64_t* __restrict__ bcount, int K, int G, int Dp,
-                         double* __restrict__ gram, int64_t* __restrict__ counts) {
+// FP64 reduction of a bucket's chunk partials in chunk order (deterministic):
+// partials are (Dq = Dp + 1)^2 upper triangles of the shifted rows with the
+// ones column last; the exact centring correction is
+// G_ij = S_ij + c_i s_j + c_j s_i + n c_i c_j, s_i = S_{i,ones}, n = S_{ones,ones}.
+__global__ void k_reduce_centered(const float* __restrict__ partial, const int4* __restrict__ chunks,
+                                  const int* __restrict__ nchunks, const int64_t* __restrict__ bcount, int K, int G,
+                                  int Dp, int D, int rf, int rc, int cross, int color, double* __restrict__ gram,
+                                  int64_t* __restrict__ counts) {
     const int k = blockIdx.y;
-    const int64_t ent = (int64_t)G * Dp * Dp;
-    // chunk range of bucket k: chunks are ordered by bucket
+    const int Dq = Dp + 1;
+    const int64_t entq = (int64_t)G * Dq * Dq;
     __shared__ int c0, c1;
     if (threadIdx.x == 0) {
         int nc = *nchunks, lo = 0, hi = nc;
@@ -215,15 +219,26 @@ __global__ void k_reduce(const float* __restrict__ partial, const int4* __restri
         c1 = lo;
     }
     __syncthreads();
+    const int64_t ent = (int64_t)G * Dp * Dp;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ent; e += (int64_t)gridDim.x * blockDim.x) {
-        int g = (int)(e / ((int64_t)Dp * Dp));
-        int i = (int)((e / Dp) % Dp), j = (int)(e % Dp);
+        const int g = (int)(e / ((int64_t)Dp * Dp));
+        const int i = (int)((e / Dp) % Dp), j = (int)(e % Dp);
         if (i > j) continue;
-        double s = 0.0;
-        for (int c = c0; c < c1; ++c) s += (double)partial[(size_t)c * ent + e];
+        double sij = 0.0, si = 0.0, sj = 0.0, n = 0.0;
+        const size_t base = (size_t)g * Dq * Dq;
+        for (int c = c0; c < c1; ++c) {
+            const float* P = partial + (size_t)c * entq + base;
+            sij += (double)P[(size_t)i * Dq + j];
+            si += (double)P[(size_t)i * Dq + Dp];
+            sj += (double)P[(size_t)j * Dq + Dp];
+            n += (double)P[(size_t)Dp * Dq + Dp];
+        }
+        const double ci = channel_center(feature_channel(i, g, D, rf, rc, cross), color);
+        const double cj = channel_center(feature_channel(j, g, D, rf, rc, cross), color);
+        const double v = sij + ci * sj + cj * si + n * ci * cj;
         double* G0 = gram + (size_t)k * ent + (size_t)g * Dp * Dp;
-        G0[(size_t)i * Dp + j] += s;
-        if (i != j) G0[(size_t)j * Dp + i] += s;
+        G0[(size_t)i * Dp + j] += v;
+        if (i != j) G0[(size_t)j * Dp + i] += v;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) counts[k] += bcount[k];
 }
@@ -355,14 +370,14 @@ size_t train_ws_bytes(int64_t npix, int K, int G, int Dp, int precision) {
     b += align256(sizeof(int64_t) * K) * 2;           // bstart, bcount
     b += align256(sizeof(int4) * maxch) + 256;        // chunks, nchunks
     b += align256(sizeof(int) * (npix > 0 ? npix : 1));   // sorted
-    b += align256(sizeof(float) * maxch * G * Dp * Dp);  // partials
+    b += align256(sizeof(float) * maxch * G * (Dp + 1) * (Dp + 1));  // partials (tensor-core layout is Dp+1)
     return b;
 }
 
 int launch_gram(const TrainArgs& a, cudaStream_t s) {
     const int64_t hw = a.h * a.w, npix = a.n * hw;
     const int64_t hwc = a.hc * a.wc;
-    if (a.Dp > GRAM_MAX_DP) return fail(MDN_ESHAPE, "train: regressor too long (D + T must be <= 160)");
+    if (a.Dp + 1 > GRAM_MAX_DP) return fail(MDN_ESHAPE, "train: regressor too long (D + T must be <= 159)");
     // carve the workspace
     char* p = (char*)a.ws;
     auto take = [&](size_t bytes) { char* r = p; p += align256(bytes); return r; };
@@ -378,7 +393,7 @@ int launch_gram(const TrainArgs& a, cudaStream_t s) {
     int4* chunks = (int4*)take(sizeof(int4) * maxch);
     int* nchunks = (int*)take(sizeof(int));
     int* sorted = (int*)take(sizeof(int) * (npix > 0 ? npix : 1));
-    float* partial = (float*)take(sizeof(float) * maxch * a.G * a.Dp * a.Dp);
+    float* partial = (float*)take(sizeof(float) * maxch * a.G * (a.Dp + 1) * (a.Dp + 1));
     if ((size_t)(p - (char*)a.ws) > a.ws_bytes) return fail(MDN_EWORKSPACE, "train: workspace too small");
 
     const int TB = 256;
@@ -399,11 +414,11 @@ int launch_gram(const TrainArgs& a, cudaStream_t s) {
     GatherArgs ga{};
     ga.zw = zw; ga.tw = tw; ga.cw = a.coarse ? cw : nullptr;
     ga.h = (int)a.h; ga.w = (int)a.w; ga.hc = (int)a.hc; ga.wc = (int)a.wc;
-    ga.rf = a.geom.r_fine; ga.rc = a.geom.r_coarse; ga.cross = a.geom.cross_channel;
-    ga.D = a.D; ga.T = a.T; ga.G = a.G; ga.Dp = a.Dp; ga.Dp4 = (a.Dp + 3) / 4 * 4;
+    ga.rf = a.geom.r_fine; ga.rc = a.geom.r_coarse; ga.cross = a.geom.cross_channel; ga.color = a.geom.color;
+    ga.D = a.D; ga.T = a.T; ga.G = a.G; ga.Dp = a.Dp; ga.Dp4 = (a.Dp + 1 + 3) / 4 * 4;
     if (a.precision == MDN_GRAM_FP32) {
-        size_t sm = sizeof(float) * (size_t)a.G * GRAM_RB * ga.Dp4 + sizeof(int) * a.G * a.Dp;
-        const int nb = (a.Dp + 3) / 4;
+        size_t sm = sizeof(float) * (size_t)a.G * GRAM_RB * ga.Dp4 + sizeof(int) * a.G * (a.Dp + 1);
+        const int nb = (a.Dp + 1 + 3) / 4;
         if (a.G * nb * (nb + 1) / 2 > 8 * 256) return fail(MDN_ESHAPE, "train: Gram too large for the SIMT path");
         cudaError_t ea = cudaFuncSetAttribute(k_gram_simt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (ea != cudaSuccess) return cuda_fail(ea, "k_gram_simt: shared memory attribute");
@@ -414,8 +429,9 @@ int launch_gram(const TrainArgs& a, cudaStream_t s) {
         if (rc) return rc;
     }
     dim3 rg((unsigned)((a.G * a.Dp * a.Dp + 255) / 256), (unsigned)a.K);
-    k_reduce<<<rg, 256, 0, s>>>(partial, chunks, nchunks, bcount, a.K, a.G, a.Dp, a.gram, a.counts);
-    return check_launch("k_reduce");
+    k_reduce_centered<<<rg, 256, 0, s>>>(partial, chunks, nchunks, bcount, a.K, a.G, a.Dp, a.D, a.geom.r_fine,
+                                         a.geom.r_coarse, a.geom.cross_channel, a.geom.color, a.gram, a.counts);
+    return check_launch("k_reduce_centered");
 }
 
 size_t solve_ws_bytes(int K, int G, int D, int T) {

@@ -232,32 +232,65 @@ def test_empty_and_degenerate_inputs(mdn):
 
 # ------------------------------------------------------------ A5/A6 training
 
-@pytest.mark.parametrize("case", [("cfg1", O.Geometry(2, -1), (128, 128), 2),
-                                  ("cfg2", O.Geometry(3, 3), (96, 80), 2),
-                                  ("cfg3", O.Geometry(3, -1, cross=1), (96, 96), 2)], ids=lambda c: c[0])
-def test_train_level_gram_and_bank(mdn, case):
-    _, geom, (h, w), n = case
-    pairs = [synth.noisy_pair(h, w, 30000 + i) for i in range(n)]
+GRAM_TOL = {0: 1e-6, 1: 3e-5, 2: 2e-4, 3: 1e-5}       # relative Frobenius error of the Gram sums
+BANK_TOL = {0: 1e-3, 1: 1e-3, 2: 1e-2, 3: 1e-3}       # BF16 alone cannot meet 1e-3 (split-BF16 can)
+PREC_IDS = {0: "fp32", 1: "tf32", 2: "bf16", 3: "split_bf16"}
+
+
+def _oracle_training_set(geom, n, h, w, seed):
+    pairs = [synth.noisy_pair(h, w, seed + i) for i in range(n)]
     bp_o = O.default_bparams(0)
     gram = counts = None
     zb, ub, cb = [], [], []
     for z, u in pairs:
-        uc = synth.clean_image((h + 1) // 2, (w + 1) // 2, 31000) if geom.r_coarse >= 0 else None
+        uc = synth.clean_image((h + 1) // 2, (w + 1) // 2, seed + 1000) if geom.r_coarse >= 0 else None
         b, _, _ = O.select(z, bp_o, mirror32=True)
         gram, counts = O.gram_accumulate(z, uc, u, b, 216, geom, gram, counts)
         zb.append(z); ub.append(u); cb.append(uc)
-    ref_bank = O.solve_bank(gram, counts, geom, 1e-3)
+    return gram, counts, O.solve_bank(gram, counts, geom, 1e-3), zb, ub, cb
+
+
+_TRAIN_CACHE = {}
+
+
+def _train_case(name):
+    if name not in _TRAIN_CACHE:
+        geom, n, (h, w) = {"cfg1": (O.Geometry(2, -1), 2, (128, 128)),
+                           "cfg2": (O.Geometry(3, 3), 2, (96, 80)),
+                           "cfg3": (O.Geometry(3, -1, cross=1), 2, (96, 96)),
+                           "cfg3_256x4": (O.Geometry(3, -1, cross=1), 4, (256, 256))}[name]
+        _TRAIN_CACHE[name] = (geom, _oracle_training_set(geom, n, h, w, 30000))
+    return _TRAIN_CACHE[name]
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2, 3], ids=lambda p: PREC_IDS[p])
+@pytest.mark.parametrize("case", ["cfg1", "cfg2", "cfg3", "cfg3_256x4"])
+def test_train_level_gram_and_bank(mdn, case, prec):
+    """Counts exact; Gram sums and the solved bank vs the FP64 oracle.  The
+    bank bar (1e-3 relative Frobenius, BF16 1e-2) applies to the whole bank
+    on the 4 x 256^2 set and to every bucket with n_k >= 10 D; the tiny sets'
+    whole banks are dominated by under-sampled buckets and get 2x slack."""
+    geom, (gram, counts, ref_bank, zb, ub, cb) = _train_case(case)
     Z = _tt(np.stack(zb), "f32")
     U = _tt(np.stack(ub), "f32")
     Cc = _tt(np.stack(cb), "f32") if geom.r_coarse >= 0 else None
-    g, c, bank = mdn.train_level_filters(Z, Cc, U, _geom(mdn, geom), mdn.default_bparams(0),
-                                         mdn.GRAM_FP32, lam=1e-3)
+    g, c, bank = mdn.train_level_filters(Z, Cc, U, _geom(mdn, geom), mdn.default_bparams(0), prec, lam=1e-3)
+    torch.cuda.synchronize()
+    assert mdn.train_status() == 0
     g, c, bank = _np(g), c.cpu().numpy(), _np(bank)
     assert np.array_equal(c, counts)
     rel = np.linalg.norm(g - gram) / np.linalg.norm(gram)
-    assert rel < 1e-5, rel
-    rb = np.linalg.norm(bank - ref_bank) / np.linalg.norm(ref_bank)
-    assert rb < 1e-3, rb
+    assert rel < GRAM_TOL[prec], rel
+    D = geom.D()
+    big = [k for k in range(216) if counts[k] >= 10 * D]
+    for k in big:
+        e = np.linalg.norm(bank[k] - ref_bank[k]) / np.linalg.norm(ref_bank[k])
+        assert e < BANK_TOL[prec], (k, e)
+    whole = np.linalg.norm(bank - ref_bank) / np.linalg.norm(ref_bank)
+    slack = 1.0 if case == "cfg3_256x4" else 2.0
+    assert whole < slack * BANK_TOL[prec], whole
+    if case == "cfg3_256x4":
+        assert len(big) >= 20
 
 
 def test_solve_bank_matches_oracle(mdn):
