@@ -299,11 +299,139 @@ def run_gpu(args, rank, world, frames):
         "clocks": {"sm_mhz": clk_summary["sm_mhz"], "sm_max_mhz": clk_summary["sm_max_mhz"],
                    "reasons": clk_summary["reasons"]},
     }
+    if args.serve and world == 1:
+        line["serving"] = serving_subprocess(args)
     if args.cpu_baseline:
         v, tot, sample = cpu_oracle_run(12, 1)
         line["cpu_baseline"] = {"value": round(v, 3), "unit": "Mpix/s", "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": sample}
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- serving
+
+SERVE_SIZES = [(480, 640), (720, 1280), (1080, 1920), (3024, 4032)]
+SERVE_SIGMAS = [15, 25, 50]
+
+
+def run_serving(args, dev):
+    """Poisson request stream (mixed sizes, sigma and level count) through the
+    continuous-batching server and through the plain per-image path (one
+    mdn_denoise_multiscale per request, in arrival order); p50/p99 latency and
+    Mpix/s for both at every rate."""
+    import torch
+    import paper_1802_06130_gb300 as mdn
+    rng = np.random.default_rng(50000)
+    # bank sets: one per (sigma, levels in {3, 4}); random FP16 banks
+    sets, set_of = [], {}
+    for si, sg in enumerate(SERVE_SIGMAS):
+        for L in (3, 4):
+            banks = [torch.tensor(b, dtype=torch.float16, device=dev) for b in random_banks(100 + 10 * si + L, nb=L - 1)]
+            set_of[(sg, L)] = len(sets)
+            sets.append((banks, [mdn.default_bparams(l) for l in range(L - 1)]))
+    # two distinct pinned input frames per size
+    import synth
+    frames = {}
+    for (h, w) in SERVE_SIZES:
+        frames[(h, w)] = [torch.tensor(synth.noisy_pair(h, w, 50100 + i + h)[0], dtype=torch.float16).pin_memory()
+                          for i in range(2)]
+    nreq = args.serve_requests
+    out_pool = {hw: [torch.empty((3, *hw), dtype=torch.float16).pin_memory() for _ in range(64)] for hw in SERVE_SIZES}
+    geom = mdn.Geometry(3, 3)
+    results = []
+    srv = mdn.Server(sets, budget_bytes=80 << 30, max_active=64, autotune=True)
+    tune = srv.stats()
+    try:
+        for rate in args.serve_rates:
+            arr = np.cumsum(rng.exponential(1.0 / rate, nreq))
+            pick = [(SERVE_SIZES[rng.integers(4)], SERVE_SIGMAS[rng.integers(3)], int(rng.integers(3, 5)), int(rng.integers(2)))
+                    for _ in range(nreq)]
+            pix = sum(hw[0] * hw[1] for hw, _, _, _ in pick)
+            # ---- server: submissions at the arrival times, a poller thread
+            # (blocking poll, GIL released in the C call) timestamps completions
+            lat, inflight, slot = [], {}, {hw: 0 for hw in SERVE_SIZES}
+            internal, by_size = [], {hw: [] for hw in SERVE_SIZES}
+            lock = threading.Lock()
+            stop = [False]
+
+            def poller():
+                got = 0
+                while got < nreq and not stop[0]:
+                    for r in srv.poll(64, 50):
+                        t = time.perf_counter() - t0
+                        with lock:
+                            a, hw_ = inflight.pop(r["id"])
+                            lat.append((t - a) * 1e3)
+                            by_size[hw_].append((t - a) * 1e3)
+                            internal.append(r["done_ms"] - r["submit_ms"])
+                        got += 1
+
+            t0 = time.perf_counter()
+            th = threading.Thread(target=poller)
+            th.start()
+            for i in range(nreq):
+                wait = arr[i] - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(wait)
+                hw, sg, L, f = pick[i]
+                y = out_pool[hw][slot[hw] % 64]
+                slot[hw] += 1
+                with lock:
+                    rid = srv.submit(frames[hw][f], y, set_of[(sg, L)])
+                    inflight[rid] = (arr[i], hw)
+            th.join(timeout=120)
+            stop[0] = True
+            span = time.perf_counter() - t0
+            srv_line = {"p50_ms": round(float(np.percentile(lat, 50)), 3),
+                        "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                        "mpix_s": round(pix / span / 1e6, 1),
+                        "internal_p50_ms": round(float(np.percentile(internal, 50)), 3),
+                        "internal_p99_ms": round(float(np.percentile(internal, 99)), 3),
+                        "by_size_p50_p99_ms": {f"{w}x{h}": [round(float(np.percentile(v, 50)), 3),
+                                                            round(float(np.percentile(v, 99)), 3)]
+                                               for (h, w), v in by_size.items() if v}}
+            # ---- plain per-image path, same stream ----
+            lat_b = []
+            stream = torch.cuda.current_stream()
+            xin = {hw: torch.empty((1, 3, *hw), dtype=torch.float16, device=dev) for hw in SERVE_SIZES}
+            t0 = time.perf_counter()
+            for k in range(nreq):
+                wait = arr[k] - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(wait)
+                hw, sg, L, f = pick[k]
+                banks, bps = sets[set_of[(sg, L)]]
+                xin[hw][0].copy_(frames[hw][f], non_blocking=True)
+                y = mdn.denoise_multiscale(xin[hw], banks, geom, bps)
+                out_pool[hw][0].copy_(y[0], non_blocking=True)
+                stream.synchronize()
+                lat_b.append((time.perf_counter() - t0 - arr[k]) * 1e3)
+            span_b = time.perf_counter() - t0
+            results.append({"rate_rps": rate, "requests": nreq, "server": srv_line,
+                            "per_image": {"p50_ms": round(float(np.percentile(lat_b, 50)), 3),
+                                          "p99_ms": round(float(np.percentile(lat_b, 99)), 3),
+                                          "mpix_s": round(pix / span_b / 1e6, 1)}})
+        st = srv.stats()
+    finally:
+        srv.close()
+    return {"workload": "Poisson arrivals; sizes uniform over 640x480, 1280x720, 1920x1080, 4032x3024 FP16; "
+                        "sigma in {15,25,50}/255 and 3 or 4 levels per request (one bank set each); 80 GB budget; "
+                        "64 slots", "rates": results, "tile_variant": tune["tile_variant"],
+            "autotune_ms": [round(v, 3) for v in tune["variant_ms"]],
+            "mean_stages_per_tick": round(st["tick_items"] / max(st["ticks"], 1), 2)}
+
+
+def serving_subprocess(args):
+    """The serving measurement runs in a fresh process (its own CUDA context and
+    host memory) so that the throughput benchmark's allocations do not colour
+    its latencies."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--serve-only", "--serve-requests", str(args.serve_requests),
+           "--serve-rates", *[str(r) for r in args.serve_rates]]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=1800)
+    for ln in r.stdout.splitlines()[::-1]:
+        if ln.startswith("{"):
+            return json.loads(ln)
+    return {"error": (r.stderr or r.stdout)[-500:]}
 
 
 def main():
@@ -314,12 +442,22 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-serve", dest="serve", action="store_false")
+    ap.add_argument("--serve-requests", type=int, default=600)
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[50, 100, 200, 400])
+    ap.add_argument("--serve-only", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     args.local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.serve_only:
+        import torch
+        import paper_1802_06130_gb300 as mdn
+        mdn.build()
+        print(json.dumps(run_serving(args, torch.device("cuda", args.local_rank))), flush=True)
         return
     # frames first: the spawn pool runs before this process touches CUDA
     frames = make_frames(args.batch, 40000 + 100 * rank)

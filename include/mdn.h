@@ -233,6 +233,79 @@ int mdn_solve_bank(const double* gram, const int64_t* counts, const mdn_geometry
                    int32_t K, double lambda, float* bank_out, int32_t* status_out, void* ws,
                    size_t ws_bytes, void* stream);
 
+
+/* ------------------------------------------------------------------ */
+/* Serving: continuous batching of multiscale denoise requests         */
+/* (a deployment layer; the paper describes per-image inference only)  */
+/* ------------------------------------------------------------------ */
+
+/* A registered bank set: the filters of one noise level for a `levels`-level
+ * pyramid.  Geometry must be 7x7 fine + 7x7 coarse per channel (r_fine = 3,
+ * r_coarse = 3, cross_channel = 0); banks are FP16 [K][3][98] device
+ * buffers owned by the caller and read for the server's lifetime. */
+typedef struct {
+    int32_t levels;                     /* 2..8 */
+    const void* const* banks;           /* HOST array of levels-1 device pointers */
+    const mdn_bucket_params* bparams;   /* HOST array of levels-1 entries */
+    int32_t color;                      /* MDN_YCBCR601 or MDN_RGB */
+} mdn_bankset;
+
+typedef struct {
+    int32_t device;              /* CUDA device ordinal */
+    size_t hbm_budget_bytes;     /* device memory for request buffers (one arena, allocated at create) */
+    int32_t max_active;          /* requests on the device at once (1..256) */
+    int32_t autotune;            /* 1: time the compiled tile shapes at create and keep the fastest */
+    int32_t tile_variant;        /* used when autotune = 0: 0, 1 or 2 (see mdn_server_get_stats) */
+} mdn_server_cfg;
+
+typedef struct {
+    uint64_t id;
+    int32_t status;              /* MDN_OK, or MDN_ETIMEOUT when cancelled before admission */
+    double submit_ms, admit_ms, done_ms;   /* server clock (ms since create) */
+} mdn_result;
+
+typedef struct {
+    uint64_t submitted, completed, cancelled, ticks, tick_items;
+    int32_t active, queued;
+    size_t arena_bytes, arena_used, arena_peak;
+    int32_t tile_variant;        /* chosen level-kernel tile shape */
+    float variant_ms[3];         /* autotuner timings (ms, -1 = not measured) */
+    int32_t variant_threads[3], variant_rows[3];   /* threads per CTA, tile rows */
+} mdn_server_stats;
+
+typedef struct mdn_server mdn_server;
+
+/* Creates a server on cfg->device: allocates the request arena
+ * (hbm_budget_bytes) once, copies the bank-set tables to the device, runs the
+ * tile-shape autotuner, captures the per-tick CUDA graph (batched pyramid
+ * launch + batched level launch, both reading a device work list) and starts
+ * the scheduler thread. */
+int mdn_server_create(const mdn_server_cfg* cfg, const mdn_bankset* sets, int32_t nsets, mdn_server** out);
+
+/* Queues one request: host_in and host_out are HOST buffers of [3][h][w]
+ * FP16 RGB (pinned memory gives asynchronous copies) that must stay valid
+ * until the request's result is polled.  Requests are admitted in FIFO order
+ * as arena space and slots free up; each tick advances every admitted
+ * request by one stage (upload, pyramid level, filter level, download), all
+ * of a tick's stages running in the same two batched launches.  Returns
+ * MDN_EBUDGET (nothing queued) if the request alone exceeds the budget. */
+int mdn_server_submit(mdn_server* srv, const void* host_in, void* host_out, int64_t h, int64_t w, int32_t set,
+                      uint64_t* id);
+
+/* Removes a request that has not been admitted yet; its result is reported
+ * with status MDN_ETIMEOUT.  Returns MDN_EINVAL if the id is not queued. */
+int mdn_server_cancel(mdn_server* srv, uint64_t id);
+
+/* Waits up to timeout_ms for at least one finished request (0 = do not
+ * wait) and returns up to max of them in results; *n = how many. */
+int mdn_server_poll(mdn_server* srv, mdn_result* results, int32_t max, int32_t* n, int32_t timeout_ms);
+
+int mdn_server_get_stats(mdn_server* srv, mdn_server_stats* st);
+
+/* Stops the scheduler (queued requests are dropped, admitted ones finish
+ * first), frees the arena and the graph. */
+int mdn_server_destroy(mdn_server* srv);
+
 #ifdef __cplusplus
 }
 #endif

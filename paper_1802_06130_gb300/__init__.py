@@ -16,7 +16,7 @@ from .build import LIB as _LIB_PATH, build
 __all__ = ["build", "lib", "Geometry", "BucketParams", "default_bparams", "MdnError",
            "build_pyramid", "select_buckets", "filter_level", "denoise_multiscale",
            "denoise_workspace_bytes", "train_level_filters", "solve_bank", "regressor_len",
-           "gram_state_shape", "train_status", "F32", "F16", "YCBCR601", "RGB", "GRAM_FP32", "GRAM_TF32",
+           "gram_state_shape", "train_status", "Server", "F32", "F16", "YCBCR601", "RGB", "GRAM_FP32", "GRAM_TF32",
            "GRAM_BF16", "GRAM_SPLIT_BF16"]
 
 F32, F16 = 0, 1
@@ -69,6 +69,29 @@ def default_bparams(level: int) -> BucketParams:
     return BucketParams(24, (0.135 * s, 0.16 * s), (0.10, 0.15), 1e-8)
 
 
+class ServerCfg(C.Structure):
+    _fields_ = [("device", C.c_int32), ("hbm_budget_bytes", C.c_size_t), ("max_active", C.c_int32),
+                ("autotune", C.c_int32), ("tile_variant", C.c_int32)]
+
+
+class BankSet(C.Structure):
+    _fields_ = [("levels", C.c_int32), ("banks", C.POINTER(C.c_void_p)), ("bparams", C.POINTER(BucketParams)),
+                ("color", C.c_int32)]
+
+
+class ServerResult(C.Structure):
+    _fields_ = [("id", C.c_uint64), ("status", C.c_int32), ("submit_ms", C.c_double), ("admit_ms", C.c_double),
+                ("done_ms", C.c_double)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("cancelled", C.c_uint64),
+                ("ticks", C.c_uint64), ("tick_items", C.c_uint64), ("active", C.c_int32), ("queued", C.c_int32),
+                ("arena_bytes", C.c_size_t), ("arena_used", C.c_size_t), ("arena_peak", C.c_size_t),
+                ("tile_variant", C.c_int32), ("variant_ms", C.c_float * 3), ("variant_threads", C.c_int32 * 3),
+                ("variant_rows", C.c_int32 * 3)]
+
+
 _lib = None
 
 
@@ -99,6 +122,12 @@ def lib():
             "mdn_solve_workspace_bytes": (sz, [G, i32]),
             "mdn_train_status": (C.c_int, [C.POINTER(C.c_int32)]),
             "mdn_solve_bank": (C.c_int, [vp, vp, G, i32, C.c_double, vp, vp, vp, sz, vp]),
+            "mdn_server_create": (C.c_int, [C.POINTER(ServerCfg), C.POINTER(BankSet), i32, C.POINTER(vp)]),
+            "mdn_server_submit": (C.c_int, [vp, vp, vp, i64, i64, i32, C.POINTER(C.c_uint64)]),
+            "mdn_server_cancel": (C.c_int, [vp, C.c_uint64]),
+            "mdn_server_poll": (C.c_int, [vp, C.POINTER(ServerResult), i32, C.POINTER(i32), i32]),
+            "mdn_server_get_stats": (C.c_int, [vp, C.POINTER(ServerStats)]),
+            "mdn_server_destroy": (C.c_int, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -272,6 +301,82 @@ def train_status() -> int:
     v = C.c_int32(0)
     _check(lib().mdn_train_status(C.byref(v)))
     return v.value
+
+
+class Server:
+    """Continuous-batching denoise server (mdn_server_*).
+
+    bank_sets: list of (banks, bparams) with banks a list of levels-1 FP16
+    [K][3][98] CUDA tensors (7x7 + 7x7 per-channel geometry) and bparams the
+    matching BucketParams list.  Inputs/outputs are host FP16 [3][h][w]
+    tensors (pinned for asynchronous copies) kept alive until polled."""
+
+    def __init__(self, bank_sets, budget_bytes: int, max_active: int = 16, autotune: bool = True,
+                 tile_variant: int = 1, device: int = 0, color: int = YCBCR601):
+        self._keep = []
+        n = len(bank_sets)
+        arr = (BankSet * n)()
+        for i, (banks, bparams) in enumerate(bank_sets):
+            if len(banks) != len(bparams):
+                raise ValueError("one BucketParams per bank")
+            ptrs = (C.c_void_p * len(banks))(*[b.data_ptr() for b in banks])
+            bps = (BucketParams * len(bparams))(*bparams)
+            self._keep += [ptrs, bps, banks]
+            arr[i].levels = len(banks) + 1
+            arr[i].banks = C.cast(ptrs, C.POINTER(C.c_void_p))
+            arr[i].bparams = C.cast(bps, C.POINTER(BucketParams))
+            arr[i].color = color
+        cfg = ServerCfg(device, budget_bytes, max_active, int(autotune), tile_variant)
+        h = C.c_void_p()
+        _check(lib().mdn_server_create(C.byref(cfg), arr, n, C.byref(h)))
+        self._h = h
+        self._io = {}
+
+    def submit(self, host_in, host_out, bank_set: int) -> int:
+        if host_in.dtype != host_out.dtype or host_in.shape != host_out.shape or host_in.dim() != 3:
+            raise ValueError("host_in/host_out: matching [3][h][w] FP16 host tensors")
+        if host_in.is_cuda or host_out.is_cuda or not host_in.is_contiguous() or not host_out.is_contiguous():
+            raise ValueError("host_in/host_out must be contiguous host tensors")
+        rid = C.c_uint64()
+        _, h, w = host_in.shape
+        _check(lib().mdn_server_submit(self._h, C.c_void_p(host_in.data_ptr()), C.c_void_p(host_out.data_ptr()),
+                                       h, w, bank_set, C.byref(rid)))
+        self._io[rid.value] = (host_in, host_out)
+        return rid.value
+
+    def cancel(self, rid: int):
+        _check(lib().mdn_server_cancel(self._h, rid))
+
+    def poll(self, max_results: int = 64, timeout_ms: int = 100):
+        res = (ServerResult * max_results)()
+        n = C.c_int32()
+        _check(lib().mdn_server_poll(self._h, res, max_results, C.byref(n), timeout_ms))
+        out = []
+        for i in range(n.value):
+            r = res[i]
+            self._io.pop(r.id, None)
+            out.append({"id": r.id, "status": r.status, "submit_ms": r.submit_ms, "admit_ms": r.admit_ms,
+                        "done_ms": r.done_ms})
+        return out
+
+    def stats(self):
+        st = ServerStats()
+        _check(lib().mdn_server_get_stats(self._h, C.byref(st)))
+        d = {f: getattr(st, f) for f, _ in ServerStats._fields_}
+        for k in ("variant_ms", "variant_threads", "variant_rows"):
+            d[k] = list(d[k])
+        return d
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(lib().mdn_server_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def solve_bank(gram, counts, geom: Geometry, lam: float = 1e-3, stream=None):

@@ -374,14 +374,19 @@ namespace v2 {
 #ifndef MDN_V2_PY
 #define MDN_V2_PY 4
 #endif
-constexpr int TW = 32, NT = MDN_V2_NT, PY = MDN_V2_PY, NW = NT / 32, TH = NW * PY;
-constexpr int HZ = 3;
-constexpr int ZW = TW + 2 * HZ, ZH = TH + 2 * HZ;
-constexpr int PW = TW + 4, PH = TH + 4;
 
-template <int RC> struct Coarse {
-    static constexpr int UW = RC >= 0 ? TW / 2 + 2 * RC : 0;
-    static constexpr int UH = RC >= 0 ? TH / 2 + 2 * RC : 0;
+// Tile shape: 32 columns (one warp), NT threads, PY rows per thread strip.
+template <int NT_, int PY_> struct Shape {
+    static constexpr int TW = 32, NT = NT_, PY = PY_, NW = NT / 32, TH = NW * PY;
+    static constexpr int HZ = 3;
+    static constexpr int ZW = TW + 2 * HZ, ZH = TH + 2 * HZ;
+    static constexpr int PW = TW + 4, PH = TH + 4;
+};
+using DefShape = Shape<MDN_V2_NT, MDN_V2_PY>;
+
+template <class SH, int RC> struct Coarse {
+    static constexpr int UW = RC >= 0 ? SH::TW / 2 + 2 * RC : 0;
+    static constexpr int UH = RC >= 0 ? SH::TH / 2 + 2 * RC : 0;
 };
 
 template <int RF, int RC, bool CROSS> struct Slots {
@@ -400,13 +405,17 @@ template <int RF, int RC, bool CROSS, typename TB> constexpr int bucket_units() 
     return (u % 2 == 1) ? u : u + 1;
 }
 
-template <int RC> constexpr size_t tile_bytes() {
-    return sizeof(float) * (3 * ZH * ZW + 3 * PH * PW + 3 * PH * TW + 3 * Coarse<RC>::UH * Coarse<RC>::UW) +
-           TH * TW;
+template <class SH, int RC> constexpr size_t tile_bytes() {
+    return sizeof(float) * (3 * SH::ZH * SH::ZW + 3 * SH::PH * SH::PW + 3 * SH::PH * SH::TW +
+                            3 * Coarse<SH, RC>::UH * Coarse<SH, RC>::UW) +
+           SH::TH * SH::TW;
 }
 
+template <class SH, int RF, int RC, bool CROSS, typename TB> size_t smem_need_s(int K) {
+    return ((tile_bytes<SH, RC>() + 15) & ~size_t(15)) + (size_t)K * bucket_units<RF, RC, CROSS, TB>() * 16;
+}
 template <int RF, int RC, bool CROSS, typename TB> size_t smem_need(int K) {
-    return ((tile_bytes<RC>() + 15) & ~size_t(15)) + (size_t)K * bucket_units<RF, RC, CROSS, TB>() * 16;
+    return smem_need_s<DefShape, RF, RC, CROSS, TB>(K);
 }
 
 // 8 taps of one slot as floats
@@ -425,222 +434,242 @@ template <> __device__ __forceinline__ void load_slot<float>(const unsigned char
     h[0] = a.x; h[1] = a.y; h[2] = a.z; h[3] = a.w; h[4] = b.x; h[5] = b.y; h[6] = b.z; h[7] = b.w;
 }
 
-template <int RF, int RC, bool CROSS, typename TS, typename TB>
-__global__ void __launch_bounds__(NT, 1) k_level2(const TS* __restrict__ z, const TS* __restrict__ coarse,
-                                                  TS* __restrict__ out, uint8_t* __restrict__ bmap,
-                                                  const TB* __restrict__ bank, int H, int W, int Hc, int Wc,
-                                                  int nimg, int K, int color, SelParams sp, float w0, float w1,
-                                                  float w2) {
+// bank [K][3][D] (regressor order) -> shared-memory slots, by nthreads threads
+template <int RF, int RC, bool CROSS, typename TB>
+__device__ __forceinline__ void load_bank_slots(const TB* __restrict__ bank, int K, unsigned char* bank_s, int tid,
+                                                int nthreads) {
     using G = Geo<RF, RC, CROSS>;
     using SL = Slots<RF, RC, CROSS>;
-    constexpr int UW = Coarse<RC>::UW, UH = Coarse<RC>::UH;
     constexpr int SB = SlotBytes<TB>::B;
-    constexpr int BSTRIDE = bucket_units<RF, RC, CROSS, TB>() * 16;   // bytes per bucket
-    constexpr int NCX = RC >= 0 ? 2 * RC + 1 : 0;                       // coarse columns per channel
+    constexpr int BSTRIDE = bucket_units<RF, RC, CROSS, TB>() * 16;
+    constexpr int NCX = RC >= 0 ? 2 * RC + 1 : 0;
     constexpr int NFX = 2 * RF + 1;
-    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int E = SB / (int)sizeof(TB);   // 8 elements per slot
+    const int total = K * SL::S * E;
+    for (int i = tid; i < total; i += nthreads) {
+        const int e = i % E, slot = (i / E) % SL::S, k = i / (E * SL::S);
+        const int oc = slot / SL::PER_OC, sr = slot % SL::PER_OC;
+        int src = -1;
+        if (sr < G::NCH * NCX) {                    // coarse block of channel cc
+            const int cc = sr / (NCX > 0 ? NCX : 1), dx = sr % (NCX > 0 ? NCX : 1);
+            if (e < NCX) src = cc * G::PC + e * NCX + dx;
+        } else {
+            const int t = sr - G::NCH * NCX;
+            const int cc = t / NFX, dx = t % NFX;
+            if (e < NFX) src = G::NCH * G::PC + cc * G::PF + e * NFX + dx;
+        }
+        TB v = src >= 0 ? bank[((int64_t)k * 3 + oc) * G::D + src] : TB(0.f);
+        reinterpret_cast<TB*>(bank_s + (size_t)k * BSTRIDE + slot * SB)[e] = v;
+    }
+}
+
+// One TW x TH tile at (x0, y0) of one image: stage, select, filter, store.
+// smem: tile buffers (tile_bytes<SH, RC>()); bank_s: the bank's slots.
+// zi/ci/oi: this image's planes; bmap_img: its bucket map or nullptr.
+template <class SH, int RF, int RC, bool CROSS, typename TS, typename TB>
+__device__ __forceinline__ void tile_v2(unsigned char* smem, const unsigned char* bank_s, const TS* __restrict__ zi,
+                                        const TS* __restrict__ ci, TS* __restrict__ oi, uint8_t* __restrict__ bmap_img,
+                                        int H, int W, int Hc, int Wc, int x0, int y0, int K, int color,
+                                        const SelParams& sp, const float wv[5]) {
+    using G = Geo<RF, RC, CROSS>;
+    using SL = Slots<RF, RC, CROSS>;
+    constexpr int TW = SH::TW, TH = SH::TH, NT = SH::NT, PY = SH::PY, HZ = SH::HZ;
+    constexpr int ZW = SH::ZW, ZH = SH::ZH, PW = SH::PW, PH = SH::PH;
+    constexpr int UW = Coarse<SH, RC>::UW, UH = Coarse<SH, RC>::UH;
+    constexpr int SB = SlotBytes<TB>::B;
+    constexpr int BSTRIDE = bucket_units<RF, RC, CROSS, TB>() * 16;
     float* zs = reinterpret_cast<float*>(smem);             // [3][ZH][ZW]
     float* ps = zs + 3 * ZH * ZW;                            // [3][PH][PW]
     float* hs = ps + 3 * PH * PW;                            // [3][PH][TW]
     float* us = hs + 3 * PH * TW;                            // [3][UH][UW]
     uint8_t* bk = reinterpret_cast<uint8_t*>(us + 3 * UH * UW);  // [TH][TW]
-    unsigned char* bank_s = smem + ((tile_bytes<RC>() + 15) & ~size_t(15));
-    const int tid = threadIdx.x;
-    const float wv[5] = {w0, w1, w2, w1, w0};
-
-    // ---- bank -> slots (once per persistent CTA) ----
-    {
-        constexpr int E = SB / (int)sizeof(TB);   // 8 elements per slot
-        const int total = K * SL::S * E;
-        for (int i = tid; i < total; i += NT) {
-            const int e = i % E, slot = (i / E) % SL::S, k = i / (E * SL::S);
-            const int oc = slot / SL::PER_OC, sr = slot % SL::PER_OC;
-            int src = -1;
-            if (sr < G::NCH * NCX) {                    // coarse block of channel cc
-                const int cc = sr / (NCX > 0 ? NCX : 1), dx = sr % (NCX > 0 ? NCX : 1);
-                if (e < NCX) src = cc * G::PC + e * NCX + dx;
-            } else {
-                const int t = sr - G::NCH * NCX;
-                const int cc = t / NFX, dx = t % NFX;
-                if (e < NFX) src = G::NCH * G::PC + cc * G::PF + e * NFX + dx;
-            }
-            TB v = src >= 0 ? bank[((int64_t)k * 3 + oc) * G::D + src] : TB(0.f);
-            reinterpret_cast<TB*>(bank_s + (size_t)k * BSTRIDE + slot * SB)[e] = v;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < 3 * ZH * ZW; i += NT) {
+        int c = i / (ZH * ZW), r = (i / ZW) % ZH, q = i % ZW;
+        int gy = clampi(y0 - HZ + r, 0, H - 1), gx = clampi(x0 - HZ + q, 0, W - 1);
+        zs[i] = ld_f(zi, ((int64_t)c * H + gy) * W + gx);
+    }
+    if constexpr (RC >= 0) {
+        const int cx0 = x0 / 2 - RC, cy0 = y0 / 2 - RC;
+        for (int i = tid; i < UH * UW; i += NT) {
+            int r = i / UW, q = i % UW;
+            int gy = clampi(cy0 + r, 0, Hc - 1), gx = clampi(cx0 + q, 0, Wc - 1);
+            int64_t o = (int64_t)gy * Wc + gx;
+            float a, b, c;
+            rgb_to_work(ld_f(ci, o), ld_f(ci, o + (int64_t)Hc * Wc), ld_f(ci, o + 2 * (int64_t)Hc * Wc), color, a, b,
+                        c);
+            us[i] = a; us[UH * UW + i] = b; us[2 * UH * UW + i] = c;
         }
     }
-
-    const int tiles_x = (W + TW - 1) / TW, tiles_y = (H + TH - 1) / TH;
-    const int64_t ntiles = (int64_t)tiles_x * tiles_y * nimg;
-    const int lane = tid & 31, warp = tid >> 5;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int img = (int)(tile / ((int64_t)tiles_x * tiles_y));
-        const int trem = (int)(tile % ((int64_t)tiles_x * tiles_y));
-        const int x0 = (trem % tiles_x) * TW, y0 = (trem / tiles_x) * TH;
-        const TS* zi = z + (int64_t)img * 3 * H * W;
-        __syncthreads();
-        for (int i = tid; i < 3 * ZH * ZW; i += NT) {
-            int c = i / (ZH * ZW), r = (i / ZW) % ZH, q = i % ZW;
-            int gy = clampi(y0 - HZ + r, 0, H - 1), gx = clampi(x0 - HZ + q, 0, W - 1);
-            zs[i] = ld_f(zi, ((int64_t)c * H + gy) * W + gx);
-        }
-        if constexpr (RC >= 0) {
-            const TS* ci = coarse + (int64_t)img * 3 * Hc * Wc;
-            const int cx0 = x0 / 2 - RC, cy0 = y0 / 2 - RC;
-            for (int i = tid; i < UH * UW; i += NT) {
-                int r = i / UW, q = i % UW;
-                int gy = clampi(cy0 + r, 0, Hc - 1), gx = clampi(cx0 + q, 0, Wc - 1);
-                int64_t o = (int64_t)gy * Wc + gx;
-                float a, b, c;
-                rgb_to_work(ld_f(ci, o), ld_f(ci, o + (int64_t)Hc * Wc), ld_f(ci, o + 2 * (int64_t)Hc * Wc), color,
-                            a, b, c);
-                us[i] = a; us[UH * UW + i] = b; us[2 * UH * UW + i] = c;
-            }
-        }
-        __syncthreads();
-        for (int i = tid; i < PH * PW; i += NT) {
-            int r = i / PW, q = i % PW;
-            int cy = clampi(y0 - 2 + r, 0, H - 1), cx = clampi(x0 - 2 + q, 0, W - 1);
-            int ly = cy - (y0 - HZ), lx = cx - (x0 - HZ);
-            int lxm = clampi(cx - 1, 0, W - 1) - (x0 - HZ), lxp = clampi(cx + 1, 0, W - 1) - (x0 - HZ);
-            int lym = clampi(cy - 1, 0, H - 1) - (y0 - HZ), lyp = clampi(cy + 1, 0, H - 1) - (y0 - HZ);
-            float gx[3], gy[3];
+    __syncthreads();
+    for (int i = tid; i < PH * PW; i += NT) {
+        int r = i / PW, q = i % PW;
+        int cy = clampi(y0 - 2 + r, 0, H - 1), cx = clampi(x0 - 2 + q, 0, W - 1);
+        int ly = cy - (y0 - HZ), lx = cx - (x0 - HZ);
+        int lxm = clampi(cx - 1, 0, W - 1) - (x0 - HZ), lxp = clampi(cx + 1, 0, W - 1) - (x0 - HZ);
+        int lym = clampi(cy - 1, 0, H - 1) - (y0 - HZ), lyp = clampi(cy + 1, 0, H - 1) - (y0 - HZ);
+        float gx[3], gy[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float* zc = zs + c * ZH * ZW;
-                gx[c] = __fmul_rn(__fsub_rn(zc[ly * ZW + lxp], zc[ly * ZW + lxm]), 0.5f);
-                gy[c] = __fmul_rn(__fsub_rn(zc[lyp * ZW + lx], zc[lym * ZW + lx]), 0.5f);
-            }
-            float pxx = __fmul_rn(gx[0], gx[0]), pxy = __fmul_rn(gx[0], gy[0]), pyy = __fmul_rn(gy[0], gy[0]);
-#pragma unroll
-            for (int c = 1; c < 3; ++c) {
-                pxx = __fmaf_rn(gx[c], gx[c], pxx);
-                pxy = __fmaf_rn(gx[c], gy[c], pxy);
-                pyy = __fmaf_rn(gy[c], gy[c], pyy);
-            }
-            ps[i] = pxx; ps[PH * PW + i] = pxy; ps[2 * PH * PW + i] = pyy;
+        for (int c = 0; c < 3; ++c) {
+            const float* zc = zs + c * ZH * ZW;
+            gx[c] = __fmul_rn(__fsub_rn(zc[ly * ZW + lxp], zc[ly * ZW + lxm]), 0.5f);
+            gy[c] = __fmul_rn(__fsub_rn(zc[lyp * ZW + lx], zc[lym * ZW + lx]), 0.5f);
         }
-        __syncthreads();
-        for (int i = tid; i < 3 * PH * TW; i += NT) {
-            int f = i / (PH * TW), r = (i / TW) % PH, q = i % TW;
-            const float* p = ps + f * PH * PW + r * PW + q;
+        float pxx = __fmul_rn(gx[0], gx[0]), pxy = __fmul_rn(gx[0], gy[0]), pyy = __fmul_rn(gy[0], gy[0]);
+#pragma unroll
+        for (int c = 1; c < 3; ++c) {
+            pxx = __fmaf_rn(gx[c], gx[c], pxx);
+            pxy = __fmaf_rn(gx[c], gy[c], pxy);
+            pyy = __fmaf_rn(gy[c], gy[c], pyy);
+        }
+        ps[i] = pxx; ps[PH * PW + i] = pxy; ps[2 * PH * PW + i] = pyy;
+    }
+    __syncthreads();
+    for (int i = tid; i < 3 * PH * TW; i += NT) {
+        int f = i / (PH * TW), r = (i / TW) % PH, q = i % TW;
+        const float* p = ps + f * PH * PW + r * PW + q;
+        float acc = __fmul_rn(wv[0], p[0]);
+#pragma unroll
+        for (int u = 1; u < 5; ++u) acc = __fmaf_rn(wv[u], p[u], acc);
+        hs[i] = acc;
+    }
+    for (int i = tid; i < ZH * ZW; i += NT) {
+        float a, b, c;
+        rgb_to_work(zs[i], zs[ZH * ZW + i], zs[2 * ZH * ZW + i], color, a, b, c);
+        zs[i] = a; zs[ZH * ZW + i] = b; zs[2 * ZH * ZW + i] = c;
+    }
+    __syncthreads();
+    for (int i = tid; i < TH * TW; i += NT) {
+        int r = i / TW, q = i % TW;
+        float t3[3];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            const float* p = hs + f * PH * TW + r * TW + q;
             float acc = __fmul_rn(wv[0], p[0]);
 #pragma unroll
-            for (int u = 1; u < 5; ++u) acc = __fmaf_rn(wv[u], p[u], acc);
-            hs[i] = acc;
+            for (int v = 1; v < 5; ++v) acc = __fmaf_rn(wv[v], p[v * TW], acc);
+            t3[f] = acc;
         }
-        for (int i = tid; i < ZH * ZW; i += NT) {
-            float a, b, c;
-            rgb_to_work(zs[i], zs[ZH * ZW + i], zs[2 * ZH * ZW + i], color, a, b, c);
-            zs[i] = a; zs[ZH * ZW + i] = b; zs[2 * ZH * ZW + i] = c;
-        }
-        __syncthreads();
-        for (int i = tid; i < TH * TW; i += NT) {
-            int r = i / TW, q = i % TW;
-            float t3[3];
+        int k = bucket_of(t3[0], t3[1], t3[2], sp);
+        k = k < K ? k : K - 1;
+        bk[i] = (uint8_t)k;
+        int gy = y0 + r, gx = x0 + q;
+        if (bmap_img && gy < H && gx < W) bmap_img[(int64_t)gy * W + gx] = (uint8_t)k;
+    }
+    __syncthreads();
+    // ---- filtering: lane = column, warp = strip of PY rows ----
+    const int q = lane, r0 = warp * PY;
+    const unsigned char* hb[PY];
 #pragma unroll
-            for (int f = 0; f < 3; ++f) {
-                const float* p = hs + f * PH * TW + r * TW + q;
-                float acc = __fmul_rn(wv[0], p[0]);
+    for (int p = 0; p < PY; ++p) hb[p] = bank_s + (size_t)bk[(r0 + p) * TW + q] * BSTRIDE;
+    float o[3][PY];
 #pragma unroll
-                for (int v = 1; v < 5; ++v) acc = __fmaf_rn(wv[v], p[v * TW], acc);
-                t3[f] = acc;
-            }
-            int k = bucket_of(t3[0], t3[1], t3[2], sp);
-            k = k < K ? k : K - 1;
-            bk[i] = (uint8_t)k;
-            int gy = y0 + r, gx = x0 + q;
-            if (bmap && gy < H && gx < W) bmap[((int64_t)img * H + gy) * W + gx] = (uint8_t)k;
-        }
-        __syncthreads();
-        // ---- filtering: lane = column, warp = strip of PY rows ----
-        const int q = lane, r0 = warp * PY;
-        const unsigned char* hb[PY];
+    for (int oc = 0; oc < 3; ++oc) {
+        float acc[PY];
 #pragma unroll
-        for (int p = 0; p < PY; ++p) hb[p] = bank_s + (size_t)bk[(r0 + p) * TW + q] * BSTRIDE;
-        float o[3][PY];
-#pragma unroll
-        for (int oc = 0; oc < 3; ++oc) {
-            float acc[PY];
-#pragma unroll
-            for (int p = 0; p < PY; ++p) acc[p] = 0.f;
-            int slot = oc * SL::PER_OC;
-            if constexpr (RC >= 0) {
-                constexpr int NCR = PY / 2 + 2 * RC;     // coarse rows touched by the strip
-#pragma unroll
-                for (int cc = 0; cc < G::NCH; ++cc) {
-                    const int c = CROSS ? cc : oc;
-                    const float* ub = us + c * UH * UW + (r0 / 2) * UW + (q / 2) + RC;
-#pragma unroll
-                    for (int dx = -RC; dx <= RC; ++dx, ++slot) {
-                        float col[NCR];
-#pragma unroll
-                        for (int j = 0; j < NCR; ++j) col[j] = ub[j * UW + dx];
-#pragma unroll
-                        for (int p = 0; p < PY; ++p) {
-                            float h[8];
-                            load_slot<TB>(hb[p] + slot * SB, h);
-#pragma unroll
-                            for (int dy = 0; dy < 2 * RC + 1; ++dy) acc[p] = fmaf(h[dy], col[p / 2 + dy], acc[p]);
-                        }
-                    }
-                }
-            }
+        for (int p = 0; p < PY; ++p) acc[p] = 0.f;
+        int slot = oc * SL::PER_OC;
+        if constexpr (RC >= 0) {
+            constexpr int NCR = PY / 2 + 2 * RC;     // coarse rows touched by the strip
 #pragma unroll
             for (int cc = 0; cc < G::NCH; ++cc) {
                 const int c = CROSS ? cc : oc;
-                const float* zb = zs + c * ZH * ZW + (r0 + HZ - RF) * ZW + q + HZ;
+                const float* ub = us + c * UH * UW + (r0 / 2) * UW + (q / 2) + RC;
 #pragma unroll
-                for (int dx = -RF; dx <= RF; ++dx, ++slot) {
-                    float col[PY + 2 * RF];
+                for (int dx = -RC; dx <= RC; ++dx, ++slot) {
+                    float col[NCR];
 #pragma unroll
-                    for (int j = 0; j < PY + 2 * RF; ++j) col[j] = zb[j * ZW + dx];
+                    for (int j = 0; j < NCR; ++j) col[j] = ub[j * UW + dx];
 #pragma unroll
                     for (int p = 0; p < PY; ++p) {
                         float h[8];
                         load_slot<TB>(hb[p] + slot * SB, h);
 #pragma unroll
-                        for (int dy = 0; dy < 2 * RF + 1; ++dy) acc[p] = fmaf(h[dy], col[p + dy], acc[p]);
+                        for (int dy = 0; dy < 2 * RC + 1; ++dy) acc[p] = fmaf(h[dy], col[p / 2 + dy], acc[p]);
                     }
                 }
             }
-#pragma unroll
-            for (int p = 0; p < PY; ++p) o[oc][p] = acc[p];
         }
-        TS* oi = out + (int64_t)img * 3 * H * W;
-        const int gx = x0 + q;
 #pragma unroll
-        for (int p = 0; p < PY; ++p) {
-            const int gy = y0 + r0 + p;
-            if (gy < H && gx < W) {
-                float R, Gc, B;
-                work_to_rgb(o[0][p], o[1][p], o[2][p], color, R, Gc, B);
-                int64_t po = (int64_t)gy * W + gx;
-                st_f(oi, po, R);
-                st_f(oi, (int64_t)H * W + po, Gc);
-                st_f(oi, 2 * (int64_t)H * W + po, B);
+        for (int cc = 0; cc < G::NCH; ++cc) {
+            const int c = CROSS ? cc : oc;
+            const float* zb = zs + c * ZH * ZW + (r0 + HZ - RF) * ZW + q + HZ;
+#pragma unroll
+            for (int dx = -RF; dx <= RF; ++dx, ++slot) {
+                float col[PY + 2 * RF];
+#pragma unroll
+                for (int j = 0; j < PY + 2 * RF; ++j) col[j] = zb[j * ZW + dx];
+#pragma unroll
+                for (int p = 0; p < PY; ++p) {
+                    float h[8];
+                    load_slot<TB>(hb[p] + slot * SB, h);
+#pragma unroll
+                    for (int dy = 0; dy < 2 * RF + 1; ++dy) acc[p] = fmaf(h[dy], col[p + dy], acc[p]);
+                }
             }
         }
+#pragma unroll
+        for (int p = 0; p < PY; ++p) o[oc][p] = acc[p];
+    }
+    const int gx = x0 + q;
+#pragma unroll
+    for (int p = 0; p < PY; ++p) {
+        const int gy = y0 + r0 + p;
+        if (gy < H && gx < W) {
+            float R, Gc, B;
+            work_to_rgb(o[0][p], o[1][p], o[2][p], color, R, Gc, B);
+            int64_t po = (int64_t)gy * W + gx;
+            st_f(oi, po, R);
+            st_f(oi, (int64_t)H * W + po, Gc);
+            st_f(oi, 2 * (int64_t)H * W + po, B);
+        }
+    }
+}
+
+template <class SH, int RF, int RC, bool CROSS, typename TS, typename TB>
+__global__ void __launch_bounds__(SH::NT, 1) k_level2(const TS* __restrict__ z, const TS* __restrict__ coarse,
+                                                      TS* __restrict__ out, uint8_t* __restrict__ bmap,
+                                                      const TB* __restrict__ bank, int H, int W, int Hc, int Wc,
+                                                      int nimg, int K, int color, SelParams sp, float w0, float w1,
+                                                      float w2) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned char* bank_s = smem + ((tile_bytes<SH, RC>() + 15) & ~size_t(15));
+    const float wv[5] = {w0, w1, w2, w1, w0};
+    load_bank_slots<RF, RC, CROSS, TB>(bank, K, bank_s, threadIdx.x, SH::NT);
+    const int tiles_x = (W + SH::TW - 1) / SH::TW, tiles_y = (H + SH::TH - 1) / SH::TH;
+    const int64_t ntiles = (int64_t)tiles_x * tiles_y * nimg;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int img = (int)(tile / ((int64_t)tiles_x * tiles_y));
+        const int trem = (int)(tile % ((int64_t)tiles_x * tiles_y));
+        const int x0 = (trem % tiles_x) * SH::TW, y0 = (trem / tiles_x) * SH::TH;
+        __syncthreads();   // bank slots loaded / previous tile finished with the shared buffers
+        tile_v2<SH, RF, RC, CROSS, TS, TB>(smem, bank_s, z + (int64_t)img * 3 * H * W,
+                                           RC >= 0 ? coarse + (int64_t)img * 3 * Hc * Wc : nullptr,
+                                           out + (int64_t)img * 3 * H * W,
+                                           bmap ? bmap + (int64_t)img * H * W : nullptr, H, W, Hc, Wc, x0, y0, K,
+                                           color, sp, wv);
     }
 }
 
 template <int RF, int RC, bool CROSS, typename TS, typename TB>
 int run2(const LevelArgs& a, cudaStream_t s) {
-    auto kern = k_level2<RF, RC, CROSS, TS, TB>;
-    const size_t bytes = smem_need<RF, RC, CROSS, TB>(a.K);
+    using SH = DefShape;
+    auto kern = k_level2<SH, RF, RC, CROSS, TS, TB>;
+    const size_t bytes = smem_need_s<SH, RF, RC, CROSS, TB>(a.K);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return cuda_fail(e, "k_level2: set smem attribute");
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, SH::NT, bytes);
     if (e != cudaSuccess) return cuda_fail(e, "k_level2: occupancy");
     if (occ < 1) return fail(MDN_ESHAPE, "k_level2: shared memory footprint too large");
-    const int64_t tiles = ((a.w + TW - 1) / TW) * ((a.h + TH - 1) / TH) * a.n;
+    const int64_t tiles = ((a.w + SH::TW - 1) / SH::TW) * ((a.h + SH::TH - 1) / SH::TH) * a.n;
     int64_t grid = (int64_t)num_sms() * occ;
     if (grid > tiles) grid = tiles;
     float w[5];
     gauss5_weights(w);
-    kern<<<(unsigned)grid, NT, bytes, s>>>((const TS*)a.z, (const TS*)a.coarse, (TS*)a.out, a.buckets,
-                                           (const TB*)a.bank, (int)a.h, (int)a.w, (int)a.hc, (int)a.wc,
-                                           (int)a.n, a.K, a.geom.color, a.sel, w[0], w[1], w[2]);
+    kern<<<(unsigned)grid, SH::NT, bytes, s>>>((const TS*)a.z, (const TS*)a.coarse, (TS*)a.out, a.buckets,
+                                               (const TB*)a.bank, (int)a.h, (int)a.w, (int)a.hc, (int)a.wc,
+                                               (int)a.n, a.K, a.geom.color, a.sel, w[0], w[1], w[2]);
     return check_launch("k_level2");
 }
 
@@ -711,25 +740,7 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
     unsigned char* bank_s = smem + front_bytes<RC>();
     const int tid = threadIdx.x;
 
-    {   // bank -> slots, all threads, once per persistent CTA
-        constexpr int E = SB / (int)sizeof(TB);
-        const int total = K * SL::S * E;
-        for (int i = tid; i < total; i += NT) {
-            const int e = i % E, slot = (i / E) % SL::S, k = i / (E * SL::S);
-            const int oc = slot / SL::PER_OC, sr = slot % SL::PER_OC;
-            int src = -1;
-            if (sr < G::NCH * NCX) {
-                const int cc = sr / (NCX > 0 ? NCX : 1), dx = sr % (NCX > 0 ? NCX : 1);
-                if (e < NCX) src = cc * G::PC + e * NCX + dx;
-            } else {
-                const int t = sr - G::NCH * NCX;
-                const int cc = t / NFX, dx = t % NFX;
-                if (e < NFX) src = G::NCH * G::PC + cc * G::PF + e * NFX + dx;
-            }
-            TB v = src >= 0 ? bank[((int64_t)k * 3 + oc) * G::D + src] : TB(0.f);
-            reinterpret_cast<TB*>(bank_s + (size_t)k * BSTRIDE + slot * SB)[e] = v;
-        }
-    }
+    v2::load_bank_slots<RF, RC, CROSS, TB>(bank, K, bank_s, tid, NT);   // once per persistent CTA
     __syncthreads();
 
     const int tiles_x = (W + TW - 1) / TW, tiles_y = (H + TH - 1) / TH;

@@ -1,0 +1,125 @@
+"""Serving (continuous batching): results identical alone and in a mixed
+stream, admission by memory budget, cancellation and bounded polling."""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mdn():
+    import paper_1802_06130_gb300 as m
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    m.build()
+    m.lib()
+    return m
+
+
+def _bank_set(mdn, levels, seed):
+    rng = np.random.default_rng(seed)
+    banks = []
+    for _ in range(levels - 1):
+        b = rng.standard_normal((216, 3, 98)).astype(np.float32) * 0.03
+        b += (1.0 - b.sum(axis=2, keepdims=True)) / 98
+        banks.append(torch.tensor(b, dtype=torch.float16, device="cuda"))
+    return banks, [mdn.default_bparams(l) for l in range(levels - 1)]
+
+
+def _frame(h, w, seed):
+    z = synth.noisy_pair(h, w, seed)[0]
+    return torch.tensor(z, dtype=torch.float16).pin_memory()
+
+
+def _drain(srv, want, timeout_s=60.0):
+    import time
+    got = {}
+    t0 = time.time()
+    while len(got) < want:
+        for r in srv.poll(64, 200):
+            got[r["id"]] = r
+        assert time.time() - t0 < timeout_s, "server did not finish in time"
+    return got
+
+
+def test_mixed_stream_equals_single_image_path(mdn):
+    sets = [_bank_set(mdn, 3, 1), _bank_set(mdn, 4, 2)]
+    sizes = [(64, 80), (131, 97), (240, 320), (33, 17), (1, 1), (480, 640), (97, 131), (256, 256)]
+    srv = mdn.Server(sets, budget_bytes=256 << 20, max_active=6, autotune=True)
+    try:
+        # frames made first so that the requests arrive in a burst and share ticks
+        io = []
+        for i in range(16):
+            h, w = sizes[i % len(sizes)]
+            x = _frame(h, w, 60000 + i)
+            io.append((x, torch.empty_like(x).pin_memory(), i % 2))
+        reqs = [(srv.submit(x, y, s), x, y, s) for x, y, s in io]
+        got = _drain(srv, len(reqs))
+        assert all(r["status"] == 0 for r in got.values())
+        for rid, x, y, s in reqs:
+            banks, bps = sets[s]
+            ref = mdn.denoise_multiscale(x.cuda()[None], banks, mdn.Geometry(3, 3), bps)[0].cpu()
+            assert torch.equal(y, ref), rid
+        st = srv.stats()
+        assert st["completed"] == len(reqs)
+        assert st["tick_items"] > st["ticks"]          # stages of several requests shared ticks
+        assert st["tile_variant"] in (0, 1, 2) and min(st["variant_ms"]) > 0
+    finally:
+        srv.close()
+
+
+def test_admission_respects_the_budget(mdn):
+    sets = [_bank_set(mdn, 3, 3)]
+    one = 2 * 3 * 480 * 640 * 2 + 3 * 240 * 320 * 2 * 2 + 3 * 120 * 160 * 2 + 4096
+    budget = max(int(2.5 * one), 1 << 20)
+    srv = mdn.Server(sets, budget_bytes=budget, max_active=16, autotune=False)
+    try:
+        reqs = []
+        for i in range(6):
+            x = _frame(480, 640, 61000 + i)
+            y = torch.empty_like(x).pin_memory()
+            reqs.append((srv.submit(x, y, 0), x, y))
+        got = _drain(srv, len(reqs))
+        assert all(r["status"] == 0 for r in got.values())
+        st = srv.stats()
+        assert st["arena_peak"] <= budget
+        assert st["arena_peak"] <= 2 * one + 8192          # at most two requests fit at a time
+        big = _frame(2000, 2000, 61999)
+        with pytest.raises(mdn.MdnError) as ei:
+            srv.submit(big, torch.empty_like(big), 0)
+        assert ei.value.code == 4
+        banks, bps = sets[0]
+        for rid, x, y in reqs:
+            ref = mdn.denoise_multiscale(x.cuda()[None], banks, mdn.Geometry(3, 3), bps)[0].cpu()
+            assert torch.equal(y, ref)
+    finally:
+        srv.close()
+
+
+def test_cancel_queued_request_and_poll_timeout(mdn):
+    sets = [_bank_set(mdn, 3, 4)]
+    srv = mdn.Server(sets, budget_bytes=64 << 20, max_active=1, autotune=False)
+    try:
+        assert srv.poll(8, 50) == []                        # nothing submitted: bounded wait, no result
+        xs = [_frame(1080, 1920, 62000 + i) for i in range(10)]
+        ys = [torch.empty_like(x).pin_memory() for x in xs]
+        ids = [srv.submit(x, y, 0) for x, y in zip(xs, ys)]
+        cancelled = None
+        for rid in reversed(ids):
+            try:
+                srv.cancel(rid)
+                cancelled = rid
+                break
+            except mdn.MdnError:
+                continue
+        assert cancelled is not None
+        got = _drain(srv, len(ids))
+        assert got[cancelled]["status"] == 5
+        assert sum(r["status"] == 0 for r in got.values()) == len(ids) - 1
+        with pytest.raises(mdn.MdnError):
+            srv.cancel(ids[0])                              # already finished
+    finally:
+        srv.close()
