@@ -28,6 +28,10 @@ sys.path.insert(0, ROOT)
 
 H, W, LEVELS = 3024, 4032, 3
 METRIC = "Mpix/s 3-level denoise at 12MP"
+# DRAM bytes (read + write) of one level-0 k_level3 launch per 4032x3024 FP16
+# frame, from the ncu capture in profiles/k_level3_12mp_level0_fp16.md; set to
+# None whenever that kernel changes until it is captured again.
+LEVEL0_TRAFFIC_PER_FRAME = (91.670528 + 37.917440) * 1e6
 
 
 def _gen_frame(seed):
@@ -115,6 +119,24 @@ def measured_peaks():
             d = json.load(f)
         return d.get("hbm_gbs", 6800.0), "measured"
     return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- multi-rank
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """Maximum of a per-rank time over all ranks (rank 0 reports it)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(pixels_per_rank_step: int, steps: int, world: int, ms_max: float) -> float:
+    """Weak scaling: every rank denoises its own batch; Mpix/s of the job."""
+    return pixels_per_rank_step * steps * world / (ms_max * 1e-3) / 1e6
 
 
 # ---------------------------------------------------------------- CPU oracle
@@ -225,11 +247,8 @@ def run_gpu(args, rank, world, frames):
             step(True)
         t1.record(stream)
         torch.cuda.synchronize()
-    ms = t0.elapsed_time(t1)
+    ms = max_over_ranks(t0.elapsed_time(t1), world, dev)
     if dist is not None:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
         dist.barrier()
     pyr = [e[0].elapsed_time(e[1]) for e in evs]
     lv1 = [e[1].elapsed_time(e[2]) for e in evs]
@@ -260,17 +279,13 @@ def run_gpu(args, rank, world, frames):
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    ems = e0.elapsed_time(e1)
-    if dist is not None:
-        tt = torch.tensor([ems], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ems = float(tt.item())
+    ems = max_over_ranks(e0.elapsed_time(e1), world, dev)
 
     if rank != 0:
         return
     pix = n * H * W
-    value = pix * args.steps * world / (ms * 1e-3) / 1e6
-    e2e_value = pix * e2e_steps * world / (ems * 1e-3) / 1e6
+    value = whole_job_rate(pix, args.steps, world, ms)
+    e2e_value = whole_job_rate(pix, e2e_steps, world, ems)
     # roofline of the dominant kernel (level-0 fused filter): algorithmic bytes
     # per launch = read z^0 (6 B/px) + read u^1 (1.5 B per finest px) + write
     # u^0 (6 B/px) = 13.5 B per finest pixel
@@ -278,8 +293,10 @@ def run_gpu(args, rank, world, frames):
     bytes_lv0 = 13.5 * pix
     achieved = bytes_lv0 / t_lv0 / 1e9
     peak, peak_kind = measured_peaks()
-    # FP32 FMA issue roof of the same kernel: 294 filter FMAs per pixel
-    clk = clk_summary = clk.summary()
+    clk_summary = clk.summary()
+    # FP32 FMA roof of the same kernel: 294 filter FMAs per pixel
+    fma_rate = 294.0 * pix / t_lv0
+    fma_peak = 152 * 128 * (clk_summary["sm_mhz"] or 2070.0) * 1e6
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
@@ -291,14 +308,21 @@ def run_gpu(args, rank, world, frames):
         "gpu_launches": 4 * args.steps,
         "kernel_ms": {"pyramid": round(statistics.mean(pyr), 4), "level1": round(statistics.mean(lv1), 4),
                       "level0": round(statistics.mean(lv0), 4)},
-        "roofline": {"bound": "hbm", "kernel": "k_level (level 0)", "achieved": round(achieved, 1),
+        "roofline": {"bound": "hbm", "kernel": "k_level3 (level 0)", "achieved": round(achieved, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": None, "peak_source": peak_kind},
+                     "traffic": (round(LEVEL0_TRAFFIC_PER_FRAME * n) if LEVEL0_TRAFFIC_PER_FRAME else None),
+                     "traffic_note": "ncu DRAM read+write of a one-frame capture, scaled by frames",
+                     "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
+                     "alu_frac": round(fma_rate / fma_peak, 4), "alu_note":
+                         "294 filter FMAs per pixel vs FP32 FMA peak 152 SMs x 128 x clock (the kernel is bound "
+                         "by shared-memory wavefronts and latency, see profiles/)"},
         "e2e": {"value": round(e2e_value, 2), "unit": "Mpix/s", "h2d_bytes_per_step": int(pix * 3 * 2),
                 "d2h_bytes_per_step": int(pix * 3 * 2)},
         "clocks": {"sm_mhz": clk_summary["sm_mhz"], "sm_max_mhz": clk_summary["sm_max_mhz"],
                    "reasons": clk_summary["reasons"]},
     }
+    if args.train and world == 1:
+        line["training"] = run_training(args, dev)
     if args.serve and world == 1:
         line["serving"] = serving_subprocess(args)
     if args.cpu_baseline:
@@ -421,6 +445,68 @@ def run_serving(args, dev):
             "mean_stages_per_tick": round(st["tick_items"] / max(st["ticks"], 1), 2)}
 
 
+# ---------------------------------------------------------------- training
+
+def _gen_pair_1mp(seed):
+    import synth
+    return synth.noisy_pair(1024, 1024, seed)
+
+
+def run_training(args, dev):
+    """Bucketed Gram accumulation (sort + Gram + FP64 reduce) on config-3
+    shaped data: n x 1024x1024 pairs, sigma 25/255, cross-channel 7x7x3
+    regressors (D = 147) + 3 targets; every Gram precision.  Algorithmic
+    FLOPs per patch = Dp (Dp + 1) with Dp = 150 (the upper triangle of the
+    symmetric Gram)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import torch
+    import paper_1802_06130_gb300 as mdn
+    n = args.train_images
+    with cf.ProcessPoolExecutor(max_workers=min(n, os.cpu_count() or 1), mp_context=mp.get_context("spawn")) as ex:
+        pairs = list(ex.map(_gen_pair_1mp, [30000 + i for i in range(n)]))
+    Z = torch.tensor(np.stack([p[0] for p in pairs]), device=dev)
+    U = torch.tensor(np.stack([p[1] for p in pairs]), device=dev)
+    geom = mdn.Geometry(3, -1, 1)
+    bp = mdn.default_bparams(0)
+    npatch = n * 1024 * 1024
+    alg = npatch * 150 * 151
+    peaks = measured_tensor_peaks()
+    out = {"workload": f"{n} x 1024x1024 pairs, cross-channel 7x7x3 (D=147) + 3 targets, 216 buckets",
+           "patches": npatch, "precisions": {}}
+    for prec, name in [(0, "fp32_simt"), (1, "tf32"), (2, "bf16"), (3, "split_bf16")]:
+        ws = None
+        times = []
+        for rep in range(3):
+            s_, e_ = torch.cuda.Event(True), torch.cuda.Event(True)
+            s_.record()
+            g, c, _ = mdn.train_level_filters(Z, None, U, geom, bp, prec, lam=1e-3, solve=False, ws=ws)
+            e_.record()
+            torch.cuda.synchronize()
+            times.append(s_.elapsed_time(e_))
+        ms = min(times[1:])
+        d = {"ms": round(ms, 3), "mpatch_s": round(npatch / ms / 1e3, 1), "alg_tflops": round(alg / ms / 1e9, 2)}
+        if prec in (1, 2, 3):
+            mult = 3 if prec == 3 else 1
+            peak = peaks["tf32"] if prec == 1 else peaks["bf16"]
+            d["tensor_frac_of_peak"] = round(mult * alg / ms / 1e9 / peak, 4)
+            d["peak_tflops"] = round(peak, 1)
+        out["precisions"][name] = d
+    out["peak_source"] = peaks["source"]
+    return out
+
+
+def measured_tensor_peaks():
+    """Dense tensor peaks: measured BF16 (burst) and TF32 = BF16 x the nominal
+    ratio 1.1 / 2.25."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    bf16, src = 1900.0, "fallback"
+    if os.path.exists(p):
+        with open(p) as f:
+            bf16, src = json.load(f).get("bf16_tflops", 1900.0), "measured"
+    return {"bf16": bf16, "tf32": bf16 * 1.1 / 2.25, "source": src + " (TF32 = BF16 x 1.1/2.25 nominal)"}
+
+
 def serving_subprocess(args):
     """The serving measurement runs in a fresh process (its own CUDA context and
     host memory) so that the throughput benchmark's allocations do not colour
@@ -446,12 +532,21 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=600)
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[50, 100, 200, 400])
     ap.add_argument("--serve-only", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--no-train", dest="train", action="store_false")
+    ap.add_argument("--train-images", type=int, default=16)
+    ap.add_argument("--train-only", action="store_true", help="only the training section (profiling driver)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     args.local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.train_only:
+        import torch
+        import paper_1802_06130_gb300 as mdn
+        mdn.build()
+        print(json.dumps(run_training(args, torch.device("cuda", args.local_rank))), flush=True)
         return
     if args.serve_only:
         import torch

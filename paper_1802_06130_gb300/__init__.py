@@ -16,7 +16,7 @@ from .build import LIB as _LIB_PATH, build
 __all__ = ["build", "lib", "Geometry", "BucketParams", "default_bparams", "MdnError",
            "build_pyramid", "select_buckets", "filter_level", "denoise_multiscale",
            "denoise_workspace_bytes", "train_level_filters", "solve_bank", "regressor_len",
-           "gram_state_shape", "train_status", "Server", "F32", "F16", "YCBCR601", "RGB", "GRAM_FP32", "GRAM_TF32",
+           "gram_state_shape", "train_status", "train_cascade", "Server", "F32", "F16", "YCBCR601", "RGB", "GRAM_FP32", "GRAM_TF32",
            "GRAM_BF16", "GRAM_SPLIT_BF16"]
 
 F32, F16 = 0, 1
@@ -377,6 +377,48 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def train_cascade(noisy, clean, geom: Geometry, levels: int, bparams=None, gram_precision: int = GRAM_FP32,
+                  lam: float = 1e-3, chunk: int = 0, stream=None):
+    """Section 4 training cascade on the GPU: pyramids of the noisy and clean
+    images, then for l = L-2 .. 0 (single-scale: l = 0 only) the bucketed
+    least-squares fit of level l (mdn_train_level_filters) with the trained
+    coarser output as the coarse input, and that level's output on every
+    training image (mdn_filter_level) for the next finer level.  Base case:
+    the coarse input of level L-2 is z^{L-1}.
+
+    noisy, clean: [n][3][h][w] CUDA tensors; chunk > 0 feeds the images to
+    the Gram accumulation in groups of that many (same result up to FP64
+    summation order).  Returns (banks [K][3][D] FP32 per level, counts per
+    level)."""
+    torch = _torch()
+    single = geom.r_coarse < 0
+    L = 1 if single else levels
+    nb = max(levels - 1, 1)
+    if bparams is None:
+        bparams = [default_bparams(l) for l in range(nb)]
+    zp = [noisy] + (build_pyramid(noisy, L, stream) if L > 1 else [])
+    up = [clean] + (build_pyramid(clean, L, stream) if L > 1 else [])
+    cur = zp[L - 1] if not single else None
+    banks, counts_out = [None] * nb, [None] * nb
+    n = noisy.shape[0]
+    step = chunk if chunk > 0 else n
+    for l in range(L - 2 if L > 1 else 0, -1, -1):
+        gram = counts = None
+        for i0 in range(0, n, step):
+            sl = slice(i0, min(n, i0 + step))
+            last = i0 + step >= n
+            gram, counts, bank = train_level_filters(
+                zp[l][sl].contiguous(), cur[sl].contiguous() if cur is not None else None, up[l][sl].contiguous(),
+                geom, bparams[l], gram_precision, gram=gram, counts=counts, accumulate=gram is not None,
+                lam=lam, solve=last, stream=stream)
+        banks[l], counts_out[l] = bank, counts
+        if l > 0 or not single:
+            out = torch.empty_like(zp[l])
+            filter_level(zp[l], cur, bank, geom, bparams[l], out=out, stream=stream)
+            cur = out
+    return banks, counts_out
 
 
 def solve_bank(gram, counts, geom: Geometry, lam: float = 1e-3, stream=None):

@@ -305,3 +305,33 @@ def test_solve_bank_matches_oracle(mdn):
     assert int(status.item()) == 0
     np.testing.assert_allclose(_np(bank), ref, rtol=1e-5, atol=1e-6)
     assert (counts == 0).any()   # the pooled path is exercised
+
+
+# ------------------------------------------------------------ A7 cascade
+
+@pytest.mark.parametrize("case", [("single", O.Geometry(2, -1), 1), ("three", O.Geometry(3, 3), 3)],
+                         ids=lambda c: c[0])
+def test_train_cascade_matches_oracle(mdn, case):
+    """Section 4 cascade on the GPU (pyramids, per-level least squares, the
+    trained level's output feeding the next finer level) vs the oracle's
+    cascade on the same pairs; FP32 storage, FP32 Gram.  Then the GPU banks
+    denoise a held-out image."""
+    _, geom, levels = case
+    pairs = [synth.noisy_pair(128, 128, 1000 + i) for i in range(3)]
+    zs = [O.round_storage(p[0], "f32") for p in pairs]
+    us = [O.round_storage(p[1], "f32") for p in pairs]
+    ref_banks, ref_counts = O.train_cascade(zs, us, geom, levels, mirror32=True, storage="f32")
+    Z, U = _tt(np.stack(zs), "f32"), _tt(np.stack(us), "f32")
+    banks, counts = mdn.train_cascade(Z, U, _geom(mdn, geom), levels, chunk=2)
+    torch.cuda.synchronize()
+    for l in range(len(ref_banks)):
+        c = counts[l].cpu().numpy()
+        assert c.sum() == ref_counts[l].sum()
+        # buckets agree except at threshold-band pixels (about 0.1 %)
+        assert np.abs(c - ref_counts[l]).sum() <= 2e-3 * c.sum(), l
+        e = np.linalg.norm(_np(banks[l]) - ref_banks[l]) / np.linalg.norm(ref_banks[l])
+        assert e < 2e-3, (l, e)
+    z, u = synth.noisy_pair(128, 128, 2000)
+    out = mdn.denoise_multiscale(_tt(z, "f32")[None], banks, _geom(mdn, geom),
+                                 [mdn.default_bparams(l) for l in range(len(banks))])
+    assert np.mean((_np(out[0]) - u) ** 2) < 0.3 * np.mean((z - u) ** 2)
