@@ -20,4 +20,16 @@ template <> __device__ __forceinline__ void st_f<__half>(__half* p, int64_t i, f
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
+// four consecutive elements as floats (8-byte aligned FP16, 16-byte aligned FP32)
+__device__ __forceinline__ void ld4(const __half* p, float* out) {
+    const uint2 q = __ldg(reinterpret_cast<const uint2*>(p));
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
+    out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
+}
+__device__ __forceinline__ void ld4(const float* p, float* out) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+    out[0] = q.x; out[1] = q.y; out[2] = q.z; out[3] = q.w;
+}
+
 }  // namespace mdn

@@ -103,13 +103,16 @@ __device__ __forceinline__ int bucket_of(float a, float b, float c, const SelPar
     } else {
         bool upper = (vy > 0.f) || (vy == 0.f && vx > 0.f);
         if (!upper) { vx = -vx; vy = -vy; }
-        int cnt = 0;
-        for (int k = 0; k < half - 1; ++k) {
-            // cross(b_k, v) >= 0  <=>  psi >= boundary k+1
-            float cr = __fmaf_rn(sp.bcos[k], vy, -__fmul_rn(sp.bsin[k], vx));
-            cnt += cr >= 0.f ? 1 : 0;
+        // number of boundaries k+1 (k < half-1) with cross(b_k, v) >= 0, i.e.
+        // psi >= boundary; the test is monotone in k (boundaries are 2 pi /
+        // n_angle apart), so a binary search finds the first failing k
+        int lo = 0, hi = half - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            const float cr = __fmaf_rn(sp.bcos[mid], vy, -__fmul_rn(sp.bsin[mid], vx));
+            if (cr >= 0.f) lo = mid + 1; else hi = mid;
         }
-        abin = (upper ? 0 : half) + cnt;
+        abin = (upper ? 0 : half) + lo;
     }
     int sb = 0, cb = 0;
     for (int t = 0; t < sp.nthr_s; ++t) sb += (sp.strength_thr[t] <= s1) ? 1 : 0;
@@ -434,10 +437,11 @@ template <> __device__ __forceinline__ void load_slot<float>(const unsigned char
     h[0] = a.x; h[1] = a.y; h[2] = a.z; h[3] = a.w; h[4] = b.x; h[5] = b.y; h[6] = b.z; h[7] = b.w;
 }
 
-// bank [K][3][D] (regressor order) -> shared-memory slots, by nthreads threads
+// bank [K][3][D] (regressor order) -> shared-memory slots, by nthreads
+// threads; bucket k goes to slot block pos[k] (pos == nullptr: block k)
 template <int RF, int RC, bool CROSS, typename TB>
 __device__ __forceinline__ void load_bank_slots(const TB* __restrict__ bank, int K, unsigned char* bank_s, int tid,
-                                                int nthreads) {
+                                                int nthreads, const uint8_t* pos = nullptr) {
     using G = Geo<RF, RC, CROSS>;
     using SL = Slots<RF, RC, CROSS>;
     constexpr int SB = SlotBytes<TB>::B;
@@ -459,7 +463,33 @@ __device__ __forceinline__ void load_bank_slots(const TB* __restrict__ bank, int
             if (e < NFX) src = G::NCH * G::PC + cc * G::PF + e * NFX + dx;
         }
         TB v = src >= 0 ? bank[((int64_t)k * 3 + oc) * G::D + src] : TB(0.f);
-        reinterpret_cast<TB*>(bank_s + (size_t)k * BSTRIDE + slot * SB)[e] = v;
+        const int kp = pos ? pos[k] : k;
+        reinterpret_cast<TB*>(bank_s + (size_t)kp * BSTRIDE + slot * SB)[e] = v;
+    }
+}
+
+// Placement of bucket k = (a * ns + s) * nc + c in the shared-memory bank:
+// with a per-bucket stride of 43 x 16 bytes, block p starts in 16-byte bank
+// group 3p mod 8.  Choosing p = pi(k) with pi(k) = 3 g mod 8 (mod 8), g = a + 2s
+// + 4c, puts every two buckets within +-1 of each other in angle, strength and
+// coherence bin (the ones that sit side by side in a quarter-warp) in
+// different bank groups.  pi is a bijection when every residue of 3g mod 8 has
+// K/8 buckets (true for n_angle divisible by 8, ns, nc <= 3); otherwise the
+// identity is used.  Built once per CTA by `nthreads` threads into pos[256].
+__device__ __forceinline__ void build_bucket_placement(const SelParams& sp, int K, uint8_t* pos, int tid,
+                                                       int nthreads) {
+    const int ns = sp.n_strength, nc = sp.n_coherence;
+    const bool ok = (sp.n_angle % 8 == 0) && ns <= 3 && nc <= 3 && K % 8 == 0 && K <= 256;
+    for (int k = tid; k < K; k += nthreads) {
+        if (!ok) { pos[k] = (uint8_t)k; continue; }
+        auto cls = [&](int q) {
+            const int a = q / (ns * nc), s = (q / nc) % ns, c = q % nc;
+            return (3 * ((a + 2 * s + 4 * c) & 7)) & 7;
+        };
+        const int r = cls(k);
+        int rank = 0;
+        for (int q = 0; q < k; ++q) rank += cls(q) == r ? 1 : 0;
+        pos[k] = (uint8_t)(8 * rank + r);
     }
 }
 
@@ -740,7 +770,10 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
     unsigned char* bank_s = smem + front_bytes<RC>();
     const int tid = threadIdx.x;
 
-    v2::load_bank_slots<RF, RC, CROSS, TB>(bank, K, bank_s, tid, NT);   // once per persistent CTA
+    __shared__ uint8_t bpos[256];   // bucket -> slot block (bank-group aware)
+    v2::build_bucket_placement(sp, K, bpos, tid, NT);
+    __syncthreads();
+    v2::load_bank_slots<RF, RC, CROSS, TB>(bank, K, bank_s, tid, NT, bpos);   // once per persistent CTA
     __syncthreads();
 
     const int tiles_x = (W + TW - 1) / TW, tiles_y = (H + TH - 1) / TH;
@@ -751,25 +784,49 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
     if (warp >= NCW) {
         // =============================== producer ===============================
         const int pt = tid - NC;
+        const int pw = pt >> 5;                       // producer warp 0..NPW-1
         const float wv[5] = {w0, w1, w2, w1, w0};
         // Register prefetch: the inputs of tile i+1 are loaded while tile i's
         // selector runs, so global latency overlaps shared-memory work.
-        constexpr int NZ = (3 * ZH * ZW + NP - 1) / NP;
+        // Interior tiles (halo inside the image, rows 8-byte aligned) load
+        // 4-element chunks covering columns x0-4 .. x0+35 without clamping;
+        // border tiles use clamped scalar loads.
+        constexpr int NCHUNK = 10;                    // 4-element chunks per staged row
+        constexpr int NZV = (3 * ZH * NCHUNK + NP - 1) / NP;
+        constexpr int NZS = (3 * ZH * ZW + NP - 1) / NP;
+        constexpr int NZ = NZV * 4 > NZS ? NZV * 4 : NZS;
         constexpr int NU = RC >= 0 ? (UH * UW + NP - 1) / NP : 0;
         float zreg[NZ];
         float ureg[NU > 0 ? NU : 1][3];
+        // vector loads need 4-element-aligned rows and an aligned image base
+        const bool rows_aligned = (W % 4) == 0 && (reinterpret_cast<uintptr_t>(z) & 15) == 0;
+        auto interior = [&](int x0, int y0) {
+            return rows_aligned && x0 - 4 >= 0 && x0 + TW + 4 <= W && y0 - HZ >= 0 && y0 + TH + HZ <= H;
+        };
         auto fetch = [&](int64_t tile) {
             const int img = (int)(tile / ((int64_t)tiles_x * tiles_y));
             const int trem = (int)(tile % ((int64_t)tiles_x * tiles_y));
             const int x0 = (trem % tiles_x) * TW, y0 = (trem / tiles_x) * TH;
             const TS* zi = z + (int64_t)img * 3 * H * W;
+            if (interior(x0, y0)) {
 #pragma unroll
-            for (int j = 0; j < NZ; ++j) {
-                const int e = pt + j * NP;
-                if (e < 3 * ZH * ZW) {
-                    int c = e / (ZH * ZW), r = (e / ZW) % ZH, q = e % ZW;
-                    int gy = clampi(y0 - HZ + r, 0, H - 1), gx = clampi(x0 - HZ + q, 0, W - 1);
-                    zreg[j] = ld_f(zi, ((int64_t)c * H + gy) * W + gx);
+                for (int j = 0; j < NZV; ++j) {
+                    const int e = pt + j * NP;
+                    if (e < 3 * ZH * NCHUNK) {
+                        const int c = e / (ZH * NCHUNK), r = (e / NCHUNK) % ZH, k = e % NCHUNK;
+                        const TS* src = zi + ((int64_t)c * H + (y0 - HZ + r)) * W + (x0 - 4 + 4 * k);
+                        ld4(src, zreg + 4 * j);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < NZS; ++j) {
+                    const int e = pt + j * NP;
+                    if (e < 3 * ZH * ZW) {
+                        int c = e / (ZH * ZW), r = (e / ZW) % ZH, q = e % ZW;
+                        int gy = clampi(y0 - HZ + r, 0, H - 1), gx = clampi(x0 - HZ + q, 0, W - 1);
+                        zreg[j] = ld_f(zi, ((int64_t)c * H + gy) * W + gx);
+                    }
                 }
             }
             if constexpr (RC >= 0) {
@@ -800,10 +857,28 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
             const int img = (int)(tile / ((int64_t)tiles_x * tiles_y));
             const int trem = (int)(tile % ((int64_t)tiles_x * tiles_y));
             const int x0 = (trem % tiles_x) * TW, y0 = (trem / tiles_x) * TH;
+            const bool inner = interior(x0, y0);
+            if (inner) {
+                // chunk k covers staged columns 4k-1 .. 4k+2 (column -1 and >= ZW dropped)
 #pragma unroll
-            for (int j = 0; j < NZ; ++j) {
-                const int e = pt + j * NP;
-                if (e < 3 * ZH * ZW) zs[e] = zreg[j];
+                for (int j = 0; j < NZV; ++j) {
+                    const int e = pt + j * NP;
+                    if (e < 3 * ZH * NCHUNK) {
+                        const int cr = e / NCHUNK, k = e % NCHUNK;
+                        float* row = zs + cr * ZW;
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) {
+                            const int q = 4 * k - 1 + t;
+                            if (q >= 0 && q < ZW) row[q] = zreg[4 * j + t];
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < NZS; ++j) {
+                    const int e = pt + j * NP;
+                    if (e < 3 * ZH * ZW) zs[e] = zreg[j];
+                }
             }
             if constexpr (RC >= 0) {
 #pragma unroll
@@ -818,49 +893,69 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
             }
             if (i + 1 < T) fetch(tile + gridDim.x);
             bar_sync(BAR_PROD, NP);
-            for (int e = pt; e < PH * PW; e += NP) {
-                int r = e / PW, q = e % PW;
-                int cy = clampi(y0 - 2 + r, 0, H - 1), cx = clampi(x0 - 2 + q, 0, W - 1);
-                int ly = cy - (y0 - HZ), lx = cx - (x0 - HZ);
-                int lxm = clampi(cx - 1, 0, W - 1) - (x0 - HZ), lxp = clampi(cx + 1, 0, W - 1) - (x0 - HZ);
-                int lym = clampi(cy - 1, 0, H - 1) - (y0 - HZ), lyp = clampi(cy + 1, 0, H - 1) - (y0 - HZ);
-                float gx[3], gy[3];
+            // products of central-difference gradients, one row per warp pass,
+            // lanes along x (two passes for the 36 columns)
+            for (int r = pw; r < PH; r += NPW) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const float* zc = zs + c * ZH * ZW;
-                    gx[c] = __fmul_rn(__fsub_rn(zc[ly * ZW + lxp], zc[ly * ZW + lxm]), 0.5f);
-                    gy[c] = __fmul_rn(__fsub_rn(zc[lyp * ZW + lx], zc[lym * ZW + lx]), 0.5f);
-                }
-                float pxx = __fmul_rn(gx[0], gx[0]), pxy = __fmul_rn(gx[0], gy[0]), pyy = __fmul_rn(gy[0], gy[0]);
+                for (int qq = 0; qq < 2; ++qq) {
+                    const int q = lane + 32 * qq;
+                    if (q >= PW) continue;
+                    int ly, lx, lxm, lxp, lym, lyp;
+                    if (inner) {
+                        ly = r + 1; lx = q + 1;
+                        lxm = lx - 1; lxp = lx + 1; lym = ly - 1; lyp = ly + 1;
+                    } else {
+                        const int cy = clampi(y0 - 2 + r, 0, H - 1), cx = clampi(x0 - 2 + q, 0, W - 1);
+                        ly = cy - (y0 - HZ); lx = cx - (x0 - HZ);
+                        lxm = clampi(cx - 1, 0, W - 1) - (x0 - HZ); lxp = clampi(cx + 1, 0, W - 1) - (x0 - HZ);
+                        lym = clampi(cy - 1, 0, H - 1) - (y0 - HZ); lyp = clampi(cy + 1, 0, H - 1) - (y0 - HZ);
+                    }
+                    float gx[3], gy[3];
 #pragma unroll
-                for (int c = 1; c < 3; ++c) {
-                    pxx = __fmaf_rn(gx[c], gx[c], pxx);
-                    pxy = __fmaf_rn(gx[c], gy[c], pxy);
-                    pyy = __fmaf_rn(gy[c], gy[c], pyy);
+                    for (int c = 0; c < 3; ++c) {
+                        const float* zc = zs + c * ZH * ZW;
+                        gx[c] = __fmul_rn(__fsub_rn(zc[ly * ZW + lxp], zc[ly * ZW + lxm]), 0.5f);
+                        gy[c] = __fmul_rn(__fsub_rn(zc[lyp * ZW + lx], zc[lym * ZW + lx]), 0.5f);
+                    }
+                    float pxx = __fmul_rn(gx[0], gx[0]), pxy = __fmul_rn(gx[0], gy[0]), pyy = __fmul_rn(gy[0], gy[0]);
+#pragma unroll
+                    for (int c = 1; c < 3; ++c) {
+                        pxx = __fmaf_rn(gx[c], gx[c], pxx);
+                        pxy = __fmaf_rn(gx[c], gy[c], pxy);
+                        pyy = __fmaf_rn(gy[c], gy[c], pyy);
+                    }
+                    const int e = r * PW + q;
+                    ps[e] = pxx; ps[PH * PW + e] = pxy; ps[2 * PH * PW + e] = pyy;
                 }
-                ps[e] = pxx; ps[PH * PW + e] = pxy; ps[2 * PH * PW + e] = pyy;
             }
             bar_sync(BAR_PROD, NP);
-            for (int e = pt; e < 3 * PH * TW; e += NP) {
-                int f = e / (PH * TW), r = (e / TW) % PH, q = e % TW;
-                const float* p = ps + f * PH * PW + r * PW + q;
+            // horizontal smoothing pass: one (field, row) per warp pass, lanes along x
+            for (int fr = pw; fr < 3 * PH; fr += NPW) {
+                const float* p = ps + fr * PW + lane;
                 float acc = __fmul_rn(wv[0], p[0]);
 #pragma unroll
                 for (int u = 1; u < 5; ++u) acc = __fmaf_rn(wv[u], p[u], acc);
-                hs[e] = acc;
+                hs[fr * TW + lane] = acc;
             }
-            for (int e = pt; e < ZH * ZW; e += NP) {
-                float a, b, c;
-                rgb_to_work(zs[e], zs[ZH * ZW + e], zs[2 * ZH * ZW + e], color, a, b, c);
-                zs[e] = a; zs[ZH * ZW + e] = b; zs[2 * ZH * ZW + e] = c;
+            // RGB tile -> working colour space
+            for (int r = pw; r < ZH; r += NPW) {
+#pragma unroll
+                for (int qq = 0; qq < 2; ++qq) {
+                    const int q = lane + 32 * qq;
+                    if (q >= ZW) continue;
+                    const int e = r * ZW + q;
+                    float a, b, c;
+                    rgb_to_work(zs[e], zs[ZH * ZW + e], zs[2 * ZH * ZW + e], color, a, b, c);
+                    zs[e] = a; zs[ZH * ZW + e] = b; zs[2 * ZH * ZW + e] = c;
+                }
             }
             bar_sync(BAR_PROD, NP);
-            for (int e = pt; e < TH * TW; e += NP) {
-                int r = e / TW, q = e % TW;
+            // vertical pass, features, bucket: one row per warp pass, lanes along x
+            for (int r = pw; r < TH; r += NPW) {
                 float t3[3];
 #pragma unroll
                 for (int f = 0; f < 3; ++f) {
-                    const float* p = hs + f * PH * TW + r * TW + q;
+                    const float* p = hs + f * PH * TW + r * TW + lane;
                     float acc = __fmul_rn(wv[0], p[0]);
 #pragma unroll
                     for (int v = 1; v < 5; ++v) acc = __fmaf_rn(wv[v], p[v * TW], acc);
@@ -868,8 +963,8 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
                 }
                 int k = bucket_of(t3[0], t3[1], t3[2], sp);
                 k = k < K ? k : K - 1;
-                bk[e] = (uint8_t)k;
-                int gy = y0 + r, gx = x0 + q;
+                bk[r * TW + lane] = bpos[k];   // consumers only need the bank block
+                const int gy = y0 + r, gx = x0 + lane;
                 if (bmap && gy < H && gx < W) bmap[((int64_t)img * H + gy) * W + gx] = (uint8_t)k;
             }
             bar_arrive(BAR_FULL0 + s, NT);
