@@ -270,10 +270,9 @@ size_t mdn_train_workspace_bytes(int64_t n, int64_t h, int64_t w, const mdn_geom
     int D = regressor_len(*geom);
     int G = geom->cross_channel ? 1 : 3, T = geom->cross_channel ? 3 : 1;
     size_t solve = solve_ws_bytes(K, G, D, T);
-    size_t tr = align256((size_t)n * h * w) +                           // bucket map
-                train_ws_bytes(n * h * w, K, G, D + T, gram_precision);  // sort + partials
-    // working-space copies of z, target (and coarse)
-    tr += 2 * align256((size_t)n * 3 * h * w * 4) + align256((size_t)n * 3 * ((h + 1) / 2) * ((w + 1) / 2) * 4);
+    const int P = geom->r_coarse > geom->r_fine ? geom->r_coarse : geom->r_fine;
+    size_t tr = align256((size_t)n * h * w) +                                   // bucket map
+                train_ws_bytes(n, h, w, P, geom->r_coarse >= 0, K, G, D + T, gram_precision);  // working planes, sort, partials
     return tr > solve + 256 ? tr : solve + 256;
 }
 

@@ -65,7 +65,7 @@ struct TrainArgs {
     void* ws;
     size_t ws_bytes;
 };
-size_t train_ws_bytes(int64_t npix, int K, int G, int Dp, int precision);
+size_t train_ws_bytes(int64_t n, int64_t h, int64_t w, int P, bool coarse, int K, int G, int Dp, int precision);
 int launch_gram(const TrainArgs& a, cudaStream_t s);
 size_t solve_ws_bytes(int K, int G, int D, int T);
 int launch_solve(const double* gram, const int64_t* counts, int K, int G, int D, int T,

@@ -9,9 +9,9 @@
 //   Gram           per chunk: A^T A of the gathered rows A = [regressor|target
 //                  shifted by a per-channel constant | 1] (SIMT FP32 here,
 //                  tcgen05 variants in k_gram_tc.cu), written as FP32 partials
-//   k_reduce_centered  FP64 sum of a bucket's partials in chunk order
-//                  (deterministic) with the exact centring correction, added
-//                  into gram[k][g]; counts[k] += n_k
+//   k_reduce_sum / k_center  FP64 sum of a bucket's partials in group and
+//                  chunk order (deterministic), then the exact centring
+//                  correction, added into gram[k][g]; counts[k] += n_k
 //   k_pool/k_chol  ridge solve (G_xx/n + lambda I) h = G_xy/n by Cholesky in
 //                  FP64 shared memory, one CTA per (bucket, group); empty
 //                  buckets copy the pooled solution
@@ -24,22 +24,42 @@ namespace trn {
 
 // ---------------------------------------------------------------- helpers
 
+// Storage RGB -> FP32 working colour space, shifted by each channel's centring
+// constant, written with a replicated border of P pixels: out is
+// [n][3][h + 2P][w + 2P] and out(y + P, x + P) takes the input at
+// (clamp(y, 0, h-1), clamp(x, 0, w-1)).  round_tf32: round the shifted value
+// to TF32 (nearest, ties away), the operand precision of the TF32 Gram.
+__device__ __forceinline__ float round_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
 template <typename TS>
-__global__ void k_to_work(const TS* __restrict__ in, float* __restrict__ out, int64_t hw, int64_t n, int color) {
+__global__ void k_to_work(const TS* __restrict__ in, float* __restrict__ out, int h, int w, int64_t n, int P,
+                          int color, int tf32) {
+    const int Hp = h + 2 * P, Wp = w + 2 * P;
+    const int64_t hwp = (int64_t)Hp * Wp, hw = (int64_t)h * w;
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= hw * n) return;
-    int64_t img = i / hw, p = i % hw;
-    const TS* s = in + img * 3 * hw + p;
+    if (i >= hwp * n) return;
+    const int64_t img = i / hwp, q = i % hwp;
+    const int yp = (int)(q / Wp), xp = (int)(q % Wp);
+    const int y = clampi(yp - P, 0, h - 1), x = clampi(xp - P, 0, w - 1);
+    const TS* s = in + img * 3 * hw + (int64_t)y * w + x;
     float r = ld_f(s, 0), g = ld_f(s, hw), b = ld_f(s, 2 * hw);
-    float y, cb, cr;
-    if (color == MDN_RGB) { y = r; cb = g; cr = b; }
+    float yy, cb, cr;
+    if (color == MDN_RGB) { yy = r; cb = g; cr = b; }
     else {
-        y = 0.299f * r + 0.587f * g + 0.114f * b;
+        yy = 0.299f * r + 0.587f * g + 0.114f * b;
         cb = -0.168735892f * r - 0.331264108f * g + 0.5f * b;
         cr = 0.5f * r - 0.418687589f * g - 0.081312411f * b;
     }
-    float* d = out + img * 3 * hw + p;
-    d[0] = y; d[hw] = cb; d[2 * hw] = cr;
+    yy -= (float)channel_center(0, color);
+    cb -= (float)channel_center(1, color);
+    cr -= (float)channel_center(2, color);
+    if (tf32) { yy = round_tf32(yy); cb = round_tf32(cb); cr = round_tf32(cr); }
+    float* d = out + img * 3 * hwp + q;
+    d[0] = yy; d[hwp] = cb; d[2 * hwp] = cr;
 }
 
 __global__ void k_hist(const uint8_t* __restrict__ bmap, int64_t npix, int K, int* __restrict__ blockhist) {
@@ -53,47 +73,127 @@ __global__ void k_hist(const uint8_t* __restrict__ bmap, int64_t npix, int K, in
     for (int k = threadIdx.x; k < K; k += blockDim.x) blockhist[(int64_t)blockIdx.x * K + k] = h[k];
 }
 
-// One CTA.  offs[b][k] = start of block b's bucket-k run in the sorted list;
-// bstart[k], bcount[k]; chunk table entries (k, begin, end); nchunks_out.
-__global__ void k_scan(const int* __restrict__ blockhist, int nblk, int K, int* __restrict__ offs,
-                       int64_t* __restrict__ bstart, int64_t* __restrict__ bcount, int4* __restrict__ chunks,
-                       int maxchunks, int chunk_rows, int* __restrict__ nchunks_out) {
-    __shared__ int64_t tot[MDN_MAX_K];
-    __shared__ int64_t cstart[MDN_MAX_K + 1];
+// Bucket offsets in three short passes over the per-block histograms
+// (blocks of SORT_CHUNK pixels, grouped into SCAN_SEGS segments):
+//   k_segsum  segsum[s][k] = sum of blockhist over segment s's blocks
+//   k_scan    bstart[k], bcount[k] and segoff[s][k] = start of segment s's
+//             bucket-k run in the sorted list (one CTA)
+//   k_offs    offs[b][k] = start of block b's bucket-k run
+constexpr int SCAN_SEGS = 64;
+
+__global__ void k_segsum(const int* __restrict__ blockhist, int nblk, int K, int seglen, int* __restrict__ segsum) {
+    const int sg = blockIdx.x, b0 = sg * seglen, b1 = min(b0 + seglen, nblk);
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        int64_t s = 0;
-        for (int b = 0; b < nblk; ++b) s += blockhist[(int64_t)b * K + k];
-        tot[k] = s;
+        int t = 0;
+        for (int b = b0; b < b1; ++b) t += blockhist[(int64_t)b * K + k];
+        segsum[sg * K + k] = t;
+    }
+}
+
+__global__ void k_scan(const int* __restrict__ segsum, int nseg, int K, int64_t* __restrict__ bstart,
+                       int64_t* __restrict__ bcount, int* __restrict__ segoff) {
+    __shared__ int64_t tot[MDN_MAX_K], st[MDN_MAX_K];
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        int64_t t = 0;
+        for (int sg = 0; sg < nseg; ++sg) t += segsum[sg * K + k];
+        tot[k] = t;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        int64_t run = 0, c = 0;
-        for (int k = 0; k < K; ++k) {
-            bstart[k] = run;
-            bcount[k] = tot[k];
-            cstart[k] = c;
-            run += tot[k];
-            c += (tot[k] + chunk_rows - 1) / chunk_rows;
-        }
-        cstart[K] = c;
-        *nchunks_out = (int)c;
+        int64_t run = 0;
+        for (int k = 0; k < K; ++k) { st[k] = run; run += tot[k]; }
     }
     __syncthreads();
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        int64_t run = bstart[k];
-        for (int b = 0; b < nblk; ++b) {
-            offs[(int64_t)b * K + k] = (int)run;
-            run += blockhist[(int64_t)b * K + k];
-        }
-        int64_t c = cstart[k];
-        for (int64_t r = 0; r < tot[k]; r += chunk_rows, ++c) {
-            if (c >= maxchunks) break;
-            int64_t e = r + chunk_rows < tot[k] ? r + chunk_rows : tot[k];
-            chunks[c] = make_int4(k, (int)(bstart[k] + r), (int)(bstart[k] + e), 0);
+        bstart[k] = st[k];
+        bcount[k] = tot[k];
+        int64_t run = st[k];
+        for (int sg = 0; sg < nseg; ++sg) {
+            segoff[sg * K + k] = (int)run;
+            run += segsum[sg * K + k];
         }
     }
-    // unused tail entries
-    for (int64_t c = cstart[K] + threadIdx.x; c < maxchunks; c += blockDim.x) chunks[c] = make_int4(-1, 0, 0, 0);
+}
+
+__global__ void k_offs(const int* __restrict__ blockhist, const int* __restrict__ segoff, int nblk, int K, int seglen,
+                       int* __restrict__ offs) {
+    const int sg = blockIdx.x, b0 = sg * seglen, b1 = min(b0 + seglen, nblk);
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        int run = segoff[sg * K + k];
+        for (int b = b0; b < b1; ++b) {
+            offs[(int64_t)b * K + k] = run;
+            run += blockhist[(int64_t)b * K + k];
+        }
+    }
+}
+
+// exclusive prefix sum over the threads of a CTA (blockDim.x <= 256)
+__device__ int block_exclusive_scan(int v, int* tmp, int* total) {
+    const int t = threadIdx.x;
+    tmp[t] = v;
+    __syncthreads();
+    for (int d = 1; d < blockDim.x; d <<= 1) {
+        const int add = t >= d ? tmp[t - d] : 0;
+        __syncthreads();
+        tmp[t] += add;
+        __syncthreads();
+    }
+    const int incl = tmp[t];
+    *total = tmp[blockDim.x - 1];
+    __syncthreads();
+    return incl - v;
+}
+
+// Chunk table of one pixel group (CTA per group).  A group is the pixel-index
+// range [g * GB, (g + 1) * GB): since the sorted list is ordered by bucket and
+// then by pixel index, the group's rows of bucket k form one contiguous run.
+// Group g's chunks, in bucket order, go to chunks[g * cap ...], each
+// (k, begin, end, w): quantum mode (tensor cores) cuts the runs at every
+// multiple of Q = max(ceil(group rows / ncta), minq) of the group's virtual row
+// position and records w = the CTA that owns the chunk (position / Q);
+// otherwise runs are cut into pieces of at most chunk_rows rows (w = 0).
+__global__ void __launch_bounds__(256) k_chunks(const int* __restrict__ offs, const int64_t* __restrict__ bstart,
+                                                const int64_t* __restrict__ bcount, int K, int nblk, int bpg,
+                                                int64_t npix, int64_t GB, int quantum_mode, int ncta, int minq,
+                                                int chunk_rows, int cap, int4* __restrict__ chunks,
+                                                int* __restrict__ gcount) {
+    __shared__ int tmp[256];
+    __shared__ int total;
+    const int g = blockIdx.x, k = threadIdx.x;
+    int start = 0, len = 0;
+    if (k < K) {
+        const int b0 = g * bpg, b1 = b0 + bpg;
+        start = offs[(int64_t)b0 * K + k];
+        const int end = b1 < nblk ? offs[(int64_t)b1 * K + k] : (int)(bstart[k] + bcount[k]);
+        len = end - start;
+    }
+    const int v = block_exclusive_scan(len, tmp, &total);
+    const int64_t grows = npix - g * GB < GB ? npix - g * GB : GB;
+    int Q = chunk_rows;
+    if (quantum_mode) {
+        const int64_t q = (grows + ncta - 1) / ncta;
+        Q = (int)(q > minq ? q : minq);
+    }
+    int nck = 0;
+    if (len > 0) {
+        if (quantum_mode) {
+            const int inner = (v + len + Q - 1) / Q - 1 - v / Q;   // multiples of Q in (v, v + len)
+            nck = (inner > 0 ? inner : 0) + 1;
+        } else {
+            nck = (len + Q - 1) / Q;
+        }
+    }
+    const int coff = block_exclusive_scan(nck, tmp, &total);
+    if (k < K) {
+        int j = coff;
+        for (int r = v; r < v + len && j < cap; ++j) {
+            int e = quantum_mode ? (r / Q + 1) * Q : r + Q;
+            if (e > v + len) e = v + len;
+            chunks[(int64_t)g * cap + j] = make_int4(k, start + (r - v), start + (e - v), quantum_mode ? r / Q : 0);
+            r = e;
+        }
+    }
+    if (k == 0) gcount[g] = total < cap ? total : cap;   // the capacity bounds the total by construction
 }
 
 // Stable scatter: pixels of a block are ranked in index order within their
@@ -135,10 +235,11 @@ __global__ void __launch_bounds__(256) k_scatter(const uint8_t* __restrict__ bma
 // Gram of one chunk, FP32 products/accumulation, 4x4 register blocks of the
 // upper triangle of every group's Dp x Dp matrix.
 __global__ void __launch_bounds__(256) k_gram_simt(GatherArgs ga, const int4* __restrict__ chunks,
-                                                    const int* __restrict__ sorted, float* __restrict__ partial) {
+                                                    const int* __restrict__ nchunks, const int* __restrict__ sorted,
+                                                    float* __restrict__ partial) {
     extern __shared__ __align__(16) unsigned char smem[];
+    if ((int)blockIdx.x >= *nchunks) return;
     const int4 ch = chunks[blockIdx.x];
-    if (ch.x < 0) return;
     const int Dq = ga.Dp + 1, G = ga.G, DPs = ga.Dp4;   // Dq: features + ones column
     float* As = reinterpret_cast<float*>(smem);        // [G][RB][DPs]
     int* coltab = reinterpret_cast<int*>(As + (size_t)G * GRAM_RB * DPs);   // [G][Dq]
@@ -198,41 +299,54 @@ __global__ void __launch_bounds__(256) k_gram_simt(GatherArgs ga, const int4* __
     }
 }
 
-// FP64 reduction of a bucket's chunk partials in chunk order (deterministic):
-// partials are (Dq = Dp + 1)^2 upper triangles of the shifted rows with the
-// ones column last; the exact centring correction is
-// G_ij = S_ij + c_i s_j + c_j s_i + n c_i c_j, s_i = S_{i,ones}, n = S_{ones,ones}.
-__global__ void k_reduce_centered(const float* __restrict__ partial, const int4* __restrict__ chunks,
-                                  const int* __restrict__ nchunks, const int64_t* __restrict__ bcount, int K, int G,
-                                  int Dp, int D, int rf, int rc, int cross, int color, double* __restrict__ gram,
-                                  int64_t* __restrict__ counts) {
+// FP64 reduction of a bucket's chunk partials in group order, then chunk order
+// (deterministic), in two passes.  Partials are (Dq = Dp + 1)^2 upper
+// triangles of the shifted rows with the ones column last.  Group g's chunks
+// are chunks[g * cap, g * cap + gcount[g]), in bucket order.
+//   k_reduce_sum  S[k][g] = sum of the bucket's partials (upper triangle)
+//   k_center      the exact centring correction
+//                 G_ij = S_ij + c_i s_j + c_j s_i + n c_i c_j,
+//                 s_i = S_{i,ones}, n = S_{ones,ones}, added into gram[k][g]
+__global__ void k_reduce_sum(const float* __restrict__ partial, const int4* __restrict__ chunks,
+                             const int* __restrict__ gcount, int ngroups, int cap, int G, int Dq,
+                             double* __restrict__ S) {
     const int k = blockIdx.y;
-    const int Dq = Dp + 1;
     const int64_t entq = (int64_t)G * Dq * Dq;
-    __shared__ int c0, c1;
-    if (threadIdx.x == 0) {
-        int nc = *nchunks, lo = 0, hi = nc;
-        while (lo < hi) { int mid = (lo + hi) / 2; if (chunks[mid].x < k) lo = mid + 1; else hi = mid; }
-        c0 = lo;
+    __shared__ int lo_s[GRAM_MAX_GROUPS], hi_s[GRAM_MAX_GROUPS];
+    for (int g = threadIdx.x; g < ngroups; g += blockDim.x) {
+        const int base = g * cap, nc = gcount[g];
+        int lo = 0, hi = nc;
+        while (lo < hi) { int mid = (lo + hi) / 2; if (chunks[base + mid].x < k) lo = mid + 1; else hi = mid; }
+        const int c0 = lo;
         hi = nc;
-        while (lo < hi) { int mid = (lo + hi) / 2; if (chunks[mid].x <= k) lo = mid + 1; else hi = mid; }
-        c1 = lo;
+        while (lo < hi) { int mid = (lo + hi) / 2; if (chunks[base + mid].x <= k) lo = mid + 1; else hi = mid; }
+        lo_s[g] = base + c0;
+        hi_s[g] = base + lo;
     }
     __syncthreads();
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < entq; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)((e / Dq) % Dq), j = (int)(e % Dq);
+        if (i > j) continue;
+        double acc = 0.0;
+        for (int gr = 0; gr < ngroups; ++gr)
+            for (int c = lo_s[gr]; c < hi_s[gr]; ++c) acc += (double)partial[(size_t)c * entq + e];
+        S[(size_t)k * entq + e] = acc;
+    }
+}
+
+__global__ void k_center(const double* __restrict__ S, const int64_t* __restrict__ bcount, int G, int Dp, int D,
+                         int rf, int rc, int cross, int color, double* __restrict__ gram,
+                         int64_t* __restrict__ counts) {
+    const int k = blockIdx.y;
+    const int Dq = Dp + 1;
     const int64_t ent = (int64_t)G * Dp * Dp;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ent; e += (int64_t)gridDim.x * blockDim.x) {
         const int g = (int)(e / ((int64_t)Dp * Dp));
         const int i = (int)((e / Dp) % Dp), j = (int)(e % Dp);
         if (i > j) continue;
-        double sij = 0.0, si = 0.0, sj = 0.0, n = 0.0;
-        const size_t base = (size_t)g * Dq * Dq;
-        for (int c = c0; c < c1; ++c) {
-            const float* P = partial + (size_t)c * entq + base;
-            sij += (double)P[(size_t)i * Dq + j];
-            si += (double)P[(size_t)i * Dq + Dp];
-            sj += (double)P[(size_t)j * Dq + Dp];
-            n += (double)P[(size_t)Dp * Dq + Dp];
-        }
+        const double* Sq = S + ((size_t)k * G + g) * Dq * Dq;
+        const double sij = Sq[(size_t)i * Dq + j], si = Sq[(size_t)i * Dq + Dp], sj = Sq[(size_t)j * Dq + Dp];
+        const double n = Sq[(size_t)Dp * Dq + Dp];
         const double ci = channel_center(feature_channel(i, g, D, rf, rc, cross), color);
         const double cj = channel_center(feature_channel(j, g, D, rf, rc, cross), color);
         const double v = sij + ci * sj + cj * si + n * ci * cj;
@@ -361,77 +475,108 @@ __global__ void __launch_bounds__(256) k_chol(const double* __restrict__ gram, c
 
 using namespace trn;
 
-size_t train_ws_bytes(int64_t npix, int K, int G, int Dp, int precision) {
-    (void)precision;
-    int64_t nblk = (npix + SORT_CHUNK - 1) / SORT_CHUNK;
-    int64_t maxch = npix / GRAM_CHUNK + K + 1;
+size_t train_ws_bytes(int64_t n, int64_t h, int64_t w, int P, bool coarse, int K, int G, int Dp, int precision) {
+    const int64_t npix = n * h * w, hc = (h + 1) / 2, wc = (w + 1) / 2;
+    const GramGroups gq = gram_groups(n, h, w, P, coarse, K, precision != MDN_GRAM_FP32);
+    const int64_t nblk = (npix + SORT_CHUNK - 1) / SORT_CHUNK;
+    const int64_t nent = (int64_t)gq.ngroups * gq.cap;
     size_t b = 0;
+    b += align256(sizeof(float) * 3 * n * (h + 2 * P) * (w + 2 * P));    // z, border P
+    b += align256(sizeof(float) * 3 * npix);                               // target
+    b += align256(sizeof(float) * 3 * n * (hc + 2 * P) * (wc + 2 * P));  // coarse, border P
     b += align256(sizeof(int) * nblk * K) * 2;        // blockhist, offs
+    b += align256(sizeof(int) * SCAN_SEGS * K) * 2;   // segsum, segoff
     b += align256(sizeof(int64_t) * K) * 2;           // bstart, bcount
-    b += align256(sizeof(int4) * maxch) + 256;        // chunks, nchunks
+    b += align256(sizeof(int4) * nent) + align256(sizeof(int) * gq.ngroups);   // chunk tables, counts
     b += align256(sizeof(int) * (npix > 0 ? npix : 1));   // sorted
-    b += align256(sizeof(float) * maxch * G * (Dp + 1) * (Dp + 1));  // partials (tensor-core layout is Dp+1)
+    b += align256(sizeof(float) * nent * G * (Dp + 1) * (Dp + 1));  // partials (Dp + 1 with the ones column)
+    b += align256(sizeof(double) * K * G * (Dp + 1) * (Dp + 1));    // FP64 bucket sums
     return b;
 }
 
 int launch_gram(const TrainArgs& a, cudaStream_t s) {
     const int64_t hw = a.h * a.w, npix = a.n * hw;
-    const int64_t hwc = a.hc * a.wc;
+    const int P = gram_border(a.geom);
+    const int64_t Hp = a.h + 2 * P, Wp = a.w + 2 * P, Hcp = a.hc + 2 * P, Wcp = a.wc + 2 * P;
     if (a.Dp + 1 > GRAM_MAX_DP) return fail(MDN_ESHAPE, "train: regressor too long (D + T must be <= 159)");
-    // carve the workspace
+    if (3 * a.n * Hp * Wp >= (int64_t(1) << 31))
+        return fail(MDN_ESHAPE, "train: padded working planes exceed 2^31 elements");
+    const bool tensor = a.precision != MDN_GRAM_FP32;
+    const GramGroups gq = gram_groups(a.n, a.h, a.w, P, a.coarse != nullptr, a.K, tensor);
+    // carve the workspace (the layout of train_ws_bytes)
     char* p = (char*)a.ws;
     auto take = [&](size_t bytes) { char* r = p; p += align256(bytes); return r; };
-    float* zw = (float*)take(sizeof(float) * 3 * npix);
+    float* zw = (float*)take(sizeof(float) * 3 * a.n * Hp * Wp);
     float* tw = (float*)take(sizeof(float) * 3 * npix);
-    float* cw = (float*)take(sizeof(float) * 3 * a.n * hwc);
-    int64_t nblk = (npix + SORT_CHUNK - 1) / SORT_CHUNK;
-    int64_t maxch = npix / GRAM_CHUNK + a.K + 1;
+    float* cw = (float*)take(sizeof(float) * 3 * a.n * Hcp * Wcp);
+    const int64_t nblk = (npix + SORT_CHUNK - 1) / SORT_CHUNK;
+    const int64_t nent = (int64_t)gq.ngroups * gq.cap;
     int* blockhist = (int*)take(sizeof(int) * nblk * a.K);
     int* offs = (int*)take(sizeof(int) * nblk * a.K);
+    int* segsum = (int*)take(sizeof(int) * SCAN_SEGS * a.K);
+    int* segoff = (int*)take(sizeof(int) * SCAN_SEGS * a.K);
     int64_t* bstart = (int64_t*)take(sizeof(int64_t) * a.K);
     int64_t* bcount = (int64_t*)take(sizeof(int64_t) * a.K);
-    int4* chunks = (int4*)take(sizeof(int4) * maxch);
-    int* nchunks = (int*)take(sizeof(int));
+    int4* chunks = (int4*)take(sizeof(int4) * nent);
+    int* gcount = (int*)take(sizeof(int) * gq.ngroups);
     int* sorted = (int*)take(sizeof(int) * (npix > 0 ? npix : 1));
-    float* partial = (float*)take(sizeof(float) * maxch * a.G * (a.Dp + 1) * (a.Dp + 1));
+    float* partial = (float*)take(sizeof(float) * nent * a.G * (a.Dp + 1) * (a.Dp + 1));
+    double* bsum = (double*)take(sizeof(double) * a.K * a.G * (a.Dp + 1) * (a.Dp + 1));
     if ((size_t)(p - (char*)a.ws) > a.ws_bytes) return fail(MDN_EWORKSPACE, "train: workspace too small");
 
-    const int TB = 256;
-    auto conv = [&](const void* in, float* out, int64_t hw_, int64_t cnt) {
-        unsigned g = (unsigned)((hw_ * cnt + TB - 1) / TB);
-        if (a.dtype == MDN_F32) k_to_work<float><<<g, TB, 0, s>>>((const float*)in, out, hw_, cnt, a.geom.color);
-        else k_to_work<__half><<<g, TB, 0, s>>>((const __half*)in, out, hw_, cnt, a.geom.color);
+    constexpr int TB = 256;
+    auto conv = [&](const void* in, float* out, int64_t hh, int64_t ww, int pad) {
+        const int64_t cnt = a.n * (hh + 2 * pad) * (ww + 2 * pad);
+        unsigned g = (unsigned)((cnt + TB - 1) / TB);
+        const int tf32 = a.precision == MDN_GRAM_TF32;
+        if (a.dtype == MDN_F32)
+            k_to_work<float><<<g, TB, 0, s>>>((const float*)in, out, (int)hh, (int)ww, a.n, pad, a.geom.color, tf32);
+        else
+            k_to_work<__half><<<g, TB, 0, s>>>((const __half*)in, out, (int)hh, (int)ww, a.n, pad, a.geom.color, tf32);
     };
-    conv(a.z, zw, hw, a.n);
-    conv(a.target, tw, hw, a.n);
-    if (a.coarse) conv(a.coarse, cw, hwc, a.n);
+    conv(a.z, zw, a.h, a.w, P);
+    conv(a.target, tw, a.h, a.w, 0);
+    if (a.coarse) conv(a.coarse, cw, a.hc, a.wc, P);
+    // sort: per-block histograms, bucket offsets, stable scatter
+    const int seglen = (int)((nblk + SCAN_SEGS - 1) / SCAN_SEGS);
+    const int nseg = (int)((nblk + seglen - 1) / seglen);
     k_hist<<<(unsigned)nblk, TB, 0, s>>>(a.buckets, npix, a.K, blockhist);
-    k_scan<<<1, TB, 0, s>>>(blockhist, (int)nblk, a.K, offs, bstart, bcount, chunks, (int)maxch, GRAM_CHUNK, nchunks);
+    k_segsum<<<nseg, TB, 0, s>>>(blockhist, (int)nblk, a.K, seglen, segsum);
+    k_scan<<<1, TB, 0, s>>>(segsum, nseg, a.K, bstart, bcount, segoff);
+    k_offs<<<nseg, TB, 0, s>>>(blockhist, segoff, (int)nblk, a.K, seglen, offs);
     k_scatter<<<(unsigned)nblk, TB, 0, s>>>(a.buckets, npix, a.K, offs, sorted);
+    // chunk tables: tensor cores one CTA per SM, each taking a share of every group
+    const int ncta = num_sms() < GRAM_MAX_CTAS ? num_sms() : GRAM_MAX_CTAS;
+    k_chunks<<<gq.ngroups, TB, 0, s>>>(offs, bstart, bcount, a.K, (int)nblk, (int)(gq.GB / SORT_CHUNK), npix, gq.GB,
+                                       tensor ? 1 : 0, ncta, GRAM_MIN_QUANTUM, GRAM_CHUNK, gq.cap, chunks, gcount);
     int rc = check_launch("train: sort");
     if (rc) return rc;
 
     GatherArgs ga{};
     ga.zw = zw; ga.tw = tw; ga.cw = a.coarse ? cw : nullptr;
     ga.h = (int)a.h; ga.w = (int)a.w; ga.hc = (int)a.hc; ga.wc = (int)a.wc;
+    ga.P = P; ga.Hp = (int)Hp; ga.Wp = (int)Wp; ga.Hcp = (int)Hcp; ga.Wcp = (int)Wcp;
     ga.rf = a.geom.r_fine; ga.rc = a.geom.r_coarse; ga.cross = a.geom.cross_channel; ga.color = a.geom.color;
     ga.D = a.D; ga.T = a.T; ga.G = a.G; ga.Dp = a.Dp; ga.Dp4 = (a.Dp + 1 + 3) / 4 * 4;
-    if (a.precision == MDN_GRAM_FP32) {
+    if (!tensor) {
         size_t sm = sizeof(float) * (size_t)a.G * GRAM_RB * ga.Dp4 + sizeof(int) * a.G * (a.Dp + 1);
         const int nb = (a.Dp + 1 + 3) / 4;
         if (a.G * nb * (nb + 1) / 2 > 8 * 256) return fail(MDN_ESHAPE, "train: Gram too large for the SIMT path");
         cudaError_t ea = cudaFuncSetAttribute(k_gram_simt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (ea != cudaSuccess) return cuda_fail(ea, "k_gram_simt: shared memory attribute");
-        k_gram_simt<<<(unsigned)maxch, 256, sm, s>>>(ga, chunks, sorted, partial);
+        k_gram_simt<<<(unsigned)gq.cap, 256, sm, s>>>(ga, chunks, gcount, sorted, partial);
         if ((rc = check_launch("k_gram_simt"))) return rc;
     } else {
-        rc = launch_gram_tc(ga, a.precision, chunks, (int)maxch, sorted, partial, s);
+        rc = launch_gram_tc(ga, a.precision, chunks, gcount, gq.ngroups, gq.cap, sorted, partial, ncta, s);
         if (rc) return rc;
     }
-    dim3 rg((unsigned)((a.G * a.Dp * a.Dp + 255) / 256), (unsigned)a.K);
-    k_reduce_centered<<<rg, 256, 0, s>>>(partial, chunks, nchunks, bcount, a.K, a.G, a.Dp, a.D, a.geom.r_fine,
-                                         a.geom.r_coarse, a.geom.cross_channel, a.geom.color, a.gram, a.counts);
-    return check_launch("k_reduce_centered");
+    const int Dq = a.Dp + 1;
+    dim3 rg1((unsigned)((a.G * Dq * Dq + 255) / 256), (unsigned)a.K);
+    k_reduce_sum<<<rg1, 256, 0, s>>>(partial, chunks, gcount, gq.ngroups, gq.cap, a.G, Dq, bsum);
+    dim3 rg2((unsigned)((a.G * a.Dp * a.Dp + 255) / 256), (unsigned)a.K);
+    k_center<<<rg2, 256, 0, s>>>(bsum, bcount, a.G, a.Dp, a.D, a.geom.r_fine, a.geom.r_coarse, a.geom.cross_channel,
+                                 a.geom.color, a.gram, a.counts);
+    return check_launch("k_reduce_sum / k_center");
 }
 
 size_t solve_ws_bytes(int K, int G, int D, int T) {
