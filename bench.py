@@ -181,6 +181,39 @@ def run_reference(args, rank, world):
 
 # ---------------------------------------------------------------- GPU arm
 
+def run_variants(mdn, x, geom, dev, stream, reps=10):
+    """The rest of the 12 MP metric run, timing only (same frames, denoise via
+    mdn_denoise_multiscale with preallocated output and workspace, L2 flushed
+    before every timed call, median): FP16 and FP32 storage, batch 1 and 8,
+    and the 4-level pipeline of the 12 MP batch."""
+    import torch
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    res = {}
+    for name, xv, levels in [("f16_batch1_3level", x[:1], 3), ("f32_batch1_3level", x[:1].float(), 3),
+                             ("f32_batch8_3level", x.float(), 3), ("f16_batch8_4level", x, 4)]:
+        banks = [torch.tensor(b, dtype=torch.float16, device=dev) for b in random_banks(7, nb=levels - 1)]
+        bps = [mdn.default_bparams(l) for l in range(levels - 1)]
+        nv = xv.shape[0]
+        dt = mdn.F16 if xv.dtype == torch.float16 else mdn.F32
+        ws = torch.empty(mdn.denoise_workspace_bytes(nv, H, W, levels, dt), dtype=torch.uint8, device=dev)
+        out = torch.empty_like(xv)
+        for _ in range(2):
+            mdn.denoise_multiscale(xv, banks, geom, bps, out=out, ws=ws)
+        times = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            mdn.denoise_multiscale(xv, banks, geom, bps, out=out, ws=ws)
+            b.record(stream)
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+        ms = statistics.median(times)
+        res[name] = {"ms": round(ms, 4), "mpix_s": round(nv * H * W / ms / 1e3, 1)}
+        del xv, out, ws
+    return res
+
+
 def run_gpu(args, rank, world, frames):
     import torch
     import paper_1802_06130_gb300 as mdn
@@ -283,6 +316,7 @@ def run_gpu(args, rank, world, frames):
 
     if rank != 0:
         return
+    variants = run_variants(mdn, x, geom, dev, stream)
     pix = n * H * W
     value = whole_job_rate(pix, args.steps, world, ms)
     e2e_value = whole_job_rate(pix, e2e_steps, world, ems)
@@ -321,6 +355,7 @@ def run_gpu(args, rank, world, frames):
         "clocks": {"sm_mhz": clk_summary["sm_mhz"], "sm_max_mhz": clk_summary["sm_max_mhz"],
                    "reasons": clk_summary["reasons"]},
     }
+    line["variants"] = variants
     if args.train and world == 1:
         line["training"] = run_training(args, dev)
     if args.serve and world == 1:
@@ -431,7 +466,9 @@ def run_serving(args, dev):
                 stream.synchronize()
                 lat_b.append((time.perf_counter() - t0 - arr[k]) * 1e3)
             span_b = time.perf_counter() - t0
-            results.append({"rate_rps": rate, "requests": nreq, "server": srv_line,
+            results.append({"rate_rps": rate, "requests": nreq,
+                            "label": "saturation sweep (offered load above capacity)" if rate >= 1000 else "offered load",
+                            "server": srv_line,
                             "per_image": {"p50_ms": round(float(np.percentile(lat_b, 50)), 3),
                                           "p99_ms": round(float(np.percentile(lat_b, 99)), 3),
                                           "mpix_s": round(pix / span_b / 1e6, 1)}})
@@ -453,20 +490,24 @@ def _gen_pair_1mp(seed):
 
 
 def run_training(args, dev):
-    """Bucketed Gram accumulation (sort + Gram + FP64 reduce) on config-3
-    shaped data: n x 1024x1024 pairs, sigma 25/255, cross-channel 7x7x3
-    regressors (D = 147) + 3 targets; every Gram precision.  Algorithmic
-    FLOPs per patch = Dp (Dp + 1) with Dp = 150 (the upper triangle of the
-    symmetric Gram)."""
+    """Bucketed Gram accumulation (sort + Gram + FP64 reduce) on config-3 data:
+    n x 1024x1024 pairs (n = 256 by default: 268,435,456 patches), sigma
+    25/255, cross-channel 7x7x3 regressors (D = 147) + 3 targets; every Gram
+    precision.  Algorithmic FLOPs per patch = Dp (Dp + 1) with Dp = 150 (the
+    upper triangle of the symmetric Gram).  Each tensor-core precision's Gram
+    and solved bank are compared with the FP32 CUDA-core path on the same
+    patches (relative Frobenius; per bucket for n_k >= 10 D)."""
     import concurrent.futures as cf
     import multiprocessing as mp
     import torch
     import paper_1802_06130_gb300 as mdn
     n = args.train_images
+    Z = torch.empty((n, 3, 1024, 1024), dtype=torch.float32, device=dev)
+    U = torch.empty_like(Z)
     with cf.ProcessPoolExecutor(max_workers=min(n, os.cpu_count() or 1), mp_context=mp.get_context("spawn")) as ex:
-        pairs = list(ex.map(_gen_pair_1mp, [30000 + i for i in range(n)]))
-    Z = torch.tensor(np.stack([p[0] for p in pairs]), device=dev)
-    U = torch.tensor(np.stack([p[1] for p in pairs]), device=dev)
+        for i, (z, u) in enumerate(ex.map(_gen_pair_1mp, [30000 + i for i in range(n)])):
+            Z[i].copy_(torch.from_numpy(z))
+            U[i].copy_(torch.from_numpy(u))
     geom = mdn.Geometry(3, -1, 1)
     bp = mdn.default_bparams(0)
     npatch = n * 1024 * 1024
@@ -474,6 +515,7 @@ def run_training(args, dev):
     peaks = measured_tensor_peaks()
     out = {"workload": f"{n} x 1024x1024 pairs, cross-channel 7x7x3 (D=147) + 3 targets, 216 buckets",
            "patches": npatch, "precisions": {}}
+    ref = None
     for prec, name in [(0, "fp32_simt"), (1, "tf32"), (2, "bf16"), (3, "split_bf16")]:
         ws = None
         times = []
@@ -491,7 +533,21 @@ def run_training(args, dev):
             peak = peaks["tf32"] if prec == 1 else peaks["bf16"]
             d["tensor_frac_of_peak"] = round(mult * alg / ms / 1e9 / peak, 4)
             d["peak_tflops"] = round(peak, 1)
+        bank, status = mdn.solve_bank(g, c, geom, 1e-3)
+        gn, bn, cn = g.cpu().numpy(), bank.cpu().numpy().astype(np.float64), c.cpu().numpy()
+        if ref is None:
+            ref = (gn, bn, cn)
+        else:
+            big = np.nonzero(cn >= 10 * 147)[0]
+            per = [np.linalg.norm(bn[k] - ref[1][k]) / np.linalg.norm(ref[1][k]) for k in big]
+            d["vs_fp32_simt"] = {"gram_rel": float(f"{np.linalg.norm(gn - ref[0]) / np.linalg.norm(ref[0]):.3g}"),
+                                 "bank_rel": float(f"{np.linalg.norm(bn - ref[1]) / np.linalg.norm(ref[1]):.3g}"),
+                                 "bank_rel_per_bucket_median": float(f"{np.median(per):.3g}"),
+                                 "bank_rel_per_bucket_max": float(f"{np.max(per):.3g}"),
+                                 "buckets_compared": int(len(big)), "counts_equal": bool(np.array_equal(cn, ref[2]))}
+        d["solve_status"] = int(status.item())
         out["precisions"][name] = d
+        del g, c, bank
     out["peak_source"] = peaks["source"]
     return out
 
@@ -529,11 +585,11 @@ def main():
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-serve", dest="serve", action="store_false")
-    ap.add_argument("--serve-requests", type=int, default=600)
-    ap.add_argument("--serve-rates", type=float, nargs="+", default=[50, 100, 200, 400])
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[50, 100, 200, 400, 1600])
     ap.add_argument("--serve-only", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-train", dest="train", action="store_false")
-    ap.add_argument("--train-images", type=int, default=16)
+    ap.add_argument("--train-images", type=int, default=256)
     ap.add_argument("--train-only", action="store_true", help="only the training section (profiling driver)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
