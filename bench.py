@@ -395,7 +395,7 @@ def run_serving(args, dev):
         frames[(h, w)] = [torch.tensor(synth.noisy_pair(h, w, 50100 + i + h)[0], dtype=torch.float16).pin_memory()
                           for i in range(2)]
     nreq = args.serve_requests
-    out_pool = {hw: [torch.empty((3, *hw), dtype=torch.float16).pin_memory() for _ in range(64)] for hw in SERVE_SIZES}
+    out_pool = {hw: [torch.empty((3, *hw), dtype=torch.float16).pin_memory() for _ in range(8)] for hw in SERVE_SIZES}
     geom = mdn.Geometry(3, 3)
     results = []
     srv = mdn.Server(sets, budget_bytes=80 << 30, max_active=64, autotune=True)
@@ -408,7 +408,14 @@ def run_serving(args, dev):
             pix = sum(hw[0] * hw[1] for hw, _, _, _ in pick)
             # ---- server: submissions at the arrival times, a poller thread
             # (blocking poll, GIL released in the C call) timestamps completions
-            lat, inflight, slot = [], {}, {hw: 0 for hw in SERVE_SIZES}
+            # output buffers: a LIFO pool of 8 per size (the most recently
+            # released host buffer is reused first; past 8 in flight of one size
+            # buffers are shared round-robin, the bench does not read outputs).
+            # Device writes into many distinct pinned buffers in turn (64 per
+            # size) grew the device-to-host copy time up to ~10x over a run on
+            # the Grace host; the per-image path reuses one buffer per size.
+            lat, inflight, spill = [], {}, {hw: 0 for hw in SERVE_SIZES}
+            free = {hw: list(range(len(out_pool[hw]) - 1, -1, -1)) for hw in SERVE_SIZES}
             internal, by_size = [], {hw: [] for hw in SERVE_SIZES}
             lock = threading.Lock()
             stop = [False]
@@ -419,7 +426,9 @@ def run_serving(args, dev):
                     for r in srv.poll(64, 50):
                         t = time.perf_counter() - t0
                         with lock:
-                            a, hw_ = inflight.pop(r["id"])
+                            a, hw_, bi = inflight.pop(r["id"])
+                            if bi not in free[hw_]:
+                                free[hw_].append(bi)
                             lat.append((t - a) * 1e3)
                             by_size[hw_].append((t - a) * 1e3)
                             internal.append(r["done_ms"] - r["submit_ms"])
@@ -433,11 +442,14 @@ def run_serving(args, dev):
                 if wait > 0:
                     time.sleep(wait)
                 hw, sg, L, f = pick[i]
-                y = out_pool[hw][slot[hw] % 64]
-                slot[hw] += 1
                 with lock:
-                    rid = srv.submit(frames[hw][f], y, set_of[(sg, L)])
-                    inflight[rid] = (arr[i], hw)
+                    if free[hw]:
+                        bi = free[hw].pop()
+                    else:
+                        bi = spill[hw] % len(out_pool[hw])
+                        spill[hw] += 1
+                    rid = srv.submit(frames[hw][f], out_pool[hw][bi], set_of[(sg, L)])
+                    inflight[rid] = (arr[i], hw, bi)
             th.join(timeout=120)
             stop[0] = True
             span = time.perf_counter() - t0
