@@ -222,6 +222,26 @@ int mdn_train_level_filters(const void* noisy_lvl, const void* coarse_out, const
  * written and the result must be discarded), else 0. */
 int mdn_train_status(int32_t* flag);
 
+/* Training-set augmentation by the 8 flips / 90-degree rotations of the
+ * pairs (Section 5 of the paper), applied to accumulated Gram sums instead of
+ * re-gathering 8x the patches.  Transform t = rot + 4 * flip (rotate the
+ * image by 90 degrees rot times, then mirror the columns if flip) maps the
+ * patch of every pixel to the same patch with its taps permuted, and moves the
+ * pixel's orientation bin a to a + rot * n_angle / 2 (mod n_angle), then to
+ * n_angle - 1 - a if flip (strength and coherence bins are invariant).  So
+ *   gram_out[k'][g] = sum_t P_t gram_in[k_t][g] P_t^T,  counts_out[k'] = sum_t counts_in[k_t]
+ * with k_t the bucket that t maps to k' and P_t the tap permutation (targets
+ * and, cross-channel, the channel order are unchanged).  Equal to training on
+ * the 8 transformed pairs except at pixels whose orientation lies on a bin
+ * boundary or is undefined (a zero structure tensor).  Single-level
+ * geometries only (geom->r_coarse < 0): the pyramid of a mirrored image is
+ * not the mirrored pyramid when a level has even size.  gram_in, counts_in:
+ * device, as filled by mdn_train_level_filters; gram_out, counts_out: device,
+ * same sizes, overwritten, not aliasing the inputs.  bp->n_angle must be
+ * even.  Asynchronous on stream.  MDN_EINVAL / MDN_ESHAPE on bad arguments. */
+int mdn_augment_dihedral(const double* gram_in, const int64_t* counts_in, const mdn_geometry* geom,
+                         const mdn_bucket_params* bp, double* gram_out, int64_t* counts_out, void* stream);
+
 /* Ridge solve per bucket and group in FP64 on the GPU:
  * h = (G_xx / n_k + lambda I)^{-1} (G_xy / n_k) by Cholesky; buckets with
  * n_k = 0 take the pooled filter solved from sum_k G_k.  bank_out: FP32

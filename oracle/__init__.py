@@ -13,6 +13,9 @@ written as plain Python loops in the paper's order:
 * ``gram_accumulate`` / ``solve_bank`` -- Eqs. 5-6: per-bucket least squares
 * ``train_cascade``      -- Section 4: train level L-1 first, apply it, feed
                             its output to the next finer level
+* ``dihedral`` / ``gram_accumulate_dihedral`` -- Section 5's training-set
+                            augmentation by flips and 90-degree rotations,
+                            by materialising the 8 transformed pairs
 
 Precision: FP64 throughout, except ``mirror32=True`` which evaluates the
 pyramid and the structure tensor/features in the documented FP32 order (for
@@ -355,3 +358,47 @@ def train_cascade(noisy_list, clean_list, geom: Geometry, levels: int, bparams=N
                                           sel[i], banks[l], geom), storage)
                for i in range(len(noisy_list))]
     return banks, stats
+
+
+# ---------------------------------------------------------------- augmentation
+
+def dihedral(img, t: int):
+    """Transform t = rot + 4 * flip (t in 0..7) of a [C][H][W] image, one of
+    the 8 flips / 90-degree rotations the paper augments its training pairs
+    with (Section 5): rotate by 90 degrees `rot` times (numpy's rot90 on the
+    (row, column) axes), then, if flip, mirror the columns."""
+    r = np.rot90(np.asarray(img), t % 4, axes=(1, 2))
+    if t >= 4:
+        r = r[:, :, ::-1]
+    return np.ascontiguousarray(r)
+
+
+def dihedral_bucket(bucket, t: int, bp: BucketParams):
+    """The bucket map of transform t of an image, from the image's own map.
+    The structure tensor turns with the image, so the minor eigenvector's
+    orientation theta moves by pi/2 per 90-degree rotation (bin a -> a + n/2
+    mod n) and to pi - theta under the mirror (a -> n - 1 - a); strength and
+    coherence are eigenvalue functions and do not change.  (Exact away from
+    bin boundaries and the undefined orientation of a zero tensor.)  The map
+    itself is transformed like the image."""
+    n = bp.n_angle
+    m = (len(bp.strength_thr) + 1) * (len(bp.coherence_thr) + 1)
+    b = np.asarray(bucket).astype(np.int64)
+    a, rest = b // m, b % m
+    a = (a + (t % 4) * (n // 2)) % n
+    if t >= 4:
+        a = n - 1 - a
+    return dihedral((a * m + rest).astype(np.uint8)[None], t)[0]
+
+
+def gram_accumulate_dihedral(z, target, bucket, K: int, geom: Geometry, bp: BucketParams, gram=None, counts=None):
+    """Gram sums of one single-level pair augmented by the 8 dihedral
+    transforms: each transformed pair (z_t, target_t) accumulated with its
+    bucket map (dihedral_bucket).  The plain definition of training on the
+    flipped and rotated copies."""
+    if geom.r_coarse >= 0:
+        raise ValueError("gram_accumulate_dihedral: single-level geometry only")
+    for t in range(8):
+        gram, counts = gram_accumulate(dihedral(z, t), None, dihedral(target, t), dihedral_bucket(bucket, t, bp),
+                                       K, geom, gram, counts)
+    return gram, counts

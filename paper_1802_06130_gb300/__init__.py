@@ -122,6 +122,7 @@ def lib():
             "mdn_solve_workspace_bytes": (sz, [G, i32]),
             "mdn_train_status": (C.c_int, [C.POINTER(C.c_int32)]),
             "mdn_solve_bank": (C.c_int, [vp, vp, G, i32, C.c_double, vp, vp, vp, sz, vp]),
+            "mdn_augment_dihedral": (C.c_int, [vp, vp, G, B, vp, vp, vp]),
             "mdn_server_create": (C.c_int, [C.POINTER(ServerCfg), C.POINTER(BankSet), i32, C.POINTER(vp)]),
             "mdn_server_submit": (C.c_int, [vp, vp, vp, i64, i64, i32, C.POINTER(C.c_uint64)]),
             "mdn_server_cancel": (C.c_int, [vp, C.c_uint64]),
@@ -380,7 +381,7 @@ class Server:
 
 
 def train_cascade(noisy, clean, geom: Geometry, levels: int, bparams=None, gram_precision: int = GRAM_FP32,
-                  lam: float = 1e-3, chunk: int = 0, stream=None):
+                  lam: float = 1e-3, chunk: int = 0, augment: bool = False, stream=None):
     """Section 4 training cascade on the GPU: pyramids of the noisy and clean
     images, then for l = L-2 .. 0 (single-scale: l = 0 only) the bucketed
     least-squares fit of level l (mdn_train_level_filters) with the trained
@@ -390,10 +391,13 @@ def train_cascade(noisy, clean, geom: Geometry, levels: int, bparams=None, gram_
 
     noisy, clean: [n][3][h][w] CUDA tensors; chunk > 0 feeds the images to
     the Gram accumulation in groups of that many (same result up to FP64
-    summation order).  Returns (banks [K][3][D] FP32 per level, counts per
-    level)."""
+    summation order).  augment (single-level geometry): train on the 8 flips /
+    90-degree rotations of every pair, by mdn_augment_dihedral on the Gram
+    sums.  Returns (banks [K][3][D] FP32 per level, counts per level)."""
     torch = _torch()
     single = geom.r_coarse < 0
+    if augment and not single:
+        raise ValueError("train_cascade: augment needs a single-level geometry (r_coarse < 0)")
     L = 1 if single else levels
     nb = max(levels - 1, 1)
     if bparams is None:
@@ -412,13 +416,27 @@ def train_cascade(noisy, clean, geom: Geometry, levels: int, bparams=None, gram_
             gram, counts, bank = train_level_filters(
                 zp[l][sl].contiguous(), cur[sl].contiguous() if cur is not None else None, up[l][sl].contiguous(),
                 geom, bparams[l], gram_precision, gram=gram, counts=counts, accumulate=gram is not None,
-                lam=lam, solve=last, stream=stream)
+                lam=lam, solve=last and not augment, stream=stream)
+        if augment:
+            gram, counts = augment_dihedral(gram, counts, geom, bparams[l], stream=stream)
+            bank, _ = solve_bank(gram, counts, geom, lam, stream=stream)
         banks[l], counts_out[l] = bank, counts
         if l > 0 or not single:
             out = torch.empty_like(zp[l])
             filter_level(zp[l], cur, bank, geom, bparams[l], out=out, stream=stream)
             cur = out
     return banks, counts_out
+
+
+def augment_dihedral(gram, counts, geom: Geometry, bp: BucketParams, stream=None):
+    """Gram sums and counts of the 8 dihedral transforms of the training pairs
+    (mdn_augment_dihedral; single-level geometry) -> (gram, counts), new tensors."""
+    torch = _torch()
+    gout = torch.empty_like(gram)
+    cout = torch.empty_like(counts)
+    _check(lib().mdn_augment_dihedral(_dev(gram, "gram"), _dev(counts, "counts"), C.byref(geom), C.byref(bp),
+                                      _dev(gout, "gram_out"), _dev(cout, "counts_out"), _stream(stream)))
+    return gout, cout
 
 
 def solve_bank(gram, counts, geom: Geometry, lam: float = 1e-3, stream=None):

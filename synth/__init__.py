@@ -12,7 +12,7 @@ an oriented sinusoid of period 4-32 px, over a per-channel linear-gradient
 background, clipped to [0, 1].  Images are planar float32 ``[3][H][W]`` RGB.
 """
 from .images import (clean_image, awgn, signal_dependent_noise, gain_field,
-                     noisy_pair, batch_pairs)
+                     quantize8, noisy_pair, batch_pairs)
 
 __all__ = ["clean_image", "awgn", "signal_dependent_noise", "gain_field",
-           "noisy_pair", "batch_pairs"]
+           "quantize8", "noisy_pair", "batch_pairs"]

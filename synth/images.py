@@ -135,12 +135,24 @@ def signal_dependent_noise(clean: np.ndarray, a: float, b: float, seed: int,
     return (clean + sd * n).astype(np.float32)
 
 
+def quantize8(img: np.ndarray) -> np.ndarray:
+    """8-bit storage of an image in [0, 1]: clamp, round to the nearest
+    multiple of 1/255 (ties to even), float32."""
+    return (np.rint(np.clip(img, 0.0, 1.0) * 255.0) / 255.0).astype(np.float32)
+
+
 def noisy_pair(h: int, w: int, seed: int, sigma: float = 25.0 / 255.0,
                model: str = "awgn"):
-    """(noisy, clean) float32 [3][h][w] pair from one seed."""
+    """(noisy, clean) float32 [3][h][w] pair from one seed.  Models: "awgn"
+    (float, no clamp), "awgn8" (8-bit clean image, AWGN, then 8-bit
+    quantisation with clamping, like noisy 8-bit photographs), "camera"
+    (signal-dependent noise with a smooth gain field)."""
     u = clean_image(h, w, seed)
     if model == "awgn":
         z = awgn(u, sigma, seed)
+    elif model == "awgn8":
+        u = quantize8(u)
+        z = quantize8(awgn(u, sigma, seed))
     elif model == "camera":
         z = signal_dependent_noise(u, 0.01, (10.0 / 255.0) ** 2, seed,
                                    gain_field(h, w, seed))

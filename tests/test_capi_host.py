@@ -81,6 +81,19 @@ def test_bad_arguments_rejected_without_device(L):
     rc = L.mdn_train_level_filters(C.c_void_p(16), None, C.c_void_p(16), 0, 1, 8, 8, C.byref(mdn.Geometry(2, -1)),
                                    C.byref(bp), 9, 0, C.c_void_p(8), C.c_void_p(8), 1e-3, None, None, 0, None)
     assert rc == 1 and b"precision" in L.mdn_last_error()
+    # dihedral augmentation: null, aliasing, multiscale geometry, odd angle count
+    g1, bp0 = mdn.Geometry(2, -1), mdn.default_bparams(0)
+    rc = L.mdn_augment_dihedral(None, C.c_void_p(16), C.byref(g1), C.byref(bp0), C.c_void_p(32), C.c_void_p(48), None)
+    assert rc == 1 and b"null" in L.mdn_last_error()
+    rc = L.mdn_augment_dihedral(C.c_void_p(16), C.c_void_p(16), C.byref(g1), C.byref(bp0), C.c_void_p(16),
+                                C.c_void_p(48), None)
+    assert rc == 1 and b"alias" in L.mdn_last_error()
+    rc = L.mdn_augment_dihedral(C.c_void_p(16), C.c_void_p(24), C.byref(mdn.Geometry(3, 3)), C.byref(bp0),
+                                C.c_void_p(32), C.c_void_p(48), None)
+    assert rc == 2 and b"single-level" in L.mdn_last_error()
+    rc = L.mdn_augment_dihedral(C.c_void_p(16), C.c_void_p(24), C.byref(g1), C.byref(mdn.BucketParams(23)),
+                                C.c_void_p(32), C.c_void_p(48), None)
+    assert rc == 1 and b"n_angle" in L.mdn_last_error()
 
 
 def test_product_path_has_no_oracle_dependency():

@@ -297,6 +297,34 @@ def test_train_level_gram_and_bank(mdn, case, prec):
         assert len(big) >= 20
 
 
+@pytest.mark.parametrize("geom", [O.Geometry(2, -1), O.Geometry(3, -1, cross=1)], ids=["5x5", "7x7x3"])
+def test_augment_dihedral_matches_oracle(mdn, geom):
+    """Section 5 augmentation (8 flips / rotations of every pair) by permuting
+    the GPU's Gram sums (mdn_augment_dihedral) vs the oracle materialising the
+    8 transformed pairs with the selector map carried along."""
+    pairs = [synth.noisy_pair(96, 80, 7000 + i) for i in range(2)]
+    bp_o = O.default_bparams(0)
+    g_ref = c_ref = None
+    for z, u in pairs:
+        b, _, _ = O.select(z, bp_o, mirror32=True)
+        g_ref, c_ref = O.gram_accumulate_dihedral(z, u, b, 216, geom, bp_o, g_ref, c_ref)
+    Z = _tt(np.stack([p[0] for p in pairs]), "f32")
+    U = _tt(np.stack([p[1] for p in pairs]), "f32")
+    gm, bp = _geom(mdn, geom), mdn.default_bparams(0)
+    g, c, _ = mdn.train_level_filters(Z, None, U, gm, bp, 0, solve=False)
+    ga, ca = mdn.augment_dihedral(g, c, gm, bp)
+    torch.cuda.synchronize()
+    assert np.array_equal(ca.cpu().numpy(), c_ref)
+    ga = _np(ga)
+    assert np.linalg.norm(ga - g_ref) / np.linalg.norm(g_ref) < GRAM_TOL[0]
+    # the cascade's augment option solves the same augmented system
+    banks, counts = mdn.train_cascade(Z, U, gm, 1, [bp], augment=True)
+    assert np.array_equal(counts[0].cpu().numpy(), c_ref)
+    ref_bank = O.solve_bank(g_ref, c_ref, geom, 1e-3)
+    e = np.linalg.norm(_np(banks[0]) - ref_bank) / np.linalg.norm(ref_bank)
+    assert e < 1e-4, e
+
+
 def test_solve_bank_matches_oracle(mdn):
     geom = O.Geometry(3, 3)
     z, u = synth.noisy_pair(80, 80, 5)

@@ -407,3 +407,70 @@ def test_training_reduces_error_single_level():
     z, u = synth.noisy_pair(64, 64, 2000)
     out = O.denoise_multiscale(z, banks, geom).out
     assert np.mean((out - u) ** 2) < 0.3 * np.mean((z - u) ** 2)
+
+
+# ------------------------------------------------------------ dihedral augmentation
+
+def test_dihedral_group_and_bucket_map():
+    """Section 5 augments the training pairs by flips and 90-degree rotations.
+    The 8 transforms are the dihedral group (distinct, rot^4 = id, mirror^2 =
+    id), and the structure tensor turns with the image: the selector on a
+    transformed image equals the transformed, angle-remapped map of the
+    original (bin + n/2 per quarter turn, n - 1 - a under the mirror) at every
+    pixel outside the threshold band of either image."""
+    idx = np.arange(35).reshape(1, 5, 7)
+    assert len({O.dihedral(idx, t).tobytes() for t in range(8)}) == 8
+    r = idx
+    for _ in range(4):
+        r = O.dihedral(r, 1)
+    assert np.array_equal(r, idx)
+    assert np.array_equal(O.dihedral(O.dihedral(idx, 4), 4), idx)
+    z, _ = synth.noisy_pair(64, 48, 11)
+    bp = O.default_bparams(0)
+    b, band, _ = O.select(z, bp, mirror32=True)
+    for t in range(8):
+        bt, bandt, _ = O.select(O.dihedral(z, t), bp, mirror32=True)
+        keep = ~(bandt | O.dihedral(band.astype(np.uint8)[None], t)[0].astype(bool))
+        assert keep.mean() > 0.98
+        assert np.array_equal(bt[keep], O.dihedral_bucket(b, t, bp)[keep]), t
+
+
+@pytest.mark.parametrize("geom", [O.Geometry(2, -1), O.Geometry(1, -1, cross=1)], ids=["5x5", "3x3x3"])
+def test_dihedral_gram_is_permuted_gram(geom):
+    """Materialising the 8 transformed pairs (with the selector map carried
+    along) gives per-bucket Gram sums that are the original sums with taps
+    permuted by the transform of the (2r+1)^2 index grid and buckets moved by
+    the angle remap; targets (and the channel order) stay in place."""
+    z, u = synth.noisy_pair(24, 20, 12)
+    bp = O.default_bparams(0)
+    b, _, _ = O.select(z, bp, mirror32=True)
+    K = 216
+    g_aug, c_aug = O.gram_accumulate_dihedral(z, u, b, K, geom, bp)
+    g, c = O.gram_accumulate(z, None, u, b, K, geom)
+    n = 2 * geom.r_fine + 1
+    D = geom.D()
+    nch = 3 if geom.cross else 1
+    exp = np.zeros_like(g)
+    cexp = np.zeros_like(c)
+    for t in range(8):
+        tap = O.dihedral(np.arange(n * n).reshape(1, n, n), t)[0].ravel()
+        fmap = np.concatenate([np.concatenate([ch * n * n + tap for ch in range(nch)]),
+                               np.arange(D, g.shape[-1])])
+        for k in range(K):
+            kp = int(O.dihedral_bucket(np.array([[k]], dtype=np.uint8), t, bp)[0, 0])
+            exp[kp] += g[k][:, fmap][:, :, fmap]
+            cexp[kp] += c[k]
+    assert np.array_equal(c_aug, cexp)
+    np.testing.assert_allclose(g_aug, exp, rtol=1e-12, atol=1e-10)
+
+
+def test_awgn8_model_is_8bit():
+    """Section 5's noisy 8-bit training images: AWGN on the 8-bit clean image,
+    then 8-bit quantisation with clamping; the same noise draw as "awgn"."""
+    z, u = synth.noisy_pair(32, 24, 5, model="awgn8")
+    for a in (z, u):
+        assert a.min() >= 0.0 and a.max() <= 1.0
+        assert np.abs(a * 255.0 - np.rint(a * 255.0)).max() < 1e-4
+    zf, _ = synth.noisy_pair(32, 24, 5)
+    assert np.abs(z - np.clip(zf, 0.0, 1.0)).max() <= 1.0 / 255.0 + 1e-6
+    assert (z == 0.0).any() or (z == 1.0).any()   # sigma 25/255 reaches the clamp
