@@ -242,6 +242,20 @@ int mdn_train_status(int32_t* flag);
 int mdn_augment_dihedral(const double* gram_in, const int64_t* counts_in, const mdn_geometry* geom,
                          const mdn_bucket_params* bp, double* gram_out, int64_t* counts_out, void* stream);
 
+/* Noise-level estimate per image, to choose the bank set trained for the
+ * nearest noise level (the paper assumes the level is known and points to
+ * estimating it for selecting the filter set, Section 6).  Robust wavelet
+ * estimate: the finest diagonal Haar detail d = (a - b - c + e) / 2 of every
+ * 2x2 block [a b; c e] (rows and columns 2i, 2i+1; an odd last row or column
+ * is left out) of every channel; sigma = median(|d|) / 0.6745, the median
+ * taken from a 16384-bin histogram over [0, 0.5) with linear interpolation in
+ * the median bin (within one bin, 3.05e-5, of the exact median of |d|).
+ * img: device [n][3][h][w] F32 or F16, h, w >= 2; sigma_out: device float[n];
+ * ws: device, mdn_noise_workspace_bytes(n).  Asynchronous on stream. */
+size_t mdn_noise_workspace_bytes(int64_t n);
+int mdn_estimate_noise(const void* img, int32_t dtype, int64_t n, int64_t h, int64_t w, float* sigma_out,
+                       void* ws, size_t ws_bytes, void* stream);
+
 /* Ridge solve per bucket and group in FP64 on the GPU:
  * h = (G_xx / n_k + lambda I)^{-1} (G_xy / n_k) by Cholesky; buckets with
  * n_k = 0 take the pooled filter solved from sum_k G_k.  bank_out: FP32

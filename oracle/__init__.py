@@ -13,6 +13,9 @@ written as plain Python loops in the paper's order:
 * ``gram_accumulate`` / ``solve_bank`` -- Eqs. 5-6: per-bucket least squares
 * ``train_cascade``      -- Section 4: train level L-1 first, apply it, feed
                             its output to the next finer level
+* ``estimate_noise``     -- noise level for choosing the bank set (the paper
+                            assumes it known, Section 6): Donoho-Johnstone's
+                            median(|HH|) / 0.6745
 * ``dihedral`` / ``gram_accumulate_dihedral`` -- Section 5's training-set
                             augmentation by flips and 90-degree rotations,
                             by materialising the 8 transformed pairs
@@ -402,3 +405,22 @@ def gram_accumulate_dihedral(z, target, bucket, K: int, geom: Geometry, bp: Buck
         gram, counts = gram_accumulate(dihedral(z, t), None, dihedral(target, t), dihedral_bucket(bucket, t, bp),
                                        K, geom, gram, counts)
     return gram, counts
+
+
+# ---------------------------------------------------------------- noise level
+
+def estimate_noise(img):
+    """Noise level of one [3][H][W] image for choosing the bank set trained
+    for the nearest level (the paper assumes the level known and points to
+    estimating it, Section 6).  Donoho and Johnstone's robust estimate: the
+    finest diagonal Haar detail d = (a - b - c + e) / 2 of every 2x2 block
+    [a b; c e] (rows and columns 2i, 2i+1; an odd last row/column left out) of
+    every channel has variance sigma^2 under i.i.d. Gaussian noise, so
+    sigma = median(|d|) / 0.6745 (the median of |N(0, 1)|), in FP64."""
+    z = _d(img)
+    _, H, W = z.shape
+    h2, w2 = H // 2 * 2, W // 2 * 2
+    a, b = z[:, 0:h2:2, 0:w2:2], z[:, 0:h2:2, 1:w2:2]
+    c, e = z[:, 1:h2:2, 0:w2:2], z[:, 1:h2:2, 1:w2:2]
+    d = 0.5 * ((a - b) - (c - e))
+    return float(np.median(np.abs(d)) / 0.6744897501960817)

@@ -123,6 +123,8 @@ def lib():
             "mdn_train_status": (C.c_int, [C.POINTER(C.c_int32)]),
             "mdn_solve_bank": (C.c_int, [vp, vp, G, i32, C.c_double, vp, vp, vp, sz, vp]),
             "mdn_augment_dihedral": (C.c_int, [vp, vp, G, B, vp, vp, vp]),
+            "mdn_noise_workspace_bytes": (sz, [i64]),
+            "mdn_estimate_noise": (C.c_int, [vp, i32, i64, i64, i64, vp, vp, sz, vp]),
             "mdn_server_create": (C.c_int, [C.POINTER(ServerCfg), C.POINTER(BankSet), i32, C.POINTER(vp)]),
             "mdn_server_submit": (C.c_int, [vp, vp, vp, i64, i64, i32, C.POINTER(C.c_uint64)]),
             "mdn_server_cancel": (C.c_int, [vp, C.c_uint64]),
@@ -426,6 +428,27 @@ def train_cascade(noisy, clean, geom: Geometry, levels: int, bparams=None, gram_
             filter_level(zp[l], cur, bank, geom, bparams[l], out=out, stream=stream)
             cur = out
     return banks, counts_out
+
+
+def estimate_noise(img, stream=None):
+    """Noise-level estimate per image (mdn_estimate_noise): robust wavelet
+    estimate median(|d|) / 0.6745 of the finest diagonal Haar details of all
+    channels.  img: [n][3][h][w] or [3][h][w] CUDA F32/F16 -> float32 [n]."""
+    torch = _torch()
+    x = _img(img)
+    n, _, h, w = x.shape
+    sig = torch.empty(n, dtype=torch.float32, device=x.device)
+    need = lib().mdn_noise_workspace_bytes(n)
+    ws = torch.empty(max(need, 1), dtype=torch.uint8, device=x.device)
+    _check(lib().mdn_estimate_noise(_dev(x, "img"), _dtype_code(x), n, h, w, _dev(sig, "sigma"), _dev(ws, "ws"),
+                                    need, _stream(stream)))
+    return sig
+
+
+def nearest_level(sigma: float, levels) -> int:
+    """Index of the trained noise level closest to an estimate (host helper
+    for choosing a bank set)."""
+    return min(range(len(levels)), key=lambda i: abs(levels[i] - sigma))
 
 
 def augment_dihedral(gram, counts, geom: Geometry, bp: BucketParams, stream=None):

@@ -81,6 +81,16 @@ def test_bad_arguments_rejected_without_device(L):
     rc = L.mdn_train_level_filters(C.c_void_p(16), None, C.c_void_p(16), 0, 1, 8, 8, C.byref(mdn.Geometry(2, -1)),
                                    C.byref(bp), 9, 0, C.c_void_p(8), C.c_void_p(8), 1e-3, None, None, 0, None)
     assert rc == 1 and b"precision" in L.mdn_last_error()
+    # noise estimate: null, dtype, size, workspace
+    rc = L.mdn_estimate_noise(None, 0, 1, 8, 8, C.c_void_p(16), C.c_void_p(32), 1 << 20, None)
+    assert rc == 1 and b"null" in L.mdn_last_error()
+    rc = L.mdn_estimate_noise(C.c_void_p(16), 7, 1, 8, 8, C.c_void_p(16), C.c_void_p(32), 1 << 20, None)
+    assert rc == 1 and b"dtype" in L.mdn_last_error()
+    rc = L.mdn_estimate_noise(C.c_void_p(16), 0, 1, 1, 8, C.c_void_p(16), C.c_void_p(32), 1 << 20, None)
+    assert rc == 2
+    rc = L.mdn_estimate_noise(C.c_void_p(16), 0, 2, 8, 8, C.c_void_p(16), C.c_void_p(32), 100, None)
+    assert rc == 3 and b"workspace" in L.mdn_last_error()
+    assert L.mdn_noise_workspace_bytes(3) == 3 * 16384 * 4
     # dihedral augmentation: null, aliasing, multiscale geometry, odd angle count
     g1, bp0 = mdn.Geometry(2, -1), mdn.default_bparams(0)
     rc = L.mdn_augment_dihedral(None, C.c_void_p(16), C.byref(g1), C.byref(bp0), C.c_void_p(32), C.c_void_p(48), None)

@@ -297,6 +297,28 @@ def test_train_level_gram_and_bank(mdn, case, prec):
         assert len(big) >= 20
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_estimate_noise_matches_oracle(mdn, storage):
+    """Noise-level estimate (median(|d|) / 0.6745 of the finest diagonal Haar
+    details) vs the oracle's exact median on the same stored input: within
+    one histogram bin (0.5 / 16384) in |d| units, plus FP32 arithmetic; a
+    batch of three AWGN levels and an odd-sized camera-noise frame.  The
+    nearest trained level is the true one."""
+    levels = [15 / 255, 25 / 255, 50 / 255]
+    batch = np.stack([synth.noisy_pair(240, 320, 8100 + i, sigma=s)[0] for i, s in enumerate(levels)])
+    X = _tt(batch, storage)
+    est = mdn.estimate_noise(X).cpu().numpy()
+    tol = 1.2 * (0.5 / 16384) / 0.6745
+    for i in range(3):
+        ref = O.estimate_noise(_np(X[i]))
+        assert abs(est[i] - ref) <= tol, (i, est[i], ref)
+        assert mdn.nearest_level(float(est[i]), levels) == i
+    cam = synth.noisy_pair(241, 199, 8200, model="camera")[0]
+    Y = _tt(cam, storage)
+    e1 = float(mdn.estimate_noise(Y)[0])
+    assert abs(e1 - O.estimate_noise(_np(Y))) <= tol
+
+
 @pytest.mark.parametrize("geom", [O.Geometry(2, -1), O.Geometry(3, -1, cross=1)], ids=["5x5", "7x7x3"])
 def test_augment_dihedral_matches_oracle(mdn, geom):
     """Section 5 augmentation (8 flips / rotations of every pair) by permuting

@@ -474,3 +474,23 @@ def test_awgn8_model_is_8bit():
     zf, _ = synth.noisy_pair(32, 24, 5)
     assert np.abs(z - np.clip(zf, 0.0, 1.0)).max() <= 1.0 / 255.0 + 1e-6
     assert (z == 0.0).any() or (z == 1.0).any()   # sigma 25/255 reaches the clamp
+
+
+# ------------------------------------------------------------ noise level
+
+def test_noise_estimate_on_pure_noise():
+    """On a constant image plus AWGN the diagonal Haar details are N(0, sigma^2)
+    samples, so the robust estimate recovers sigma (12,288 samples: the
+    median's standard error is about 1.1 %); it scales exactly with the noise
+    and ignores a constant offset and a linear ramp (their d is 0)."""
+    rng = np.random.default_rng(3)
+    noise = rng.standard_normal((3, 128, 128))
+    for s in (15 / 255, 25 / 255, 50 / 255):
+        est = O.estimate_noise(0.5 + s * noise)
+        assert abs(est - s) < 0.035 * s, (est, s)
+    base = O.estimate_noise(noise)
+    assert abs(O.estimate_noise(3.0 * noise) - 3.0 * base) < 1e-12
+    yy, xx = np.mgrid[0:128, 0:128]
+    ramp = 0.002 * xx + 0.003 * yy
+    assert abs(O.estimate_noise(noise + ramp[None]) - base) < 1e-9
+    assert O.estimate_noise(np.ones((3, 9, 7))) == 0.0
