@@ -71,7 +71,8 @@ constexpr int MAX_STAGES = 4;
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s per wait
 
 __device__ int g_gram_error;   // set to 1 when a bounded wait expired
-__device__ float g_one = 1.0f; // the ones column reads this value
+__device__ float g_one = 1.0f;                 // the ones column reads this value
+__device__ unsigned short g_one_bf16 = 0x3F80;  // 1.0 in BF16 (the BF16 planes' ones column)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -272,7 +273,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int e = tid; e < G * rows; e += NTHREADS) {
         const int g = e / rows, f = e % rows;
         Item it;
-        it.ptr = &g_one;
+        it.ptr = MODE == P_BF16 ? reinterpret_cast<const float*>(&g_one_bf16) : &g_one;
         it.meta = 0;
         it.pad = 0;
         if (f < Dq) {
@@ -294,11 +295,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             // the address arithmetic is done on integers: a tap offset may be
             // negative, the base of every pixel makes the sum non-negative
             intptr_t off = 0;
-            const float* plane = &g_one;
+            const float* plane = MODE == P_BF16 ? reinterpret_cast<const float*>(&g_one_bf16) : &g_one;
+            constexpr intptr_t ESZ = MODE == P_BF16 ? 2 : 4;   // the BF16 Gram's planes hold 16-bit values
             if (src == 0) { plane = ga.cw; off = (intptr_t)c * ga.Hcp * ga.Wcp + (intptr_t)dy * ga.Wcp + dx; }
             else if (src == 1) { plane = ga.zw; off = (intptr_t)c * ga.Hp * ga.Wp + (intptr_t)dy * ga.Wp + dx; }
             else if (src == 2) { plane = ga.tw; off = (intptr_t)c * ga.h * ga.w; }
-            it.ptr = reinterpret_cast<const float*>(reinterpret_cast<intptr_t>(plane) + off * (intptr_t)sizeof(float));
+            it.ptr = reinterpret_cast<const float*>(reinterpret_cast<intptr_t>(plane) + off * ESZ);
             const uint32_t rowoff = (uint32_t)g * C::NBUF * tile_bytes + (uint32_t)(f >> 3) * 1024 + (uint32_t)(f & 7) * 128;
             it.meta = 1u | ((uint32_t)src << 1) | ((uint32_t)(f & 7) << 3) | (rowoff << 8);
         }
@@ -506,8 +508,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                                     for (int pg = 0; pg < PGS; ++pg) {
                                         const int2 b = *reinterpret_cast<const int2*>(bsrc + 8 * pg);
-                                        v0[h][pg] = __ldg(it2.ptr + b.x);
-                                        v1[h][pg] = __ldg(it2.ptr + b.y);
+                                        if constexpr (MODE == P_BF16) {
+                                            // BF16 planes: the operands themselves, kept as bit patterns
+                                            const unsigned short* p16 = reinterpret_cast<const unsigned short*>(it2.ptr);
+                                            v0[h][pg] = __uint_as_float((uint32_t)__ldg(p16 + b.x));
+                                            v1[h][pg] = __uint_as_float((uint32_t)__ldg(p16 + b.y));
+                                        } else {
+                                            v0[h][pg] = __ldg(it2.ptr + b.x);
+                                            v1[h][pg] = __ldg(it2.ptr + b.y);
+                                        }
                                     }
                                 }
                             }
@@ -528,6 +537,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                             for (int pg = 0; pg < PGS; ++pg) {
                                 unsigned char* dst = stage + rowb[h] + ((pg ^ sw[h]) << 4);
+                                if constexpr (MODE == P_BF16) {
+                                    // two 16-bit patterns (zero past the chunk end) -> one bf16x2 word
+                                    *reinterpret_cast<uint32_t*>(dst) =
+                                        __float_as_uint(v0[h][pg]) | (__float_as_uint(v1[h][pg]) << 16);
+                                    continue;
+                                }
                                 const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0[h][pg], v1[h][pg]);
                                 *reinterpret_cast<__nv_bfloat162*>(dst) = h2;
                                 if constexpr (MODE == P_SPLIT) {

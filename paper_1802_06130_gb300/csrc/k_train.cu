@@ -1,7 +1,8 @@
 // k_train.cu -- A5/A6: bucketed least-squares training (Eqs. 5-6).
 //
 // Pipeline for one level (all on the stream, no host synchronisation):
-//   k_to_work      storage RGB -> FP32 working colour space (z, coarse, target)
+//   k_to_work      storage RGB -> working colour space (z, coarse, target),
+//                  centred; FP32, TF32-rounded or BF16 by the Gram precision
 //   k_hist         per-block bucket histograms of the bucket map
 //   k_scan         bucket-major exclusive scan -> stable scatter offsets and
 //                  the chunk table (bucket, begin, end), chunks <= CHUNK rows
@@ -15,6 +16,8 @@
 //   k_pool/k_chol  ridge solve (G_xx/n + lambda I) h = G_xy/n by Cholesky in
 //                  FP64 shared memory, one CTA per (bucket, group); empty
 //                  buckets copy the pooled solution
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "internal.h"
 #include "train_common.cuh"
@@ -35,9 +38,11 @@ __device__ __forceinline__ float round_tf32(float x) {
     return __uint_as_float(r);
 }
 
+// mode: 0 FP32 value, 1 rounded to TF32 (nearest, ties away), 2 rounded to
+// BF16 (nearest even) and stored as 16-bit BF16 (the BF16 Gram's operands)
 template <typename TS>
-__global__ void k_to_work(const TS* __restrict__ in, float* __restrict__ out, int h, int w, int64_t n, int P,
-                          int color, int tf32) {
+__global__ void k_to_work(const TS* __restrict__ in, void* __restrict__ outv, int h, int w, int64_t n, int P,
+                          int color, int mode) {
     const int Hp = h + 2 * P, Wp = w + 2 * P;
     const int64_t hwp = (int64_t)Hp * Wp, hw = (int64_t)h * w;
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -57,8 +62,14 @@ __global__ void k_to_work(const TS* __restrict__ in, float* __restrict__ out, in
     yy -= (float)channel_center(0, color);
     cb -= (float)channel_center(1, color);
     cr -= (float)channel_center(2, color);
-    if (tf32) { yy = round_tf32(yy); cb = round_tf32(cb); cr = round_tf32(cr); }
-    float* d = out + img * 3 * hwp + q;
+    const int64_t o = img * 3 * hwp + q;
+    if (mode == 2) {
+        __nv_bfloat16* d = reinterpret_cast<__nv_bfloat16*>(outv) + o;
+        d[0] = __float2bfloat16_rn(yy); d[hwp] = __float2bfloat16_rn(cb); d[2 * hwp] = __float2bfloat16_rn(cr);
+        return;
+    }
+    if (mode == 1) { yy = round_tf32(yy); cb = round_tf32(cb); cr = round_tf32(cr); }
+    float* d = reinterpret_cast<float*>(outv) + o;
     d[0] = yy; d[hwp] = cb; d[2 * hwp] = cr;
 }
 
@@ -528,11 +539,11 @@ int launch_gram(const TrainArgs& a, cudaStream_t s) {
     auto conv = [&](const void* in, float* out, int64_t hh, int64_t ww, int pad) {
         const int64_t cnt = a.n * (hh + 2 * pad) * (ww + 2 * pad);
         unsigned g = (unsigned)((cnt + TB - 1) / TB);
-        const int tf32 = a.precision == MDN_GRAM_TF32;
+        const int mode = a.precision == MDN_GRAM_TF32 ? 1 : (a.precision == MDN_GRAM_BF16 ? 2 : 0);
         if (a.dtype == MDN_F32)
-            k_to_work<float><<<g, TB, 0, s>>>((const float*)in, out, (int)hh, (int)ww, a.n, pad, a.geom.color, tf32);
+            k_to_work<float><<<g, TB, 0, s>>>((const float*)in, out, (int)hh, (int)ww, a.n, pad, a.geom.color, mode);
         else
-            k_to_work<__half><<<g, TB, 0, s>>>((const __half*)in, out, (int)hh, (int)ww, a.n, pad, a.geom.color, tf32);
+            k_to_work<__half><<<g, TB, 0, s>>>((const __half*)in, out, (int)hh, (int)ww, a.n, pad, a.geom.color, mode);
     };
     conv(a.z, zw, a.h, a.w, P);
     conv(a.target, tw, a.h, a.w, 0);

@@ -62,7 +62,8 @@ __host__ __device__ inline double channel_center(int c, int color) {
 }
 
 // The working planes hold each value already shifted by its channel's centring
-// constant (and, for the TF32 Gram, already rounded to TF32).  The regressor
+// constant (and, for the TF32 Gram, already rounded to TF32; for the BF16 Gram
+// they hold 16-bit BF16 values, the operands themselves).  The regressor
 // planes are stored with a replicated border of P = max(rf, rc) pixels, so
 // that every tap of every pixel is an in-range load and clamping to the image
 // (the border rule of the filter) needs no per-tap test.
