@@ -242,6 +242,15 @@ int mdn_train_status(int32_t* flag);
 int mdn_augment_dihedral(const double* gram_in, const int64_t* counts_in, const mdn_geometry* geom,
                          const mdn_bucket_params* bp, double* gram_out, int64_t* counts_out, void* stream);
 
+/* The image form of transform t (0..7) for multiscale training, whose
+ * pyramids do not commute with the mirror: out = mirror_columns_if(t >= 4)(
+ * rot90^(t mod 4)(in)) per channel, rot90 of an (h x w) plane being the
+ * (w x h) plane r[i][j] = in[j][w - 1 - i].  in: device [n][3][h][w] F32 or
+ * F16; out: device, [n][3][w][h] for odd t, else [n][3][h][w], not aliasing
+ * in.  Asynchronous on stream. */
+int mdn_dihedral_images(const void* in, int32_t dtype, int64_t n, int64_t h, int64_t w, int32_t t, void* out,
+                        void* stream);
+
 /* Noise-level estimate per image, to choose the bank set trained for the
  * nearest noise level (the paper assumes the level is known and points to
  * estimating it for selecting the filter set, Section 6).  Robust wavelet

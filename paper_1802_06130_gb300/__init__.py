@@ -124,6 +124,7 @@ def lib():
             "mdn_solve_bank": (C.c_int, [vp, vp, G, i32, C.c_double, vp, vp, vp, sz, vp]),
             "mdn_augment_dihedral": (C.c_int, [vp, vp, G, B, vp, vp, vp]),
             "mdn_noise_workspace_bytes": (sz, [i64]),
+            "mdn_dihedral_images": (C.c_int, [vp, i32, i64, i64, i64, i32, vp, vp]),
             "mdn_estimate_noise": (C.c_int, [vp, i32, i64, i64, i64, vp, vp, sz, vp]),
             "mdn_server_create": (C.c_int, [C.POINTER(ServerCfg), C.POINTER(BankSet), i32, C.POINTER(vp)]),
             "mdn_server_submit": (C.c_int, [vp, vp, vp, i64, i64, i32, C.POINTER(C.c_uint64)]),
@@ -382,6 +383,18 @@ class Server:
             pass
 
 
+def dihedral(img, t: int, stream=None):
+    """Transform t = rot + 4 * flip of [n][3][h][w] (or [3][h][w]) images on the
+    device (mdn_dihedral_images): rotate by 90 degrees rot times (numpy's rot90
+    on the row/column axes), then mirror the columns if flip."""
+    torch = _torch()
+    x = _img(img)
+    n, _, h, w = x.shape
+    out = torch.empty((n, 3, w, h) if t & 1 else (n, 3, h, w), dtype=x.dtype, device=x.device)
+    _check(lib().mdn_dihedral_images(_dev(x, "img"), _dtype_code(x), n, h, w, t, _dev(out, "out"), _stream(stream)))
+    return out
+
+
 def train_cascade(noisy, clean, geom: Geometry, levels: int, bparams=None, gram_precision: int = GRAM_FP32,
                   lam: float = 1e-3, chunk: int = 0, augment: bool = False, stream=None):
     """Section 4 training cascade on the GPU: pyramids of the noisy and clean
@@ -391,42 +404,62 @@ def train_cascade(noisy, clean, geom: Geometry, levels: int, bparams=None, gram_
     training image (mdn_filter_level) for the next finer level.  Base case:
     the coarse input of level L-2 is z^{L-1}.
 
-    noisy, clean: [n][3][h][w] CUDA tensors; chunk > 0 feeds the images to
+    noisy, clean: [n][3][h][w] CUDA tensors, or lists of such tensors (image
+    sets of different shapes, trained together); chunk > 0 feeds the images to
     the Gram accumulation in groups of that many (same result up to FP64
-    summation order).  augment (single-level geometry): train on the 8 flips /
-    90-degree rotations of every pair, by mdn_augment_dihedral on the Gram
-    sums.  Returns (banks [K][3][D] FP32 per level, counts per level)."""
+    summation order).  augment: train on the 8 flips / 90-degree rotations of
+    every pair (Section 5) -- single-level geometries by permuting the Gram
+    sums (mdn_augment_dihedral), multiscale ones on the transformed pairs
+    (mdn_dihedral_images), whose pyramids are their own.  Returns (banks
+    [K][3][D] FP32 per level, counts per level)."""
     torch = _torch()
     single = geom.r_coarse < 0
+    nsets = list(noisy) if isinstance(noisy, (list, tuple)) else [noisy]
+    csets = list(clean) if isinstance(clean, (list, tuple)) else [clean]
     if augment and not single:
-        raise ValueError("train_cascade: augment needs a single-level geometry (r_coarse < 0)")
+        # the 8 transformed copies of every set, grouped by shape
+        by_shape = {}
+        for z, u in zip(nsets, csets):
+            for t in range(8):
+                zt, ut = dihedral(z, t, stream), dihedral(u, t, stream)
+                by_shape.setdefault(tuple(zt.shape[2:]), []).append((zt, ut))
+        nsets = [torch.cat([a for a, _ in v]) for v in by_shape.values()]
+        csets = [torch.cat([b for _, b in v]) for v in by_shape.values()]
     L = 1 if single else levels
     nb = max(levels - 1, 1)
     if bparams is None:
         bparams = [default_bparams(l) for l in range(nb)]
-    zp = [noisy] + (build_pyramid(noisy, L, stream) if L > 1 else [])
-    up = [clean] + (build_pyramid(clean, L, stream) if L > 1 else [])
-    cur = zp[L - 1] if not single else None
+    zp = [[z] + (build_pyramid(z, L, stream) if L > 1 else []) for z in nsets]
+    up = [[u] + (build_pyramid(u, L, stream) if L > 1 else []) for u in csets]
+    cur = [p[L - 1] if not single else None for p in zp]
     banks, counts_out = [None] * nb, [None] * nb
-    n = noisy.shape[0]
-    step = chunk if chunk > 0 else n
+    perm = augment and single
     for l in range(L - 2 if L > 1 else 0, -1, -1):
-        gram = counts = None
-        for i0 in range(0, n, step):
-            sl = slice(i0, min(n, i0 + step))
-            last = i0 + step >= n
-            gram, counts, bank = train_level_filters(
-                zp[l][sl].contiguous(), cur[sl].contiguous() if cur is not None else None, up[l][sl].contiguous(),
-                geom, bparams[l], gram_precision, gram=gram, counts=counts, accumulate=gram is not None,
-                lam=lam, solve=last and not augment, stream=stream)
-        if augment:
+        gram = counts = bank = None
+        nchunks = sum((z.shape[0] + (chunk if chunk > 0 else z.shape[0]) - 1) // (chunk if chunk > 0 else z.shape[0])
+                      for z in nsets)
+        done = 0
+        for si in range(len(nsets)):
+            n = nsets[si].shape[0]
+            step = chunk if chunk > 0 else n
+            for i0 in range(0, n, step):
+                sl = slice(i0, min(n, i0 + step))
+                done += 1
+                last = done == nchunks
+                c_in = cur[si][sl].contiguous() if cur[si] is not None else None
+                gram, counts, bank = train_level_filters(
+                    zp[si][l][sl].contiguous(), c_in, up[si][l][sl].contiguous(), geom, bparams[l], gram_precision,
+                    gram=gram, counts=counts, accumulate=gram is not None, lam=lam, solve=last and not perm,
+                    stream=stream)
+        if perm:
             gram, counts = augment_dihedral(gram, counts, geom, bparams[l], stream=stream)
             bank, _ = solve_bank(gram, counts, geom, lam, stream=stream)
         banks[l], counts_out[l] = bank, counts
         if l > 0 or not single:
-            out = torch.empty_like(zp[l])
-            filter_level(zp[l], cur, bank, geom, bparams[l], out=out, stream=stream)
-            cur = out
+            for si in range(len(nsets)):
+                out = torch.empty_like(zp[si][l])
+                filter_level(zp[si][l], cur[si], bank, geom, bparams[l], out=out, stream=stream)
+                cur[si] = out
     return banks, counts_out
 
 

@@ -4,6 +4,8 @@
 // taps of every patch and moves the orientation bin of every pixel (the
 // structure tensor turns with the image), so the augmented sums are permuted
 // copies of the original ones; no patch is gathered again.
+#include <cuda_fp16.h>
+
 #include "internal.h"
 #include "train_common.cuh"
 
@@ -70,6 +72,34 @@ __global__ void k_dihedral(const double* __restrict__ gin, const int64_t* __rest
     }
 }
 
+// Image form of transform t (for multiscale training, whose pyramids do not
+// commute with the mirror): out = mirror_columns_if(t >= 4)(rot90^(t mod 4)(in))
+// per channel, where rot90 of an (h x w) image is the (w x h) image r with
+// r[i][j] = in[j][w - 1 - i].  One thread per output value.
+template <typename TS>
+__global__ void k_dihedral_img(const TS* __restrict__ in, TS* __restrict__ out, int64_t n, int h, int w, int t) {
+    const bool swap = (t & 1) != 0;
+    const int ho = swap ? w : h, wo = swap ? h : w;
+    const int64_t plane = (int64_t)ho * wo;
+    const int64_t total = n * 3 * plane;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t ch = e / plane, q = e % plane;
+        int i = (int)(q / wo), j = (int)(q % wo);
+        int cw = wo, chh = ho;   // shape of the image the coordinates refer to
+        if (t >= 4) j = cw - 1 - j;
+        for (int r = 0; r < (t & 3); ++r) {
+            // (i, j) in a rotated image of shape (chh, cw) comes from (j, chh - 1 - i) of shape (cw, chh)
+            const int ni = j, nj = chh - 1 - i;
+            i = ni;
+            j = nj;
+            const int tmp = cw;
+            cw = chh;
+            chh = tmp;
+        }
+        out[e] = in[ch * (int64_t)h * w + (int64_t)i * w + j];
+    }
+}
+
 }  // namespace aug
 }  // namespace mdn
 
@@ -97,4 +127,22 @@ extern "C" int mdn_augment_dihedral(const double* gram_in, const int64_t* counts
                                                              geom->cross_channel, bp->n_angle,
                                                              bp->n_strength * bp->n_coherence, gram_out, counts_out);
     return check_launch("k_dihedral");
+}
+
+extern "C" int mdn_dihedral_images(const void* in, int32_t dtype, int64_t n, int64_t h, int64_t w, int32_t t, void* out,
+                                   void* stream) {
+    if (!in || !out) return fail(MDN_EINVAL, "dihedral_images: null pointer");
+    if (in == out) return fail(MDN_EINVAL, "dihedral_images: out must not alias in");
+    if (dtype != MDN_F32 && dtype != MDN_F16) return fail(MDN_EINVAL, "dihedral_images: dtype must be F32 or F16");
+    if (t < 0 || t > 7) return fail(MDN_EINVAL, "dihedral_images: t must be 0..7");
+    if (n < 0 || h < 1 || w < 1 || h > (1 << 20) || w > (1 << 20)) return fail(MDN_ESHAPE, "dihedral_images: bad shape");
+    const int64_t total = n * 3 * h * w;
+    if (total == 0) return MDN_OK;
+    const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == MDN_F32)
+        aug::k_dihedral_img<float><<<grid, 256, 0, s>>>((const float*)in, (float*)out, n, (int)h, (int)w, t);
+    else
+        aug::k_dihedral_img<__half><<<grid, 256, 0, s>>>((const __half*)in, (__half*)out, n, (int)h, (int)w, t);
+    return check_launch("k_dihedral_img");
 }

@@ -91,6 +91,13 @@ def test_bad_arguments_rejected_without_device(L):
     rc = L.mdn_estimate_noise(C.c_void_p(16), 0, 2, 8, 8, C.c_void_p(16), C.c_void_p(32), 100, None)
     assert rc == 3 and b"workspace" in L.mdn_last_error()
     assert L.mdn_noise_workspace_bytes(3) == 3 * 16384 * 4
+    # image transforms: null, aliasing, transform index
+    rc = L.mdn_dihedral_images(None, 0, 1, 4, 4, 0, C.c_void_p(16), None)
+    assert rc == 1 and b"null" in L.mdn_last_error()
+    rc = L.mdn_dihedral_images(C.c_void_p(16), 0, 1, 4, 4, 0, C.c_void_p(16), None)
+    assert rc == 1 and b"alias" in L.mdn_last_error()
+    rc = L.mdn_dihedral_images(C.c_void_p(16), 0, 1, 4, 4, 8, C.c_void_p(32), None)
+    assert rc == 1 and b"0..7" in L.mdn_last_error()
     # dihedral augmentation: null, aliasing, multiscale geometry, odd angle count
     g1, bp0 = mdn.Geometry(2, -1), mdn.default_bparams(0)
     rc = L.mdn_augment_dihedral(None, C.c_void_p(16), C.byref(g1), C.byref(bp0), C.c_void_p(32), C.c_void_p(48), None)

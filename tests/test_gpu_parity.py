@@ -298,6 +298,42 @@ def test_train_level_gram_and_bank(mdn, case, prec):
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_dihedral_images_match_oracle(mdn, storage):
+    """The image form of the 8 transforms (mdn_dihedral_images) equals the
+    oracle's on non-square batches, bit for bit (a pure permutation)."""
+    x = synth.noisy_pair(37, 53, 9)[0]
+    batch = np.stack([x, x[:, ::-1, :]])
+    X = _tt(batch, storage)
+    for t in range(8):
+        got = mdn.dihedral(X, t)
+        ref = np.stack([O.dihedral(_np(X[i]), t) for i in range(2)])
+        assert got.shape == ref.shape
+        assert np.array_equal(_np(got), ref), t
+
+
+def test_train_cascade_augment_multiscale_matches_oracle(mdn):
+    """Section 5 augmentation for a multiscale geometry: the GPU cascade on the
+    transformed pairs (mdn_dihedral_images, two shapes for a non-square set)
+    vs the oracle's cascade on the 8 materialised copies of every pair."""
+    geom = O.Geometry(3, 3)
+    pairs = [synth.noisy_pair(64, 48, 1100 + i) for i in range(2)]
+    zs = [O.round_storage(p[0], "f32") for p in pairs]
+    us = [O.round_storage(p[1], "f32") for p in pairs]
+    zt = [O.dihedral(z, t) for z in zs for t in range(8)]
+    ut = [O.dihedral(u, t) for u in us for t in range(8)]
+    ref_banks, ref_counts = O.train_cascade(zt, ut, geom, 3, mirror32=True, storage="f32")
+    Z, U = _tt(np.stack(zs), "f32"), _tt(np.stack(us), "f32")
+    banks, counts = mdn.train_cascade(Z, U, _geom(mdn, geom), 3, augment=True, chunk=3)
+    torch.cuda.synchronize()
+    for l in range(len(ref_banks)):
+        c = counts[l].cpu().numpy()
+        assert c.sum() == ref_counts[l].sum() == 16 * (64 >> l) * (48 >> l)
+        assert np.abs(c - ref_counts[l]).sum() <= 2e-3 * c.sum(), l
+        e = np.linalg.norm(_np(banks[l]) - ref_banks[l]) / np.linalg.norm(ref_banks[l])
+        assert e < 2e-3, (l, e)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
 def test_estimate_noise_matches_oracle(mdn, storage):
     """Noise-level estimate (median(|d|) / 0.6745 of the finest diagonal Haar
     details) vs the oracle's exact median on the same stored input: within
