@@ -564,6 +564,87 @@ def run_training(args, dev):
     return out
 
 
+def _gen_pair(args_):
+    import synth
+    h, w, seed, sigma = args_
+    return synth.noisy_pair(h, w, seed, sigma=sigma)
+
+
+def run_quality(args, dev):
+    """Whole-pipeline sanity check on synthetic data (the paper's test images
+    and training set are not available): banks trained on the GPU, then
+    denoising of held-out frames, PSNR = 10 log10(1 / MSE) against the clean
+    frame.  Config 1: 8 pairs of 256x256, sigma 25/255, 5x5 single-level
+    filters, with and without the dihedral augmentation.  Config 2: 1920x1080,
+    3 levels, 7x7 + 7x7 filters, one bank set per sigma in {15, 25, 50}/255
+    trained on args.quality_pairs pairs; held-out frames are denoised with the
+    bank set of the nearest estimated noise level."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import torch
+    import paper_1802_06130_gb300 as mdn
+
+    def psnr(a, b):
+        return float(10 * np.log10(1.0 / np.mean((a.astype(np.float64) - b) ** 2)))
+
+    sig = [15 / 255, 25 / 255, 50 / 255]
+    npair = args.quality_pairs
+    jobs = [(256, 256, 1000 + i, 25 / 255) for i in range(8)] + [(256, 256, 2000, 25 / 255)]
+    train_at, test_at = [], []
+    for si, s_ in enumerate(sig):
+        train_at.append(len(jobs))
+        jobs += [(1080, 1920, 10000 + 1000 * si + i, s_) for i in range(npair)]
+        test_at.append(len(jobs))
+        jobs += [(1080, 1920, 20000 + 1000 * si + i, s_) for i in range(4)]
+    with cf.ProcessPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 1),
+                                mp_context=mp.get_context("spawn")) as ex:
+        data = list(ex.map(_gen_pair, jobs))
+    out = {}
+    # config 1
+    tr, te = data[:8], data[8]
+    Z = torch.tensor(np.stack([p[0] for p in tr]), device=dev)
+    U = torch.tensor(np.stack([p[1] for p in tr]), device=dev)
+    g1 = mdn.Geometry(2, -1)
+    xt = torch.tensor(te[0], device=dev)[None]
+    c1 = {"psnr_noisy_db": round(psnr(te[0], te[1]), 2)}
+    for aug in (False, True):
+        banks, _ = mdn.train_cascade(Z, U, g1, 1, augment=aug)
+        y = mdn.denoise_multiscale(xt, banks, g1, [mdn.default_bparams(0)])
+        c1["psnr_denoised_augmented_db" if aug else "psnr_denoised_db"] = round(psnr(_np_(y[0]), te[1]), 2)
+    out["config1_256x256_single_level_5x5"] = c1
+    # config 2
+    g2 = mdn.Geometry(3, 3)
+    bsets = []
+    for si in range(3):
+        tr = data[train_at[si]:train_at[si] + npair]
+        Z = torch.tensor(np.stack([p[0] for p in tr]), device=dev)
+        U = torch.tensor(np.stack([p[1] for p in tr]), device=dev)
+        banks, _ = mdn.train_cascade(Z, U, g2, 3, chunk=4)
+        bsets.append(banks)
+        del Z, U
+    c2 = {"training_pairs_per_sigma": npair, "per_sigma": []}
+    for si in range(3):
+        rows = []
+        for k in range(4):
+            z, u = data[test_at[si] + k]
+            x = torch.tensor(z, device=dev)[None]
+            est = float(mdn.estimate_noise(x)[0])
+            pick = mdn.nearest_level(est, sig)
+            y = mdn.denoise_multiscale(x, bsets[pick], g2, [mdn.default_bparams(l) for l in range(2)])
+            rows.append((psnr(z, u), psnr(_np_(y[0]), u), est * 255, pick == si))
+        r = np.array(rows, dtype=np.float64)
+        c2["per_sigma"].append({"sigma_255": round(sig[si] * 255), "psnr_noisy_db": round(r[:, 0].mean(), 2),
+                                "psnr_denoised_db": round(r[:, 1].mean(), 2),
+                                "sigma_estimate_255": round(r[:, 2].mean(), 2),
+                                "bank_set_chosen_correctly": int(r[:, 3].sum())})
+    out["config2_1080p_3level_7x7_7x7"] = c2
+    return out
+
+
+def _np_(t):
+    return t.detach().float().cpu().numpy()
+
+
 def measured_tensor_peaks():
     """Dense tensor peaks: measured BF16 (burst) and TF32 = BF16 x the nominal
     ratio 1.1 / 2.25."""
@@ -603,6 +684,8 @@ def main():
     ap.add_argument("--no-train", dest="train", action="store_false")
     ap.add_argument("--train-images", type=int, default=256)
     ap.add_argument("--train-only", action="store_true", help="only the training section (profiling driver)")
+    ap.add_argument("--quality", action="store_true", help="whole-pipeline PSNR sanity check (configs 1 and 2), then exit")
+    ap.add_argument("--quality-pairs", type=int, default=16, help="training pairs per sigma for --quality config 2")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -615,6 +698,12 @@ def main():
         import paper_1802_06130_gb300 as mdn
         mdn.build()
         print(json.dumps(run_training(args, torch.device("cuda", args.local_rank))), flush=True)
+        return
+    if args.quality:
+        import torch
+        import paper_1802_06130_gb300 as mdn
+        mdn.build()
+        print(json.dumps(run_quality(args, torch.device("cuda", args.local_rank))), flush=True)
         return
     if args.serve_only:
         import torch
