@@ -17,7 +17,7 @@ __all__ = ["build", "lib", "Geometry", "BucketParams", "default_bparams", "MdnEr
            "build_pyramid", "select_buckets", "filter_level", "denoise_multiscale",
            "denoise_workspace_bytes", "train_level_filters", "solve_bank", "regressor_len",
            "gram_state_shape", "train_status", "train_cascade", "Server", "F32", "F16", "YCBCR601", "RGB", "GRAM_FP32", "GRAM_TF32",
-           "GRAM_BF16", "GRAM_SPLIT_BF16"]
+           "GRAM_BF16", "GRAM_SPLIT_BF16", "augment_dihedral", "dihedral", "estimate_noise", "nearest_level"]
 
 F32, F16 = 0, 1
 YCBCR601, RGB = 0, 1
