@@ -434,6 +434,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const int g = rb / RBG, f = (rb - g * RBG) * 8 + lr;
             return items[g * rows + f];
         };
+        // TF32 gathers with cp.async: on 16 x 1 MP of cross-channel 7x7x3
+        // patches a whole level took 5.8 ms this way and 6.2 ms through the
+        // register path below (which BF16 and split BF16 use).
         if constexpr (MODE == P_TF32) {
             // TF32: the planes already hold the rounded operands, so each lane
             // copies one value per chunk with a 4-byte cp.async straight into
@@ -476,9 +479,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 if (lane == 0) bar_arrive(&full[pend]);
             }
         } else {
-            // BF16: lane (r, e) loads pixels 2e, 2e+1 of each chunk and stores
-            // them as one bf16x2 word; the loads of two row blocks (32 per
-            // lane) are issued before any of them is rounded and stored.
+            // Register path: lane (r, e) loads pixel e (TF32) or pixels 2e, 2e+1
+            // (BF16) of each chunk and stores them as one 4-byte word; the loads
+            // of two row blocks (16 or 32 per lane) are issued before any of
+            // them is stored.
+            constexpr int PPL = MODE == P_TF32 ? 1 : 2;
             for (ChunkIter it = cit0; !it.done() && ok; it.next()) {
                 const int4 ch = chunks[it.c];
                 for (int r0 = ch.y; r0 < ch.z; r0 += KB) {
@@ -502,20 +507,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                                 const Item it2 = item_of(rb);
                                 if (it2.meta & 1u) {
                                     live[h] = true;
-                                    const int* bsrc = pb + ((it2.meta >> 1) & 3u) * BSTR + 2 * le;
+                                    const int* bsrc = pb + ((it2.meta >> 1) & 3u) * BSTR + PPL * le;
                                     rowb[h] = (it2.meta >> 8) + 4 * le;
                                     sw[h] = (it2.meta >> 3) & 7u;
 #pragma unroll
                                     for (int pg = 0; pg < PGS; ++pg) {
-                                        const int2 b = *reinterpret_cast<const int2*>(bsrc + 8 * pg);
-                                        if constexpr (MODE == P_BF16) {
-                                            // BF16 planes: the operands themselves, kept as bit patterns
-                                            const unsigned short* p16 = reinterpret_cast<const unsigned short*>(it2.ptr);
-                                            v0[h][pg] = __uint_as_float((uint32_t)__ldg(p16 + b.x));
-                                            v1[h][pg] = __uint_as_float((uint32_t)__ldg(p16 + b.y));
+                                        if constexpr (MODE == P_TF32) {
+                                            v0[h][pg] = __ldg(it2.ptr + bsrc[4 * pg]);
                                         } else {
-                                            v0[h][pg] = __ldg(it2.ptr + b.x);
-                                            v1[h][pg] = __ldg(it2.ptr + b.y);
+                                            const int2 b = *reinterpret_cast<const int2*>(bsrc + 8 * pg);
+                                            if constexpr (MODE == P_BF16) {
+                                                // BF16 planes: the operands themselves, kept as bit patterns
+                                                const unsigned short* p16 = reinterpret_cast<const unsigned short*>(it2.ptr);
+                                                v0[h][pg] = __uint_as_float((uint32_t)__ldg(p16 + b.x));
+                                                v1[h][pg] = __uint_as_float((uint32_t)__ldg(p16 + b.y));
+                                            } else {
+                                                v0[h][pg] = __ldg(it2.ptr + b.x);
+                                                v1[h][pg] = __ldg(it2.ptr + b.y);
+                                            }
                                         }
                                     }
                                 }
@@ -526,7 +535,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             for (int h = 0; h < 2; ++h)
 #pragma unroll
                                 for (int pg = 0; pg < PGS; ++pg) {
-                                    const int px = 8 * pg + 2 * le;
+                                    const int px = 4 * PPL * pg + PPL * le;
                                     if (px >= nv) v0[h][pg] = 0.f;
                                     if (px + 1 >= nv) v1[h][pg] = 0.f;
                                 }
@@ -537,15 +546,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                             for (int pg = 0; pg < PGS; ++pg) {
                                 unsigned char* dst = stage + rowb[h] + ((pg ^ sw[h]) << 4);
-                                if constexpr (MODE == P_BF16) {
+                                if constexpr (MODE == P_TF32) {
+                                    *reinterpret_cast<float*>(dst) = v0[h][pg];   // the plane holds TF32 values
+                                } else if constexpr (MODE == P_BF16) {
                                     // two 16-bit patterns (zero past the chunk end) -> one bf16x2 word
                                     *reinterpret_cast<uint32_t*>(dst) =
                                         __float_as_uint(v0[h][pg]) | (__float_as_uint(v1[h][pg]) << 16);
-                                    continue;
-                                }
-                                const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0[h][pg], v1[h][pg]);
-                                *reinterpret_cast<__nv_bfloat162*>(dst) = h2;
-                                if constexpr (MODE == P_SPLIT) {
+                                } else {
+                                    const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0[h][pg], v1[h][pg]);
+                                    *reinterpret_cast<__nv_bfloat162*>(dst) = h2;
                                     const float2 hf = __bfloat1622float2(h2);
                                     *reinterpret_cast<__nv_bfloat162*>(dst + tile_bytes) =
                                         __floats2bfloat162_rn(v0[h][pg] - hf.x, v1[h][pg] - hf.y);
