@@ -320,17 +320,21 @@ def run_gpu(args, rank, world, frames):
     pix = n * H * W
     value = whole_job_rate(pix, args.steps, world, ms)
     e2e_value = whole_job_rate(pix, e2e_steps, world, ems)
-    # roofline of the dominant kernel (level-0 fused filter): algorithmic bytes
-    # per launch = read z^0 (6 B/px) + read u^1 (1.5 B per finest px) + write
-    # u^0 (6 B/px) = 13.5 B per finest pixel
+    # roofline of the dominant kernel (level-0 fused select + filter).  Its
+    # binding roof is the FP32 ALU: algorithmic FLOPs per filtered pixel =
+    # 3 x 98 x 2 = 588 (filter) + 180 (structure tensor, features, colour
+    # conversions) = 768; peak = 152 SMs x 128 FP32 lanes x 2 FLOP x the SM
+    # clock.  The HBM roof is reported beside it: algorithmic bytes per launch =
+    # read z^0 (6 B/px) + read u^1 (1.5 B per finest px) + write u^0 (6 B/px)
+    # = 13.5 B per finest pixel, against the measured copy bandwidth.
     t_lv0 = statistics.mean(lv0) * 1e-3
     bytes_lv0 = 13.5 * pix
     achieved = bytes_lv0 / t_lv0 / 1e9
     peak, peak_kind = measured_peaks()
     clk_summary = clk.summary()
-    # FP32 FMA roof of the same kernel: 294 filter FMAs per pixel
-    fma_rate = 294.0 * pix / t_lv0
-    fma_peak = 152 * 128 * (clk_summary["sm_mhz"] or 2070.0) * 1e6
+    flop_rate = 768.0 * pix / t_lv0 / 1e12
+    sm_mhz = clk_summary["sm_mhz"] or 2070.0
+    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
@@ -342,14 +346,18 @@ def run_gpu(args, rank, world, frames):
         "gpu_launches": 4 * args.steps,
         "kernel_ms": {"pyramid": round(statistics.mean(pyr), 4), "level1": round(statistics.mean(lv1), 4),
                       "level0": round(statistics.mean(lv0), 4)},
-        "roofline": {"bound": "hbm", "kernel": "k_level3 (level 0)", "achieved": round(achieved, 1),
-                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+        "roofline": {"bound": "alu", "kernel": "k_level3 (level 0)", "achieved": round(flop_rate, 2),
+                     "peak": round(alu_peak, 1), "unit": "TFLOP/s", "frac": round(flop_rate / alu_peak, 4),
                      "traffic": (round(LEVEL0_TRAFFIC_PER_FRAME * n) if LEVEL0_TRAFFIC_PER_FRAME else None),
                      "traffic_note": "ncu DRAM read+write of a one-frame capture, scaled by frames",
-                     "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
-                     "alu_frac": round(fma_rate / fma_peak, 4), "alu_note":
-                         "294 filter FMAs per pixel vs FP32 FMA peak 152 SMs x 128 x clock (the kernel is bound "
-                         "by shared-memory wavefronts and latency, see profiles/)"},
+                     "flop_per_pixel": 768, "peak_source":
+                         "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x median SM clock (FMA throughput probe on "
+                         "this part: 72-76 TFLOP/s at 2.07 GHz)",
+                     "hbm": {"achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                             "frac": round(achieved / peak, 4),
+                             "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"},
+                     "note": "bound on chip by shared-memory wavefronts and issue (see profiles/); at 768 FLOP per "
+                             "13.5 B the kernel's HBM roof is about 5x its FP32 ALU roof"},
         "e2e": {"value": round(e2e_value, 2), "unit": "Mpix/s", "h2d_bytes_per_step": int(pix * 3 * 2),
                 "d2h_bytes_per_step": int(pix * 3 * 2)},
         "clocks": {"sm_mhz": clk_summary["sm_mhz"], "sm_max_mhz": clk_summary["sm_max_mhz"],
