@@ -761,8 +761,6 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
     constexpr int UW = Coarse<RC>::UW, UH = Coarse<RC>::UH;
     constexpr int SB = v2::SlotBytes<TB>::B;
     constexpr int BSTRIDE = v2::bucket_units<RF, RC, CROSS, TB>() * 16;
-    constexpr int NCX = RC >= 0 ? 2 * RC + 1 : 0;
-    constexpr int NFX = 2 * RF + 1;
     constexpr size_t SBY = stage_bytes<RC>();
     extern __shared__ __align__(16) unsigned char smem[];
     float* ps = reinterpret_cast<float*>(smem + 2 * SBY);   // producer scratch [3][PH][PW]
