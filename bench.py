@@ -316,7 +316,7 @@ def run_gpu(args, rank, world, frames):
 
     if rank != 0:
         return
-    variants = run_variants(mdn, x, geom, dev, stream)
+    variants = run_variants(mdn, x, geom, dev, stream) if args.variants else None
     pix = n * H * W
     value = whole_job_rate(pix, args.steps, world, ms)
     e2e_value = whole_job_rate(pix, e2e_steps, world, ems)
@@ -363,7 +363,8 @@ def run_gpu(args, rank, world, frames):
         "clocks": {"sm_mhz": clk_summary["sm_mhz"], "sm_max_mhz": clk_summary["sm_max_mhz"],
                    "reasons": clk_summary["reasons"]},
     }
-    line["variants"] = variants
+    if variants is not None:
+        line["variants"] = variants
     if args.train and world == 1:
         line["training"] = run_training(args, dev)
     if args.serve and world == 1:
@@ -690,6 +691,7 @@ def main():
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[50, 100, 200, 400, 1600])
     ap.add_argument("--serve-only", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-train", dest="train", action="store_false")
+    ap.add_argument("--no-variants", dest="variants", action="store_false")
     ap.add_argument("--train-images", type=int, default=256)
     ap.add_argument("--train-only", action="store_true", help="only the training section (profiling driver)")
     ap.add_argument("--quality", action="store_true", help="whole-pipeline PSNR sanity check (configs 1 and 2), then exit")
