@@ -17,7 +17,8 @@ __all__ = ["build", "lib", "Geometry", "BucketParams", "default_bparams", "MdnEr
            "build_pyramid", "select_buckets", "filter_level", "denoise_multiscale",
            "denoise_workspace_bytes", "train_level_filters", "solve_bank", "regressor_len",
            "gram_state_shape", "train_status", "train_cascade", "Server", "F32", "F16", "YCBCR601", "RGB", "GRAM_FP32", "GRAM_TF32",
-           "GRAM_BF16", "GRAM_SPLIT_BF16", "augment_dihedral", "dihedral", "estimate_noise", "nearest_level"]
+           "GRAM_BF16", "GRAM_SPLIT_BF16", "augment_dihedral", "dihedral", "estimate_noise", "nearest_level",
+           "save_banks", "load_banks", "save_gram_state", "load_gram_state"]
 
 F32, F16 = 0, 1
 YCBCR601, RGB = 0, 1
@@ -396,7 +397,7 @@ def dihedral(img, t: int, stream=None):
 
 
 def train_cascade(noisy, clean, geom: Geometry, levels: int, bparams=None, gram_precision: int = GRAM_FP32,
-                  lam: float = 1e-3, chunk: int = 0, augment: bool = False, stream=None):
+                  lam: float = 1e-3, chunk: int = 0, augment: bool = False, checkpoint: str = None, stream=None):
     """Section 4 training cascade on the GPU: pyramids of the noisy and clean
     images, then for l = L-2 .. 0 (single-scale: l = 0 only) the bucketed
     least-squares fit of level l (mdn_train_level_filters) with the trained
@@ -410,8 +411,13 @@ def train_cascade(noisy, clean, geom: Geometry, levels: int, bparams=None, gram_
     summation order).  augment: train on the 8 flips / 90-degree rotations of
     every pair (Section 5) -- single-level geometries by permuting the Gram
     sums (mdn_augment_dihedral), multiscale ones on the transformed pairs
-    (mdn_dihedral_images), whose pyramids are their own.  Returns (banks
-    [K][3][D] FP32 per level, counts per level)."""
+    (mdn_dihedral_images), whose pyramids are their own.  checkpoint: path
+    prefix; each trained level writes "<prefix>.level<l>.gram" (its Gram
+    state) and "<prefix>.level<l>.bank", and a level whose files exist is
+    loaded instead of trained (its outputs are recomputed for the finer
+    levels), so an interrupted cascade resumes at the level it stopped in.
+    Returns (banks [K][3][D] FP32 per level, counts per level)."""
+    import os
     torch = _torch()
     single = geom.r_coarse < 0
     nsets = list(noisy) if isinstance(noisy, (list, tuple)) else [noisy]
@@ -436,6 +442,18 @@ def train_cascade(noisy, clean, geom: Geometry, levels: int, bparams=None, gram_
     perm = augment and single
     for l in range(L - 2 if L > 1 else 0, -1, -1):
         gram = counts = bank = None
+        ck = f"{checkpoint}.level{l}" if checkpoint else None
+        if ck and os.path.exists(ck + ".bank") and os.path.exists(ck + ".gram"):
+            dev = nsets[0].device
+            bl, _, _, _ = load_banks(ck + ".bank", device=dev)
+            _, counts, _, _, _ = load_gram_state(ck + ".gram", device=dev)
+            banks[l], counts_out[l] = bl[0], counts
+            if l > 0 or not single:
+                for si in range(len(nsets)):
+                    out = torch.empty_like(zp[si][l])
+                    filter_level(zp[si][l], cur[si], banks[l], geom, bparams[l], out=out, stream=stream)
+                    cur[si] = out
+            continue
         nchunks = sum((z.shape[0] + (chunk if chunk > 0 else z.shape[0]) - 1) // (chunk if chunk > 0 else z.shape[0])
                       for z in nsets)
         done = 0
@@ -455,12 +473,120 @@ def train_cascade(noisy, clean, geom: Geometry, levels: int, bparams=None, gram_
             gram, counts = augment_dihedral(gram, counts, geom, bparams[l], stream=stream)
             bank, _ = solve_bank(gram, counts, geom, lam, stream=stream)
         banks[l], counts_out[l] = bank, counts
+        if ck:
+            save_gram_state(ck + ".gram", gram, counts, geom, bparams[l], l)
+            save_banks(ck + ".bank", [bank], geom, [bparams[l]])
         if l > 0 or not single:
             for si in range(len(nsets)):
                 out = torch.empty_like(zp[si][l])
                 filter_level(zp[si][l], cur[si], bank, geom, bparams[l], out=out, stream=stream)
                 cur[si] = out
     return banks, counts_out
+
+
+# ---------------------------------------------------------------- checkpoints
+#
+# File format (banks and Gram state alike): one line of UTF-8 JSON (the
+# header, ending in "\n"), then the arrays it lists, raw little-endian, in
+# header order.  Banks are FP32 [K][3][D] per level; the Gram state is FP64
+# [K][G][Dp][Dp] plus int64 counts [K].
+
+_CKPT_FORMAT = "mdn-1"
+
+
+def _geom_dict(g: Geometry) -> dict:
+    return {"r_fine": g.r_fine, "r_coarse": g.r_coarse, "cross_channel": g.cross_channel, "color": g.color}
+
+
+def _bp_dict(b: BucketParams) -> dict:
+    return {"n_angle": b.n_angle, "n_strength": b.n_strength, "n_coherence": b.n_coherence,
+            "strength_thr": [float(b.strength_thr[i]) for i in range(b.n_strength - 1)],
+            "coherence_thr": [float(b.coherence_thr[i]) for i in range(b.n_coherence - 1)],
+            "coh_eps": float(b.coh_eps)}
+
+
+def _bp_from(d: dict) -> BucketParams:
+    b = BucketParams(d["n_angle"])
+    b.n_strength, b.n_coherence = d["n_strength"], d["n_coherence"]
+    for i, t in enumerate(d["strength_thr"]):
+        b.strength_thr[i] = t
+    for i, t in enumerate(d["coherence_thr"]):
+        b.coherence_thr[i] = t
+    b.coh_eps = d["coh_eps"]
+    return b
+
+
+def _write(path, header: dict, arrays):
+    import json
+    import numpy as np
+    with open(path, "wb") as f:
+        f.write((json.dumps(header) + "\n").encode())
+        for a in arrays:
+            f.write(np.ascontiguousarray(a).tobytes())
+
+
+def _read(path):
+    import json
+    with open(path, "rb") as f:
+        header = json.loads(f.readline().decode())
+        if header.get("format") != _CKPT_FORMAT:
+            raise ValueError(f"{path}: not an {_CKPT_FORMAT} checkpoint")
+        return header, f.read()
+
+
+def save_banks(path, banks, geom: Geometry, bparams, sigma=None):
+    """Writes a bank set (one [K][3][D] bank per level) with its geometry,
+    per-level bucket parameters and the noise level it was trained for."""
+    import numpy as np
+    arr = [b.detach().float().cpu().numpy().astype("<f4") for b in banks]
+    header = {"format": _CKPT_FORMAT, "kind": "banks", "geometry": _geom_dict(geom),
+              "bparams": [_bp_dict(b) for b in bparams], "sigma": sigma,
+              "shapes": [list(a.shape) for a in arr], "dtype": "<f4"}
+    _write(path, header, arr)
+
+
+def load_banks(path, device="cuda"):
+    """-> (banks, geometry, bparams, sigma) from save_banks."""
+    import numpy as np
+    torch = _torch()
+    h, raw = _read(path)
+    if h["kind"] != "banks":
+        raise ValueError(f"{path}: not a bank checkpoint")
+    banks, off = [], 0
+    for shp in h["shapes"]:
+        n = int(np.prod(shp))
+        a = np.frombuffer(raw, dtype="<f4", count=n, offset=off).reshape(shp)
+        off += 4 * n
+        banks.append(torch.tensor(a, dtype=torch.float32, device=device))
+    g = h["geometry"]
+    geom = Geometry(g["r_fine"], g["r_coarse"], g["cross_channel"], g["color"])
+    return banks, geom, [_bp_from(d) for d in h["bparams"]], h["sigma"]
+
+
+def save_gram_state(path, gram, counts, geom: Geometry, bp: BucketParams, level: int = 0):
+    """Writes the accumulated Gram sums of one level (FP64 [K][G][Dp][Dp]) and
+    its counts (int64 [K]), so that training can resume or add more pairs."""
+    g = gram.detach().cpu().numpy().astype("<f8")
+    c = counts.detach().cpu().numpy().astype("<i8")
+    header = {"format": _CKPT_FORMAT, "kind": "gram", "geometry": _geom_dict(geom), "bparams": _bp_dict(bp),
+              "level": level, "gram_shape": list(g.shape), "counts_shape": list(c.shape)}
+    _write(path, header, [g, c])
+
+
+def load_gram_state(path, device="cuda"):
+    """-> (gram, counts, geometry, bparams, level) from save_gram_state."""
+    import numpy as np
+    torch = _torch()
+    h, raw = _read(path)
+    if h["kind"] != "gram":
+        raise ValueError(f"{path}: not a Gram checkpoint")
+    n = int(np.prod(h["gram_shape"]))
+    g = np.frombuffer(raw, dtype="<f8", count=n).reshape(h["gram_shape"])
+    c = np.frombuffer(raw, dtype="<i8", count=int(np.prod(h["counts_shape"])), offset=8 * n)
+    gm = h["geometry"]
+    geom = Geometry(gm["r_fine"], gm["r_coarse"], gm["cross_channel"], gm["color"])
+    return (torch.tensor(g, device=device), torch.tensor(c, device=device), geom, _bp_from(h["bparams"]),
+            h["level"])
 
 
 def estimate_noise(img, stream=None):

@@ -136,6 +136,7 @@ size_t mdn_pyramid_bytes(int64_t n, int64_t h, int64_t w, int32_t levels, int32_
 
 int mdn_build_pyramid(const void* img, int32_t dtype, int64_t n, int64_t h, int64_t w, int32_t levels,
                       void* const* out_levels, void* stream) {
+    NvtxRange nvtx_range("mdn_build_pyramid");
     int rc = check_img(img, dtype, n, h, w, "build_pyramid");
     if (rc) return rc;
     if (levels < 1 || levels > 8) return fail(MDN_EINVAL, "build_pyramid: levels must be 1..8");
@@ -156,6 +157,7 @@ int mdn_build_pyramid(const void* img, int32_t dtype, int64_t n, int64_t h, int6
 
 int mdn_select_buckets(const void* z, int32_t dtype, int64_t n, int64_t h, int64_t w,
                        const mdn_bucket_params* bp, uint8_t* buckets, void* stream) {
+    NvtxRange nvtx_range("mdn_select_buckets");
     int rc = check_img(z, dtype, n, h, w, "select_buckets");
     if (rc) return rc;
     if (!buckets) return fail(MDN_EINVAL, "select_buckets: null output");
@@ -171,6 +173,7 @@ int mdn_select_buckets(const void* z, int32_t dtype, int64_t n, int64_t h, int64
 int mdn_filter_level(const void* z, const void* coarse, int32_t dtype, int64_t n, int64_t h, int64_t w,
                      const void* bank, int32_t bank_dtype, const mdn_geometry* geom,
                      const mdn_bucket_params* bp, void* out, uint8_t* buckets_out, void* stream) {
+    NvtxRange nvtx_range("mdn_filter_level");
     int rc = check_img(z, dtype, n, h, w, "filter_level");
     if (rc) return rc;
     if ((rc = check_geom(geom))) return rc;
@@ -204,6 +207,7 @@ int mdn_denoise_multiscale(const void* noisy, int32_t dtype, int64_t n, int64_t 
                            const void* const* banks, int32_t bank_dtype, const mdn_geometry* geom,
                            const mdn_bucket_params* bparams, void* out, uint8_t* const* bucket_maps, void* ws,
                            size_t ws_bytes, void* stream) {
+    NvtxRange nvtx_range("mdn_denoise_multiscale");
     int rc = check_img(noisy, dtype, n, h, w, "denoise_multiscale");
     if (rc) return rc;
     if ((rc = check_geom(geom))) return rc;
@@ -237,9 +241,12 @@ int mdn_denoise_multiscale(const void* noisy, int32_t dtype, int64_t n, int64_t 
         p += align256((size_t)n * 3 * hl[l] * wl[l] * esize(dtype));
     }
     ul[0] = out;
-    for (int l = 1; l < levels; ++l) {
-        rc = launch_pyramid_down(zl[l - 1], (void*)zl[l], dtype, n, hl[l - 1], wl[l - 1], s);
-        if (rc) return rc;
+    {
+        NvtxRange r("pyramid");
+        for (int l = 1; l < levels; ++l) {
+            rc = launch_pyramid_down(zl[l - 1], (void*)zl[l], dtype, n, hl[l - 1], wl[l - 1], s);
+            if (rc) return rc;
+        }
     }
     const void* coarse = levels > 1 ? zl[levels - 1] : nullptr;   // base case u^{L-1} = z^{L-1}
     for (int l = nb - 1; l >= 0; --l) {
@@ -251,6 +258,7 @@ int mdn_denoise_multiscale(const void* noisy, int32_t dtype, int64_t n, int64_t 
         a.dtype = dtype; a.bank_dtype = bank_dtype;
         a.K = bparams[l].n_angle * bparams[l].n_strength * bparams[l].n_coherence;
         a.geom = *geom;
+        NvtxRange r(l == 0 ? "level 0" : l == 1 ? "level 1" : l == 2 ? "level 2" : "level 3+");
         if ((rc = launch_level(a, s))) return rc;
         coarse = ul[l];
     }
@@ -288,6 +296,7 @@ int mdn_train_level_filters(const void* noisy_lvl, const void* coarse_out, const
                             const mdn_bucket_params* bp, int32_t gram_precision, int32_t accumulate,
                             double* gram, int64_t* counts, double lambda, float* bank_out, void* ws,
                             size_t ws_bytes, void* stream) {
+    NvtxRange nvtx_range("mdn_train_level_filters");
     int rc = check_img(noisy_lvl, dtype, n, h, w, "train_level_filters");
     if (rc) return rc;
     if ((rc = check_img(clean_lvl, dtype, n, h, w, "train_level_filters (clean)"))) return rc;
@@ -322,7 +331,11 @@ int mdn_train_level_filters(const void* noisy_lvl, const void* coarse_out, const
         LevelArgs a{};
         a.sel = sp; a.z = noisy_lvl; a.out = nullptr; a.buckets = bmap; a.n = n; a.h = h; a.w = w;
         a.dtype = dtype; a.K = K; a.geom = mdn_geometry{3, -1, 0, MDN_YCBCR601};
-        if ((rc = launch_level(a, s))) return rc;
+        {
+            NvtxRange r("select");
+            if ((rc = launch_level(a, s))) return rc;
+        }
+        NvtxRange r("gram");
         if ((rc = launch_gram(t, s))) return rc;
     }
     if (bank_out) {
@@ -336,6 +349,7 @@ int mdn_train_level_filters(const void* noisy_lvl, const void* coarse_out, const
 
 int mdn_solve_bank(const double* gram, const int64_t* counts, const mdn_geometry* geom, int32_t K, double lambda,
                    float* bank_out, int32_t* status_out, void* ws, size_t ws_bytes, void* stream) {
+    NvtxRange nvtx_range("mdn_solve_bank");
     int rc;
     if ((rc = check_geom(geom))) return rc;
     if (!gram || !counts || !bank_out || !status_out) return fail(MDN_EINVAL, "solve_bank: null pointer");

@@ -7,8 +7,18 @@
 #include <string>
 
 #include "../../include/mdn.h"
+#include <nvtx3/nvToolsExt.h>
 
 namespace mdn {
+
+// NVTX range over the lifetime of the object (a named span of host time on a
+// profiler's timeline; free when no profiler is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Per-thread error message; returns `code` for convenient `return fail(...)`.
 int fail(int code, const std::string& msg);

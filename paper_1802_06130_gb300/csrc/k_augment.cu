@@ -108,6 +108,7 @@ using namespace mdn;
 extern "C" int mdn_augment_dihedral(const double* gram_in, const int64_t* counts_in, const mdn_geometry* geom,
                                     const mdn_bucket_params* bp, double* gram_out, int64_t* counts_out,
                                     void* stream) {
+    NvtxRange nvtx_range("mdn_augment_dihedral");
     if (!gram_in || !counts_in || !geom || !bp || !gram_out || !counts_out)
         return fail(MDN_EINVAL, "augment_dihedral: null argument");
     if (gram_out == gram_in || counts_out == counts_in)
@@ -131,6 +132,7 @@ extern "C" int mdn_augment_dihedral(const double* gram_in, const int64_t* counts
 
 extern "C" int mdn_dihedral_images(const void* in, int32_t dtype, int64_t n, int64_t h, int64_t w, int32_t t, void* out,
                                    void* stream) {
+    NvtxRange nvtx_range("mdn_dihedral_images");
     if (!in || !out) return fail(MDN_EINVAL, "dihedral_images: null pointer");
     if (in == out) return fail(MDN_EINVAL, "dihedral_images: out must not alias in");
     if (dtype != MDN_F32 && dtype != MDN_F16) return fail(MDN_EINVAL, "dihedral_images: dtype must be F32 or F16");

@@ -91,6 +91,7 @@ extern "C" size_t mdn_noise_workspace_bytes(int64_t n) {
 
 extern "C" int mdn_estimate_noise(const void* img, int32_t dtype, int64_t n, int64_t h, int64_t w, float* sigma_out,
                                   void* ws, size_t ws_bytes, void* stream) {
+    NvtxRange nvtx_range("mdn_estimate_noise");
     if (!img || !sigma_out || (n > 0 && !ws)) return fail(MDN_EINVAL, "estimate_noise: null pointer");
     if (dtype != MDN_F32 && dtype != MDN_F16) return fail(MDN_EINVAL, "estimate_noise: dtype must be F32 or F16");
     if (n < 0 || n > 65535 || h < 2 || w < 2 || h > (1 << 20) || w > (1 << 20))

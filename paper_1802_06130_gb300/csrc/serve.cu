@@ -387,6 +387,7 @@ static void build_worklist(const mdn_server* s, std::vector<Request>& reqs, Work
 }
 
 int mdn_server::launch_tick(TickCtx& c) {
+    NvtxRange nvtx_range("mdn_server tick");
     build_worklist(this, c.reqs, c.h_wl);
     cudaError_t e = cudaSuccess;
     // upload stream: inputs (overlapping the previous tick's kernels)

@@ -1,0 +1,47 @@
+"""Bank and Gram-state checkpoints (host only): round trips, header contents
+and rejection of the wrong kind of file."""
+import json
+
+import numpy as np
+import pytest
+import torch
+
+import paper_1802_06130_gb300 as mdn
+
+
+def test_bank_round_trip(tmp_path):
+    geom = mdn.Geometry(3, 3)
+    bps = [mdn.default_bparams(0), mdn.default_bparams(1)]
+    rng = np.random.default_rng(0)
+    banks = [torch.tensor(rng.standard_normal((216, 3, 98)), dtype=torch.float32) for _ in range(2)]
+    p = tmp_path / "set.bank"
+    mdn.save_banks(p, banks, geom, bps, sigma=25 / 255)
+    with open(p, "rb") as f:
+        head = json.loads(f.readline())
+    assert head["kind"] == "banks" and head["shapes"] == [[216, 3, 98]] * 2 and head["dtype"] == "<f4"
+    b2, g2, bp2, sig = mdn.load_banks(p, device="cpu")
+    assert all(torch.equal(a, b) for a, b in zip(banks, b2))
+    assert (g2.r_fine, g2.r_coarse, g2.cross_channel, g2.color) == (3, 3, 0, 0)
+    assert sig == pytest.approx(25 / 255)
+    for a, b in zip(bps, bp2):
+        assert (a.n_angle, a.n_strength, a.n_coherence) == (b.n_angle, b.n_strength, b.n_coherence)
+        assert [a.strength_thr[i] for i in range(2)] == [b.strength_thr[i] for i in range(2)]
+        assert [a.coherence_thr[i] for i in range(2)] == [b.coherence_thr[i] for i in range(2)]
+        assert a.coh_eps == b.coh_eps
+
+
+def test_gram_round_trip_and_kind_check(tmp_path):
+    geom = mdn.Geometry(3, -1, 1)
+    rng = np.random.default_rng(1)
+    g = torch.tensor(rng.standard_normal((216, 1, 150, 150)), dtype=torch.float64)
+    c = torch.tensor(rng.integers(0, 1 << 40, 216), dtype=torch.int64)
+    p = tmp_path / "l0.gram"
+    mdn.save_gram_state(p, g, c, geom, mdn.default_bparams(0), level=0)
+    g2, c2, geom2, bp2, lev = mdn.load_gram_state(p, device="cpu")
+    assert torch.equal(g, g2) and torch.equal(c, c2) and lev == 0 and geom2.cross_channel == 1
+    with pytest.raises(ValueError):
+        mdn.load_banks(p, device="cpu")
+    bad = tmp_path / "bad"
+    bad.write_bytes(b'{"format": "other"}\n')
+    with pytest.raises(ValueError):
+        mdn.load_gram_state(bad, device="cpu")

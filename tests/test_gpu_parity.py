@@ -333,6 +333,25 @@ def test_train_cascade_augment_multiscale_matches_oracle(mdn):
         assert e < 2e-3, (l, e)
 
 
+def test_train_cascade_resumes_from_checkpoints(mdn, tmp_path):
+    """A cascade with a checkpoint prefix writes every level's Gram state and
+    bank; a rerun loads them, and after the finest level's files are removed
+    it retrains only that level on the loaded coarser levels' outputs: the
+    same banks (the training is deterministic)."""
+    geom = mdn.Geometry(3, 3)
+    pairs = [synth.noisy_pair(80, 64, 1300 + i) for i in range(2)]
+    Z, U = _tt(np.stack([p[0] for p in pairs]), "f32"), _tt(np.stack([p[1] for p in pairs]), "f32")
+    pre = str(tmp_path / "ck")
+    a, ca = mdn.train_cascade(Z, U, geom, 3, checkpoint=pre)
+    b, cb = mdn.train_cascade(Z, U, geom, 3, checkpoint=pre)
+    for l in range(2):
+        assert torch.equal(a[l], b[l]) and torch.equal(ca[l], cb[l])
+    import os
+    os.remove(pre + ".level0.bank")
+    c, _ = mdn.train_cascade(Z, U, geom, 3, checkpoint=pre)
+    assert torch.equal(a[0], c[0]) and torch.equal(a[1], c[1])
+
+
 @pytest.mark.parametrize("storage", ["f32", "f16"])
 def test_estimate_noise_matches_oracle(mdn, storage):
     """Noise-level estimate (median(|d|) / 0.6745 of the finest diagonal Haar
