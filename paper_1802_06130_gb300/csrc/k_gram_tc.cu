@@ -179,23 +179,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// TF32 operand: round to nearest (the tensor core would otherwise drop the
-// low mantissa bits, a bias that does not average out over many rows)
-__device__ __forceinline__ float to_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
-
-__device__ __forceinline__ float center_of(int c, int color) { return (float)channel_center(c, color); }
-
 // Precision modes
 enum { P_TF32 = 0, P_BF16 = 1, P_SPLIT = 2 };
 
 template <int MODE> struct Cfg {
     static constexpr bool TF32 = MODE == P_TF32;
     static constexpr int KB = TF32 ? 32 : 64;          // pixels per K-step (one 128-byte atom)
-    static constexpr int PPG = KB / PGS;               // pixels per 16-byte chunk
     static constexpr int NBUF = MODE == P_SPLIT ? 2 : 1;  // hi (+ lo) operand copies
     static constexpr int FMT = TF32 ? 2 : 1;           // TF32 = 2, BF16 = 1
     static constexpr int BSTR = KB + 4;                // ints per base array (16-byte pad: no bank aliasing)

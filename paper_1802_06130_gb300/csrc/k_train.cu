@@ -31,7 +31,9 @@ namespace trn {
 // constant, written with a replicated border of P pixels: out is
 // [n][3][h + 2P][w + 2P] and out(y + P, x + P) takes the input at
 // (clamp(y, 0, h-1), clamp(x, 0, w-1)).  round_tf32: round the shifted value
-// to TF32 (nearest, ties away), the operand precision of the TF32 Gram.
+// to TF32 (nearest, ties away), the operand precision of the TF32 Gram (the
+// tensor core would otherwise drop the low mantissa bits, a bias that does not
+// average out over many rows).
 __device__ __forceinline__ float round_tf32(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
