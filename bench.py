@@ -185,26 +185,32 @@ def run_variants(mdn, x, geom, dev, stream, reps=10):
     """The rest of the 12 MP metric run, timing only (same frames, denoise via
     mdn_denoise_multiscale with preallocated output and workspace, L2 flushed
     before every timed call, median): FP16 and FP32 storage, batch 1 and 8,
-    and the 4-level pipeline of the 12 MP batch."""
+    the 4-level pipeline of the 12 MP batch, and the paper's own 16 x 16 x 16
+    grid with 7x7 + 5x5 taps (4096 buckets, bank read through L2)."""
     import torch
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     res = {}
+    paper_geom = mdn.Geometry(3, 2)
     for name, xv, levels in [("f16_batch1_3level", x[:1], 3), ("f32_batch1_3level", x[:1].float(), 3),
-                             ("f32_batch8_3level", x.float(), 3), ("f16_batch8_4level", x, 4)]:
-        banks = [torch.tensor(b, dtype=torch.float16, device=dev) for b in random_banks(7, nb=levels - 1)]
-        bps = [mdn.default_bparams(l) for l in range(levels - 1)]
+                             ("f32_batch8_3level", x.float(), 3), ("f16_batch8_4level", x, 4),
+                             ("f16_batch1_3level_grid16x16x16_7x7+5x5", x[:1], 3)]:
+        paper = "grid16" in name     # the paper's 4096-bucket grid: bank read through L2
+        g = paper_geom if paper else geom
+        banks = [torch.tensor(b, dtype=torch.float16, device=dev)
+                 for b in (random_banks(7, D=74, K=4096, nb=levels - 1) if paper else random_banks(7, nb=levels - 1))]
+        bps = [(mdn.paper_grid_bparams if paper else mdn.default_bparams)(l) for l in range(levels - 1)]
         nv = xv.shape[0]
         dt = mdn.F16 if xv.dtype == torch.float16 else mdn.F32
         ws = torch.empty(mdn.denoise_workspace_bytes(nv, H, W, levels, dt), dtype=torch.uint8, device=dev)
         out = torch.empty_like(xv)
         for _ in range(2):
-            mdn.denoise_multiscale(xv, banks, geom, bps, out=out, ws=ws)
+            mdn.denoise_multiscale(xv, banks, g, bps, out=out, ws=ws)
         times = []
         for _ in range(reps):
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            mdn.denoise_multiscale(xv, banks, geom, bps, out=out, ws=ws)
+            mdn.denoise_multiscale(xv, banks, g, bps, out=out, ws=ws)
             b.record(stream)
             torch.cuda.synchronize()
             times.append(a.elapsed_time(b))
@@ -570,6 +576,26 @@ def run_training(args, dev):
         out["precisions"][name] = d
         del g, c, bank
     out["peak_source"] = peaks["source"]
+    # the paper's own selector grid and footprint on the same pairs: 16 x 16 x 16
+    # = 4096 buckets, 7x7 fine + 5x5 coarse per channel (D = 74, three Gram
+    # groups of Dp = 75), the coarse input z^1 of each pair; TF32
+    pg = mdn.Geometry(3, 2)
+    Zc = mdn.build_pyramid(Z, 2)[0]
+    times = []
+    for rep in range(3):
+        s_, e_ = torch.cuda.Event(True), torch.cuda.Event(True)
+        s_.record()
+        g, c, _ = mdn.train_level_filters(Z, Zc, U, pg, mdn.paper_grid_bparams(0), mdn.GRAM_TF32, lam=1e-3,
+                                          solve=False)
+        e_.record()
+        torch.cuda.synchronize()
+        times.append(s_.elapsed_time(e_))
+    ms = min(times[1:])
+    alg16 = npatch * 3 * 75 * 76
+    out["grid16x16x16_7x7+5x5_tf32"] = {
+        "ms": round(ms, 3), "mpatch_s": round(npatch / ms / 1e3, 1), "alg_tflops": round(alg16 / ms / 1e9, 2),
+        "counts_total_ok": bool(int(c.sum().item()) == npatch), "buckets_hit": int((c > 0).sum().item())}
+    del g, c, Zc
     return out
 
 

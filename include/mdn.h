@@ -63,8 +63,8 @@ extern "C" {
 #define MDN_GRAM_BF16 2        /* tcgen05 kind::f16 with BF16 operands */
 #define MDN_GRAM_SPLIT_BF16 3  /* hi*hi + hi*lo + lo*hi BF16 products */
 
-#define MDN_MAX_THR 8
-#define MDN_MAX_K 256
+#define MDN_MAX_THR 16
+#define MDN_MAX_K 4096
 
 /* Filter footprint.  r_fine: radius of the fine patch R_i z^l (1..3);
  * r_coarse: radius of the coarse patch R_{i/2} u^{l+1} (0..3) or -1 for
@@ -84,7 +84,10 @@ typedef struct {
  * sqrt(lambda1) and coherence (sqrt l1 - sqrt l2)/(sqrt l1 + sqrt l2) are
  * binned by the n_strength-1 and n_coherence-1 ascending thresholds
  * (lower-inclusive).  Coherence is 0 where sqrt l1 + sqrt l2 < coh_eps.
- * Bucket k = (a * n_strength + s) * n_coherence + c, K = product <= 256. */
+ * Bucket k = (a * n_strength + s) * n_coherence + c, K = product <= 4096
+ * (n_strength, n_coherence <= MDN_MAX_THR + 1), e.g. the paper's own
+ * 16 x 16 x 16 grid (Section 5).  Bucket maps hold one u8 per pixel when
+ * K <= 256 and one u16 (native byte order) when K > 256. */
 typedef struct {
     int32_t n_angle;
     int32_t n_strength;
@@ -103,6 +106,10 @@ const char* mdn_last_error(void);
 
 /* Regressor length D per output channel for a geometry, or -1 if invalid. */
 int mdn_regressor_len(const mdn_geometry* geom);
+
+/* Bytes per pixel of a bucket map for K buckets: 1 (u8) for K <= 256, 2 (u16)
+ * for 256 < K <= MDN_MAX_K, 0 for K outside 1..MDN_MAX_K. */
+int mdn_bucket_elem_bytes(int32_t K);
 
 /* ------------------------------------------------------------------ */
 /* Pyramid (Section 4, "Multiscale filtering": downsampling by two)    */
@@ -124,9 +131,10 @@ int mdn_build_pyramid(const void* img, int32_t dtype, int64_t n, int64_t h, int6
 /* Filter selection only (Section 3)                                   */
 /* ------------------------------------------------------------------ */
 
-/* Writes the bucket map s(i) (u8, [n][h][w]) of image z ([n][3][h][w]). */
+/* Writes the bucket map s(i) ([n][h][w], u8 or u16 by K, see
+ * mdn_bucket_elem_bytes) of image z ([n][3][h][w]). */
 int mdn_select_buckets(const void* z, int32_t dtype, int64_t n, int64_t h, int64_t w,
-                       const mdn_bucket_params* bp, uint8_t* buckets, void* stream);
+                       const mdn_bucket_params* bp, void* buckets, void* stream);
 
 /* ------------------------------------------------------------------ */
 /* One level of filtering (Eq. 1; Section 4 multiscale equation)       */
@@ -136,11 +144,13 @@ int mdn_select_buckets(const void* z, int32_t dtype, int64_t n, int64_t h, int64
  * R_i z] per output channel, converted back to RGB and rounded to dtype.
  * z, out: [n][3][h][w]; coarse: [n][3][ceil(h/2)][ceil(w/2)] or NULL when
  * geom->r_coarse < 0; bank: [K][3][D] of bank_dtype, K = bucket count of bp;
- * buckets_out: optional u8 [n][h][w] copy of s(i).  out must not alias z or
- * coarse. */
+ * buckets_out: optional [n][h][w] copy of s(i) (u8 or u16 by K).  out must
+ * not alias z or coarse.  Banks of up to ~220 KB (e.g. 216 buckets of 7x7 +
+ * 7x7 taps in FP16) are held in shared memory; larger ones (the paper's
+ * 4096-bucket grid) are read through L2 by a slower kernel. */
 int mdn_filter_level(const void* z, const void* coarse, int32_t dtype, int64_t n, int64_t h,
                      int64_t w, const void* bank, int32_t bank_dtype, const mdn_geometry* geom,
-                     const mdn_bucket_params* bp, void* out, uint8_t* buckets_out, void* stream);
+                     const mdn_bucket_params* bp, void* out, void* buckets_out, void* stream);
 
 /* ------------------------------------------------------------------ */
 /* Multiscale denoising (Section 4)                                    */
@@ -156,12 +166,12 @@ size_t mdn_denoise_workspace_bytes(int64_t n, int64_t h, int64_t w, int32_t leve
  * banks[0] and geom->r_coarse = -1.  banks: HOST array of max(levels-1, 1)
  * device pointers; bparams: HOST array of the same length (level l uses
  * bparams[l]); bucket_maps: NULL or a HOST array of the same length of device
- * u8 [n][h_l][w_l] pointers (entries may be NULL).  ws: device workspace of
+ * [n][h_l][w_l] pointers, u8 or u16 by the level's K (entries may be NULL).  ws: device workspace of
  * at least mdn_denoise_workspace_bytes(). */
 int mdn_denoise_multiscale(const void* noisy, int32_t dtype, int64_t n, int64_t h, int64_t w,
                            int32_t levels, const void* const* banks, int32_t bank_dtype,
                            const mdn_geometry* geom, const mdn_bucket_params* bparams,
-                           void* out, uint8_t* const* bucket_maps, void* ws, size_t ws_bytes,
+                           void* out, void* const* bucket_maps, void* ws, size_t ws_bytes,
                            void* stream);
 
 /* Same as mdn_denoise_multiscale, for callers that cannot allocate device
@@ -185,7 +195,7 @@ int mdn_denoise_multiscale(const void* noisy, int32_t dtype, int64_t n, int64_t 
 int mdn_denoise_multiscale_static(const void* noisy, int32_t dtype, int64_t n, int64_t h, int64_t w,
                                   int32_t levels, const void* const* banks, int32_t bank_dtype,
                                   const mdn_geometry* geom, const mdn_bucket_params* bparams,
-                                  void* out, uint8_t* const* bucket_maps, void* stream);
+                                  void* out, void* const* bucket_maps, void* stream);
 
 /* ------------------------------------------------------------------ */
 /* Training (Eqs. 5-6: per-bucket least squares; Section 4 cascade)    */
@@ -285,7 +295,8 @@ int mdn_solve_bank(const double* gram, const int64_t* counts, const mdn_geometry
 /* A registered bank set: the filters of one noise level for a `levels`-level
  * pyramid.  Geometry must be 7x7 fine + 7x7 coarse per channel (r_fine = 3,
  * r_coarse = 3, cross_channel = 0); banks are FP16 [K][3][98] device
- * buffers owned by the caller and read for the server's lifetime. */
+ * buffers (K <= 256: the server's kernels keep the bank in shared memory)
+ * owned by the caller and read for the server's lifetime. */
 typedef struct {
     int32_t levels;                     /* 2..8 */
     const void* const* banks;           /* HOST array of levels-1 device pointers */

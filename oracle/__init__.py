@@ -40,7 +40,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liborc.so")
 
 STORAGE = {"f64": 0, "f32": 1, "f16": 2}
-MAX_THR = 8
+MAX_THR = 16
 
 
 def build(force: bool = False) -> str:
@@ -69,20 +69,21 @@ def lib():
     if _lib is None:
         L = C.CDLL(build())
         dp, u8p, i64p = C.POINTER(C.c_double), C.POINTER(C.c_uint8), C.POINTER(C.c_int64)
+        i32p = C.POINTER(C.c_int32)
         L.orc_round_f16.restype = C.c_double
         L.orc_round_f16.argtypes = [C.c_double]
         L.orc_round_storage.argtypes = [dp, C.c_long, C.c_int]
         L.orc_pyramid_down.argtypes = [dp, C.c_int, C.c_int, C.c_int, dp, C.c_int]
         L.orc_structure_tensor.argtypes = [dp, C.c_int, C.c_int, C.c_int, dp]
         L.orc_features.argtypes = [dp, C.c_int, C.c_int, C.c_int, C.c_float, dp]
-        L.orc_buckets.argtypes = [dp, C.c_int, C.c_int, C.POINTER(_BParams), C.c_double, u8p, u8p]
+        L.orc_buckets.argtypes = [dp, C.c_int, C.c_int, C.POINTER(_BParams), C.c_double, i32p, u8p]
         L.orc_to_work.argtypes = [dp, C.c_long, C.c_int, dp]
         L.orc_from_work.argtypes = [dp, C.c_long, C.c_int, dp]
         L.orc_regressor_len.restype = C.c_int
         L.orc_regressor_len.argtypes = [C.c_int, C.c_int, C.c_int]
-        L.orc_filter_level.argtypes = [dp, C.c_int, C.c_int, dp, C.c_int, C.c_int, u8p, dp, C.c_int,
+        L.orc_filter_level.argtypes = [dp, C.c_int, C.c_int, dp, C.c_int, C.c_int, i32p, dp, C.c_int,
                                        C.c_int, C.c_int, C.c_int, C.c_int, dp]
-        L.orc_gram_accumulate.argtypes = [dp, C.c_int, C.c_int, dp, C.c_int, C.c_int, dp, u8p, C.c_int,
+        L.orc_gram_accumulate.argtypes = [dp, C.c_int, C.c_int, dp, C.c_int, C.c_int, dp, i32p, C.c_int,
                                           C.c_int, C.c_int, C.c_int, C.c_int, dp, i64p]
         L.orc_cholesky_solve.restype = C.c_int
         L.orc_cholesky_solve.argtypes = [dp, C.c_int, dp, C.c_int]
@@ -151,6 +152,39 @@ def default_bparams(level: int) -> BucketParams:
     return BucketParams(strength_thr=(0.135 * s, 0.16 * s), coherence_thr=(0.10, 0.15))
 
 
+# The paper's own grid, 16 x 16 x 16 = 4096 buckets (Section 5).  Reading
+# (the paper gives no thresholds): equal-population strength and coherence
+# bins, the 15 quantiles k/16 of each feature over the 256x256, sigma =
+# 25/255 training set (seeds 1000-1007) at levels 0 and 1, rounded to 4
+# digits and frozen; coarser levels halve the level-1 strength thresholds
+# per level and keep its coherence thresholds.
+PAPER_GRID_STRENGTH = (
+    (0.1101, 0.1145, 0.1176, 0.1202, 0.1225, 0.1247, 0.1268, 0.129, 0.1311, 0.1334, 0.1359, 0.1387,
+     0.1422, 0.1469, 0.1556),
+    (0.0297, 0.031, 0.032, 0.0329, 0.0336, 0.0343, 0.035, 0.0357, 0.0364, 0.0372, 0.038, 0.0391,
+     0.0403, 0.0423, 0.0497))
+PAPER_GRID_COHERENCE = (
+    (0.0232, 0.0335, 0.042, 0.0496, 0.0569, 0.0641, 0.0713, 0.0789, 0.0869, 0.0955, 0.105, 0.1163,
+     0.1299, 0.1484, 0.1801),
+    (0.0278, 0.0402, 0.0504, 0.0598, 0.0687, 0.0774, 0.0861, 0.095, 0.1047, 0.1153, 0.1273, 0.1412,
+     0.1588, 0.1844, 0.242))
+
+
+def paper_grid_bparams(level: int) -> BucketParams:
+    """16 angle x 16 strength x 16 coherence bins for level l."""
+    if level <= 1:
+        return BucketParams(n_angle=16, strength_thr=PAPER_GRID_STRENGTH[level],
+                            coherence_thr=PAPER_GRID_COHERENCE[level])
+    s = 0.5 ** (level - 1)
+    return BucketParams(n_angle=16, strength_thr=tuple(t * s for t in PAPER_GRID_STRENGTH[1]),
+                        coherence_thr=PAPER_GRID_COHERENCE[1])
+
+
+def bucket_dtype(K: int):
+    """Element type of a bucket map: u8 up to 256 buckets, else u16."""
+    return np.uint8 if K <= 256 else np.uint16
+
+
 # ---------------------------------------------------------------- primitives
 
 def round_storage(x, storage: str):
@@ -194,11 +228,11 @@ def features(T, coh_eps: float = 1e-8, mirror32: bool = False):
 def buckets(feat, bp: BucketParams, band_eps: float = 1e-5):
     feat = _d(feat)
     _, H, W = feat.shape
-    b = np.empty((H, W), dtype=np.uint8)
+    b = np.empty((H, W), dtype=np.int32)
     band = np.empty((H, W), dtype=np.uint8)
     cb = bp.c()
-    lib().orc_buckets(_p(feat), H, W, C.byref(cb), band_eps, _p(b, C.c_uint8), _p(band, C.c_uint8))
-    return b, band.astype(bool)
+    lib().orc_buckets(_p(feat), H, W, C.byref(cb), band_eps, _p(b, C.c_int32), _p(band, C.c_uint8))
+    return b.astype(bucket_dtype(bp.K)), band.astype(bool)
 
 
 def select(z, bp: BucketParams, mirror32: bool = False, band_eps: float = 1e-5):
@@ -229,7 +263,7 @@ def filter_level(z, uc, bucket, bank, geom: Geometry):
     bank = _d(bank)
     K = bank.shape[0]
     assert bank.shape == (K, 3, geom.D()), (bank.shape, geom.D())
-    bucket = np.ascontiguousarray(bucket, dtype=np.uint8)
+    bucket = np.ascontiguousarray(bucket, dtype=np.int32)
     out = np.empty_like(z)
     if geom.r_coarse >= 0:
         uc = _d(uc)
@@ -238,7 +272,7 @@ def filter_level(z, uc, bucket, bank, geom: Geometry):
     else:
         Hc = Wc = 0
         ucp = None
-    lib().orc_filter_level(_p(z), H, W, ucp, Hc, Wc, _p(bucket, C.c_uint8), _p(bank), K,
+    lib().orc_filter_level(_p(z), H, W, ucp, Hc, Wc, _p(bucket, C.c_int32), _p(bank), K,
                            geom.r_fine, geom.r_coarse, geom.cross, geom.color, _p(out))
     return out
 
@@ -293,7 +327,7 @@ def gram_accumulate(z, uc, target, bucket, K: int, geom: Geometry, gram=None, co
     if gram is None:
         gram = np.zeros((K, G, D + T, D + T))
         counts = np.zeros(K, dtype=np.int64)
-    bucket = np.ascontiguousarray(bucket, dtype=np.uint8)
+    bucket = np.ascontiguousarray(bucket, dtype=np.int32)
     if geom.r_coarse >= 0:
         uc = _d(uc)
         Hc, Wc = uc.shape[1:]
@@ -301,7 +335,7 @@ def gram_accumulate(z, uc, target, bucket, K: int, geom: Geometry, gram=None, co
     else:
         Hc = Wc = 0
         ucp = None
-    lib().orc_gram_accumulate(_p(z), H, W, ucp, Hc, Wc, _p(target), _p(bucket, C.c_uint8), K,
+    lib().orc_gram_accumulate(_p(z), H, W, ucp, Hc, Wc, _p(target), _p(bucket, C.c_int32), K,
                               geom.r_fine, geom.r_coarse, geom.cross, geom.color,
                               _p(gram), _p(counts, C.c_int64))
     return gram, counts
@@ -391,7 +425,7 @@ def dihedral_bucket(bucket, t: int, bp: BucketParams):
     a = (a + (t % 4) * (n // 2)) % n
     if t >= 4:
         a = n - 1 - a
-    return dihedral((a * m + rest).astype(np.uint8)[None], t)[0]
+    return dihedral((a * m + rest).astype(bucket_dtype(bp.K))[None], t)[0]
 
 
 def gram_accumulate_dihedral(z, target, bucket, K: int, geom: Geometry, bp: BucketParams, gram=None, counts=None):

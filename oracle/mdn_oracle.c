@@ -39,7 +39,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define ORC_MAX_THR 8
+#define ORC_MAX_THR 16
 #ifndef M_PI
 #define M_PI 3.14159265358979323846
 #endif
@@ -282,7 +282,7 @@ static int count_le(const float* thr, int n, double v)
  * thresholds, and coh_eps for sqrt(l1)+sqrt(l2), approximated here by the
  * strength feature). */
 void orc_buckets(const double* feat, int H, int W, const orc_bparams* bp, double band_eps,
-                 uint8_t* bucket, uint8_t* band)
+                 int32_t* bucket, uint8_t* band)
 {
     long HW = (long)H * W;
     int ns = bp->n_strength - 1, nc = bp->n_coherence - 1;
@@ -293,7 +293,7 @@ void orc_buckets(const double* feat, int H, int W, const orc_bparams* bp, double
         if (a < 0) a = 0;
         int s = count_le(bp->strength_thr, ns, st);
         int c = count_le(bp->coherence_thr, nc, co);
-        bucket[i] = (uint8_t)((a * bp->n_strength + s) * bp->n_coherence + c);
+        bucket[i] = (a * bp->n_strength + s) * bp->n_coherence + c;
         if (band) {
             int bd = 0;
             double ta = t * bp->n_angle;
@@ -389,7 +389,7 @@ int orc_regressor_len(int rf, int rc, int cross)
  * z: level-l RGB image; uc: level-(l+1) RGB image (Hc x Wc) or NULL when
  * rc < 0; bank: [K][3][D] (D = orc_regressor_len). */
 void orc_filter_level(const double* z, int H, int W, const double* uc, int Hc, int Wc,
-                      const uint8_t* bucket, const double* bank, int K,
+                      const int32_t* bucket, const double* bank, int K,
                       int rf, int rc, int cross, int color, double* out)
 {
     long HW = (long)H * W;
@@ -436,7 +436,7 @@ void orc_filter_level(const double* z, int H, int W, const double* uc, int Hc, i
  * cross-channel: G = 1 group, T = 3 targets.  counts[k] += 1 per pixel.
  * target: level-l clean RGB image. */
 void orc_gram_accumulate(const double* z, int H, int W, const double* uc, int Hc, int Wc,
-                         const double* target, const uint8_t* bucket, int K,
+                         const double* target, const int32_t* bucket, int K,
                          int rf, int rc, int cross, int color, double* gram, int64_t* counts)
 {
     long HW = (long)H * W;

@@ -18,12 +18,14 @@ __all__ = ["build", "lib", "Geometry", "BucketParams", "default_bparams", "MdnEr
            "denoise_workspace_bytes", "train_level_filters", "solve_bank", "regressor_len",
            "gram_state_shape", "train_status", "train_cascade", "Server", "F32", "F16", "YCBCR601", "RGB", "GRAM_FP32", "GRAM_TF32",
            "GRAM_BF16", "GRAM_SPLIT_BF16", "augment_dihedral", "dihedral", "estimate_noise", "nearest_level",
-           "save_banks", "load_banks", "save_gram_state", "load_gram_state"]
+           "save_banks", "load_banks", "save_gram_state", "load_gram_state", "paper_grid_bparams",
+           "bucket_map_dtype", "MAX_K"]
 
 F32, F16 = 0, 1
 YCBCR601, RGB = 0, 1
 GRAM_FP32, GRAM_TF32, GRAM_BF16, GRAM_SPLIT_BF16 = 0, 1, 2, 3
-MAX_THR = 8
+MAX_THR = 16
+MAX_K = 4096
 
 
 class MdnError(RuntimeError):
@@ -70,6 +72,39 @@ def default_bparams(level: int) -> BucketParams:
     return BucketParams(24, (0.135 * s, 0.16 * s), (0.10, 0.15), 1e-8)
 
 
+# Thresholds of the paper's own 16 x 16 x 16 grid (Section 5 gives the grid,
+# not the thresholds): equal-population bins of strength and coherence, the
+# quantiles k/16 (k = 1..15) of each feature over a 256x256, sigma = 25/255
+# training set at levels 0 and 1; coarser levels halve the level-1 strength
+# thresholds per level and keep its coherence thresholds.
+_GRID16_STRENGTH = (
+    (0.1101, 0.1145, 0.1176, 0.1202, 0.1225, 0.1247, 0.1268, 0.129, 0.1311, 0.1334, 0.1359, 0.1387,
+     0.1422, 0.1469, 0.1556),
+    (0.0297, 0.031, 0.032, 0.0329, 0.0336, 0.0343, 0.035, 0.0357, 0.0364, 0.0372, 0.038, 0.0391,
+     0.0403, 0.0423, 0.0497))
+_GRID16_COHERENCE = (
+    (0.0232, 0.0335, 0.042, 0.0496, 0.0569, 0.0641, 0.0713, 0.0789, 0.0869, 0.0955, 0.105, 0.1163,
+     0.1299, 0.1484, 0.1801),
+    (0.0278, 0.0402, 0.0504, 0.0598, 0.0687, 0.0774, 0.0861, 0.095, 0.1047, 0.1153, 0.1273, 0.1412,
+     0.1588, 0.1844, 0.242))
+
+
+def paper_grid_bparams(level: int) -> BucketParams:
+    """The paper's 16 x 16 x 16 = 4096-bucket selector for level l (bucket
+    maps are then u16, stored as int16 tensors; the bank is read through L2)."""
+    if level <= 1:
+        return BucketParams(16, _GRID16_STRENGTH[level], _GRID16_COHERENCE[level], 1e-8)
+    s = 0.5 ** (level - 1)
+    return BucketParams(16, tuple(t * s for t in _GRID16_STRENGTH[1]), _GRID16_COHERENCE[1], 1e-8)
+
+
+def bucket_map_dtype(K: int):
+    """torch dtype of a bucket map for K buckets: uint8 up to 256, else int16
+    (the library writes u16 values < 4096)."""
+    torch = _torch()
+    return torch.uint8 if K <= 256 else torch.int16
+
+
 class ServerCfg(C.Structure):
     _fields_ = [("device", C.c_int32), ("hbm_budget_bytes", C.c_size_t), ("max_active", C.c_int32),
                 ("autotune", C.c_int32), ("tile_variant", C.c_int32)]
@@ -109,6 +144,7 @@ def lib():
             "mdn_version": (C.c_int, []),
             "mdn_last_error": (C.c_char_p, []),
             "mdn_regressor_len": (C.c_int, [G]),
+            "mdn_bucket_elem_bytes": (C.c_int, [i32]),
             "mdn_pyramid_bytes": (sz, [i64, i64, i64, i32, i32]),
             "mdn_build_pyramid": (C.c_int, [vp, i32, i64, i64, i64, i32, C.POINTER(vp), vp]),
             "mdn_select_buckets": (C.c_int, [vp, i32, i64, i64, i64, B, vp, vp]),
@@ -216,12 +252,23 @@ def build_pyramid(img, levels: int, stream=None):
     return [o if img.dim() == 4 else o[0] for o in outs]
 
 
+def _map(m, K: int, n: int, h: int, w: int, name: str):
+    """Device pointer of a bucket map after checking its type and size (the
+    library writes one u8 per pixel for K <= 256 and one u16 above)."""
+    if m is None:
+        return None
+    if m.dtype != bucket_map_dtype(K) or m.numel() != n * h * w:
+        raise ValueError(f"{name}: need {bucket_map_dtype(K)} with {n * h * w} elements for {K} buckets, "
+                         f"got {m.dtype} with {m.numel()}")
+    return _dev(m, name)
+
+
 def select_buckets(z, bp: BucketParams, stream=None):
-    """Bucket map s(i), uint8 [n][h][w] (mdn_select_buckets)."""
+    """Bucket map s(i), [n][h][w] uint8 (K <= 256) or int16 (mdn_select_buckets)."""
     torch = _torch()
     z4 = _img(z)
     n, _, h, w = z4.shape
-    out = torch.empty((n, h, w), dtype=torch.uint8, device=z4.device)
+    out = torch.empty((n, h, w), dtype=bucket_map_dtype(bp.K), device=z4.device)
     _check(lib().mdn_select_buckets(_dev(z4, "z"), _dtype_code(z4), n, h, w, C.byref(bp), _dev(out), _stream(stream)))
     return out if z.dim() == 4 else out[0]
 
@@ -236,7 +283,7 @@ def filter_level(z, coarse, bank, geom: Geometry, bp: BucketParams, out=None, bu
         out = torch.empty_like(z4)
     _check(lib().mdn_filter_level(_dev(z4, "z"), _dev(c4, "coarse"), _dtype_code(z4), n, h, w, _dev(bank, "bank"),
                                   _dtype_code(bank), C.byref(geom), C.byref(bp), _dev(out, "out"),
-                                  _dev(buckets_out, "buckets_out"), _stream(stream)))
+                                  _map(buckets_out, bp.K, n, h, w, "buckets_out"), _stream(stream)))
     return out if z.dim() == 4 else out[0]
 
 
@@ -266,7 +313,14 @@ def denoise_multiscale(noisy, banks, geom: Geometry, bparams, out=None, bucket_m
     parr = (BucketParams * nb)(*bparams)
     marr = None
     if bucket_maps is not None:
-        marr = (C.c_void_p * nb)(*[m.data_ptr() if m is not None else None for m in bucket_maps])
+        if len(bucket_maps) != nb:
+            raise ValueError("need one bucket map entry (or None) per bank")
+        ptrs, hl, wl = [], h, w
+        for l in range(nb):
+            p = _map(bucket_maps[l], bparams[l].K, n, hl, wl, f"bucket_maps[{l}]")
+            ptrs.append(p.value if p is not None else None)
+            hl, wl = (hl + 1) // 2, (wl + 1) // 2
+        marr = (C.c_void_p * nb)(*ptrs)
     _check(lib().mdn_denoise_multiscale(_dev(z4, "noisy"), _dtype_code(z4), n, h, w, levels, barr, bank_dt,
                                         C.byref(geom), parr, _dev(out, "out"), marr, _dev(ws, "ws"),
                                         ws.numel() * ws.element_size(), _stream(stream)))

@@ -54,9 +54,9 @@ int make_sel_params(const mdn_bucket_params* bp, SelParams* sp) {
         return fail(MDN_EINVAL, "bucket params: n_angle must be even, 2..64");
     if (bp->n_strength < 1 || bp->n_strength > MDN_MAX_THR + 1 || bp->n_coherence < 1 ||
         bp->n_coherence > MDN_MAX_THR + 1)
-        return fail(MDN_EINVAL, "bucket params: n_strength/n_coherence out of range 1..9");
+        return fail(MDN_EINVAL, "bucket params: n_strength/n_coherence out of range 1..17");
     int K = bp->n_angle * bp->n_strength * bp->n_coherence;
-    if (K > MDN_MAX_K) return fail(MDN_EINVAL, "bucket params: more than 256 buckets");
+    if (K > MDN_MAX_K) return fail(MDN_EINVAL, "bucket params: more than 4096 buckets");
     std::memset(sp, 0, sizeof(*sp));
     sp->n_angle = bp->n_angle;
     sp->n_strength = bp->n_strength;
@@ -124,6 +124,8 @@ int mdn_regressor_len(const mdn_geometry* geom) {
     return regressor_len(*geom);
 }
 
+int mdn_bucket_elem_bytes(int32_t K) { return K < 1 || K > MDN_MAX_K ? 0 : bucket_bytes(K); }
+
 size_t mdn_pyramid_bytes(int64_t n, int64_t h, int64_t w, int32_t levels, int32_t dtype) {
     size_t tot = 0;
     for (int l = 1; l < levels; ++l) {
@@ -156,7 +158,7 @@ int mdn_build_pyramid(const void* img, int32_t dtype, int64_t n, int64_t h, int6
 }
 
 int mdn_select_buckets(const void* z, int32_t dtype, int64_t n, int64_t h, int64_t w,
-                       const mdn_bucket_params* bp, uint8_t* buckets, void* stream) {
+                       const mdn_bucket_params* bp, void* buckets, void* stream) {
     NvtxRange nvtx_range("mdn_select_buckets");
     int rc = check_img(z, dtype, n, h, w, "select_buckets");
     if (rc) return rc;
@@ -172,7 +174,7 @@ int mdn_select_buckets(const void* z, int32_t dtype, int64_t n, int64_t h, int64
 
 int mdn_filter_level(const void* z, const void* coarse, int32_t dtype, int64_t n, int64_t h, int64_t w,
                      const void* bank, int32_t bank_dtype, const mdn_geometry* geom,
-                     const mdn_bucket_params* bp, void* out, uint8_t* buckets_out, void* stream) {
+                     const mdn_bucket_params* bp, void* out, void* buckets_out, void* stream) {
     NvtxRange nvtx_range("mdn_filter_level");
     int rc = check_img(z, dtype, n, h, w, "filter_level");
     if (rc) return rc;
@@ -205,7 +207,7 @@ size_t mdn_denoise_workspace_bytes(int64_t n, int64_t h, int64_t w, int32_t leve
 
 int mdn_denoise_multiscale(const void* noisy, int32_t dtype, int64_t n, int64_t h, int64_t w, int32_t levels,
                            const void* const* banks, int32_t bank_dtype, const mdn_geometry* geom,
-                           const mdn_bucket_params* bparams, void* out, uint8_t* const* bucket_maps, void* ws,
+                           const mdn_bucket_params* bparams, void* out, void* const* bucket_maps, void* ws,
                            size_t ws_bytes, void* stream) {
     NvtxRange nvtx_range("mdn_denoise_multiscale");
     int rc = check_img(noisy, dtype, n, h, w, "denoise_multiscale");
@@ -279,7 +281,7 @@ size_t mdn_train_workspace_bytes(int64_t n, int64_t h, int64_t w, const mdn_geom
     int G = geom->cross_channel ? 1 : 3, T = geom->cross_channel ? 3 : 1;
     size_t solve = solve_ws_bytes(K, G, D, T);
     const int P = geom->r_coarse > geom->r_fine ? geom->r_coarse : geom->r_fine;
-    size_t tr = align256((size_t)n * h * w) +                                   // bucket map
+    size_t tr = align256((size_t)n * h * w * bucket_bytes(K)) +                 // bucket map
                 train_ws_bytes(n, h, w, P, geom->r_coarse >= 0, K, G, D + T, gram_precision);  // working planes, sort, partials
     return tr > solve + 256 ? tr : solve + 256;
 }
@@ -318,10 +320,11 @@ int mdn_train_level_filters(const void* noisy_lvl, const void* coarse_out, const
     t.geom = *geom; t.K = K; t.D = regressor_len(*geom);
     t.G = geom->cross_channel ? 1 : 3; t.T = geom->cross_channel ? 3 : 1; t.Dp = t.D + t.T;
     t.precision = gram_precision; t.gram = gram; t.counts = counts;
-    uint8_t* bmap = (uint8_t*)ws;
+    void* bmap = ws;
     t.buckets = bmap;
-    t.ws = (char*)ws + align256((size_t)n * h * w);
-    t.ws_bytes = ws_bytes - align256((size_t)n * h * w);
+    const size_t bmap_bytes = align256((size_t)n * h * w * bucket_bytes(K));
+    t.ws = (char*)ws + bmap_bytes;
+    t.ws_bytes = ws_bytes - bmap_bytes;
     if (!accumulate) {
         cudaError_t e = cudaMemsetAsync(gram, 0, mdn_gram_state_bytes(geom, K), s);
         if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, sizeof(int64_t) * K, s);
@@ -353,7 +356,7 @@ int mdn_solve_bank(const double* gram, const int64_t* counts, const mdn_geometry
     int rc;
     if ((rc = check_geom(geom))) return rc;
     if (!gram || !counts || !bank_out || !status_out) return fail(MDN_EINVAL, "solve_bank: null pointer");
-    if (K < 1 || K > MDN_MAX_K) return fail(MDN_EINVAL, "solve_bank: K must be 1..256");
+    if (K < 1 || K > MDN_MAX_K) return fail(MDN_EINVAL, "solve_bank: K must be 1..4096");
     if (!(lambda >= 0.0)) return fail(MDN_EINVAL, "solve_bank: lambda must be >= 0");
     int D = regressor_len(*geom);
     int G = geom->cross_channel ? 1 : 3, T = geom->cross_channel ? 3 : 1;

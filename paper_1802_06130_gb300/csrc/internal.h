@@ -47,7 +47,7 @@ struct LevelArgs {
     const void* z;        // [n][3][h][w] storage type
     const void* coarse;   // [n][3][hc][wc] or nullptr
     void* out;            // [n][3][h][w] or nullptr (select-only)
-    uint8_t* buckets;     // [n][h][w] or nullptr
+    void* buckets;        // [n][h][w] or nullptr, u8 (K <= 256) or u16
     const void* bank;     // [K][3][D]
     int64_t n, h, w, hc, wc;
     int dtype, bank_dtype;
@@ -71,7 +71,7 @@ struct TrainArgs {
     int precision;
     double* gram;         // [K][G][Dp][Dp]
     int64_t* counts;      // [K]
-    const uint8_t* buckets;  // [n][h][w] (computed beforehand)
+    const void* buckets;  // [n][h][w] (computed beforehand), u8 (K <= 256) or u16
     void* ws;
     size_t ws_bytes;
 };
@@ -84,6 +84,8 @@ int launch_solve(const double* gram, const int64_t* counts, int K, int G, int D,
 
 int num_sms();
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+// bytes per pixel of a bucket map of K buckets
+inline int bucket_bytes(int K) { return K <= 256 ? 1 : 2; }
 inline int regressor_len(const mdn_geometry& g) {
     int pf = (2 * g.r_fine + 1) * (2 * g.r_fine + 1);
     int pc = g.r_coarse >= 0 ? (2 * g.r_coarse + 1) * (2 * g.r_coarse + 1) : 0;

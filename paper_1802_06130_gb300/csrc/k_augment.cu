@@ -119,7 +119,7 @@ extern "C" int mdn_augment_dihedral(const double* gram_in, const int64_t* counts
     if (bp->n_angle < 2 || bp->n_angle % 2 || bp->n_strength < 1 || bp->n_coherence < 1)
         return fail(MDN_EINVAL, "augment_dihedral: n_angle must be even and the grid non-empty");
     const int K = bp->n_angle * bp->n_strength * bp->n_coherence;
-    if (K > MDN_MAX_K) return fail(MDN_EINVAL, "augment_dihedral: more than 256 buckets");
+    if (K > MDN_MAX_K) return fail(MDN_EINVAL, "augment_dihedral: more than 4096 buckets");
     const int D = regressor_len(*geom);
     const int G = geom->cross_channel ? 1 : 3, T = geom->cross_channel ? 3 : 1, Dp = D + T;
     const int64_t total = (int64_t)K * G * Dp * Dp;

@@ -62,10 +62,10 @@ template <typename TB, int D> struct BankLayout {
     static constexpr int DP = (D + V - 1) / V * V;   // padded row length
 };
 
-// shared-memory footprint of the tile buffers (bytes)
+// shared-memory footprint of the tile buffers (bytes; the bucket tile is u16)
 template <int RC> constexpr size_t tile_bytes() {
     return sizeof(float) * (3 * ZH * ZW + 3 * PH * PW + 3 * PH * TW + 3 * Coarse<RC>::UH * Coarse<RC>::UW) +
-           TH * TW;
+           sizeof(uint16_t) * TH * TW;
 }
 
 __device__ __forceinline__ void rgb_to_work(float r, float g, float b, int color, float& y, float& cb, float& cr) {
@@ -173,7 +173,7 @@ __device__ __forceinline__ float apply_filter(const TB* __restrict__ hb, const f
 
 template <int RF, int RC, bool CROSS, typename TS, typename TB, bool SMEM, bool FILTER>
 __global__ void __launch_bounds__(NT) k_level(const TS* __restrict__ z, const TS* __restrict__ coarse,
-                                              TS* __restrict__ out, uint8_t* __restrict__ bmap,
+                                              TS* __restrict__ out, void* __restrict__ bmap,
                                               const TB* __restrict__ bank, int H, int W, int Hc, int Wc,
                                               int nimg, int K, int color, SelParams sp, float w0, float w1,
                                               float w2) {
@@ -185,8 +185,9 @@ __global__ void __launch_bounds__(NT) k_level(const TS* __restrict__ z, const TS
     float* ps = zs + 3 * ZH * ZW;                            // [3][PH][PW]
     float* hs = ps + 3 * PH * PW;                            // [3][PH][TW]
     float* us = hs + 3 * PH * TW;                            // [3][UH][UW]
-    uint8_t* bk = reinterpret_cast<uint8_t*>(us + 3 * UH * UW);  // [TH][TW]
+    uint16_t* bk = reinterpret_cast<uint16_t*>(us + 3 * UH * UW);  // [TH][TW]
     TB* bank_s = reinterpret_cast<TB*>(smem + ((tile_bytes<RC>() + 15) & ~size_t(15)));
+    const bool wide = K > 256;   // bucket map element: u8, or u16 above 256 buckets
     const int tid = threadIdx.x;
     const float wv[5] = {w0, w1, w2, w1, w0};
 
@@ -282,9 +283,13 @@ __global__ void __launch_bounds__(NT) k_level(const TS* __restrict__ z, const TS
             }
             int k = bucket_of(t3[0], t3[1], t3[2], sp);
             k = k < K ? k : K - 1;
-            bk[i] = (uint8_t)k;
+            bk[i] = (uint16_t)k;
             int gy = y0 + r, gx = x0 + q;
-            if (bmap && gy < H && gx < W) bmap[((int64_t)img * H + gy) * W + gx] = (uint8_t)k;
+            if (bmap && gy < H && gx < W) {
+                const int64_t o = ((int64_t)img * H + gy) * W + gx;
+                if (wide) static_cast<uint16_t*>(bmap)[o] = (uint16_t)k;
+                else static_cast<uint8_t*>(bmap)[o] = (uint8_t)k;
+            }
         }
         if constexpr (FILTER) {
             __syncthreads();
@@ -697,7 +702,7 @@ int run2(const LevelArgs& a, cudaStream_t s) {
     if (grid > tiles) grid = tiles;
     float w[5];
     gauss5_weights(w);
-    kern<<<(unsigned)grid, SH::NT, bytes, s>>>((const TS*)a.z, (const TS*)a.coarse, (TS*)a.out, a.buckets,
+    kern<<<(unsigned)grid, SH::NT, bytes, s>>>((const TS*)a.z, (const TS*)a.coarse, (TS*)a.out, (uint8_t*)a.buckets,
                                                (const TB*)a.bank, (int)a.h, (int)a.w, (int)a.hc, (int)a.wc,
                                                (int)a.n, a.K, a.geom.color, a.sel, w[0], w[1], w[2]);
     return check_launch("k_level2");
@@ -1067,7 +1072,7 @@ int run3(const LevelArgs& a, cudaStream_t s) {
     if (grid > tiles) grid = tiles;
     float w[5];
     gauss5_weights(w);
-    kern<<<(unsigned)grid, NT, bytes, s>>>((const TS*)a.z, (const TS*)a.coarse, (TS*)a.out, a.buckets,
+    kern<<<(unsigned)grid, NT, bytes, s>>>((const TS*)a.z, (const TS*)a.coarse, (TS*)a.out, (uint8_t*)a.buckets,
                                            (const TB*)a.bank, (int)a.h, (int)a.w, (int)a.hc, (int)a.wc,
                                            (int)a.n, a.K, a.geom.color, a.sel, w[0], w[1], w[2]);
     return check_launch("k_level3");
@@ -1085,9 +1090,9 @@ template <typename TS, typename TB> int dispatch(const LevelArgs& a, cudaStream_
     const mdn_geometry& g = a.geom;
 #define MDN_GEO(RF_, RC_, CR_)                                                                  \
     if (g.r_fine == RF_ && g.r_coarse == RC_ && (g.cross_channel != 0) == CR_) {                \
-        if (MDN_USE_V3 && v3::smem_need<RF_, RC_, CR_, TB>(a.K) <= SMEM_LIMIT)                \
+        if (MDN_USE_V3 && a.K <= 256 && v3::smem_need<RF_, RC_, CR_, TB>(a.K) <= SMEM_LIMIT)  \
             return v3::run3<RF_, RC_, CR_, TS, TB>(a, s);                                      \
-        if (v2::smem_need<RF_, RC_, CR_, TB>(a.K) <= SMEM_LIMIT)                              \
+        if (a.K <= 256 && v2::smem_need<RF_, RC_, CR_, TB>(a.K) <= SMEM_LIMIT)                \
             return v2::run2<RF_, RC_, CR_, TS, TB>(a, s);                                      \
         if (smem_need<RF_, RC_, CR_, TB>(a.K) <= SMEM_LIMIT)                                  \
             return run<RF_, RC_, CR_, TS, TB, true, true>(a, s);                              \

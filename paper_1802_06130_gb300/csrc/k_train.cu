@@ -75,7 +75,9 @@ __global__ void k_to_work(const TS* __restrict__ in, void* __restrict__ outv, in
     d[0] = yy; d[hwp] = cb; d[2 * hwp] = cr;
 }
 
-__global__ void k_hist(const uint8_t* __restrict__ bmap, int64_t npix, int K, int* __restrict__ blockhist) {
+// Per-block bucket histograms; TK = uint8_t (K <= 256) or uint16_t.
+template <typename TK>
+__global__ void k_hist(const TK* __restrict__ bmap, int64_t npix, int K, int* __restrict__ blockhist) {
     __shared__ int h[MDN_MAX_K];
     for (int k = threadIdx.x; k < K; k += blockDim.x) h[k] = 0;
     __syncthreads();
@@ -90,7 +92,7 @@ __global__ void k_hist(const uint8_t* __restrict__ bmap, int64_t npix, int K, in
 // (blocks of SORT_CHUNK pixels, grouped into SCAN_SEGS segments):
 //   k_segsum  segsum[s][k] = sum of blockhist over segment s's blocks
 //   k_scan    bstart[k], bcount[k] and segoff[s][k] = start of segment s's
-//             bucket-k run in the sorted list (one CTA)
+//             bucket-k run in the sorted list (one CTA, below)
 //   k_offs    offs[b][k] = start of block b's bucket-k run
 constexpr int SCAN_SEGS = 64;
 
@@ -100,31 +102,6 @@ __global__ void k_segsum(const int* __restrict__ blockhist, int nblk, int K, int
         int t = 0;
         for (int b = b0; b < b1; ++b) t += blockhist[(int64_t)b * K + k];
         segsum[sg * K + k] = t;
-    }
-}
-
-__global__ void k_scan(const int* __restrict__ segsum, int nseg, int K, int64_t* __restrict__ bstart,
-                       int64_t* __restrict__ bcount, int* __restrict__ segoff) {
-    __shared__ int64_t tot[MDN_MAX_K], st[MDN_MAX_K];
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        int64_t t = 0;
-        for (int sg = 0; sg < nseg; ++sg) t += segsum[sg * K + k];
-        tot[k] = t;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int64_t run = 0;
-        for (int k = 0; k < K; ++k) { st[k] = run; run += tot[k]; }
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        bstart[k] = st[k];
-        bcount[k] = tot[k];
-        int64_t run = st[k];
-        for (int sg = 0; sg < nseg; ++sg) {
-            segoff[sg * K + k] = (int)run;
-            run += segsum[sg * K + k];
-        }
     }
 }
 
@@ -157,6 +134,32 @@ __device__ int block_exclusive_scan(int v, int* tmp, int* total) {
     return incl - v;
 }
 
+// One CTA (256 threads); thread t owns the contiguous buckets
+// [t * per, (t + 1) * per), per = ceil(K / 256), so any K <= MDN_MAX_K works.
+__global__ void __launch_bounds__(256) k_scan(const int* __restrict__ segsum, int nseg, int K,
+                                              int64_t* __restrict__ bstart, int64_t* __restrict__ bcount,
+                                              int* __restrict__ segoff) {
+    __shared__ int tmp[256];
+    __shared__ int total;
+    const int per = (K + blockDim.x - 1) / blockDim.x;
+    const int k0 = min((int)threadIdx.x * per, K), k1 = min(k0 + per, K);
+    int mine = 0;
+    for (int k = k0; k < k1; ++k) {
+        int t = 0;
+        for (int sg = 0; sg < nseg; ++sg) t += segsum[sg * K + k];
+        bcount[k] = t;
+        mine += t;
+    }
+    int run = block_exclusive_scan(mine, tmp, &total);   // pixel counts are < 2^31
+    for (int k = k0; k < k1; ++k) {
+        bstart[k] = run;
+        for (int sg = 0; sg < nseg; ++sg) {
+            segoff[sg * K + k] = run;
+            run += segsum[sg * K + k];
+        }
+    }
+}
+
 // Chunk table of one pixel group (CTA per group).  A group is the pixel-index
 // range [g * GB, (g + 1) * GB): since the sorted list is ordered by bucket and
 // then by pixel index, the group's rows of bucket k form one contiguous run.
@@ -172,54 +175,73 @@ __global__ void __launch_bounds__(256) k_chunks(const int* __restrict__ offs, co
                                                 int* __restrict__ gcount) {
     __shared__ int tmp[256];
     __shared__ int total;
-    const int g = blockIdx.x, k = threadIdx.x;
-    int start = 0, len = 0;
-    if (k < K) {
-        const int b0 = g * bpg, b1 = b0 + bpg;
+    const int g = blockIdx.x;
+    const int b0 = g * bpg, b1 = b0 + bpg;
+    // thread t handles the contiguous buckets [k0, k1) (one bucket when K <= 256)
+    const int per = (K + blockDim.x - 1) / blockDim.x;
+    const int k0 = min((int)threadIdx.x * per, K), k1 = min(k0 + per, K);
+    auto run_of = [&](int k, int& start, int& len) {
         start = offs[(int64_t)b0 * K + k];
         const int end = b1 < nblk ? offs[(int64_t)b1 * K + k] : (int)(bstart[k] + bcount[k]);
         len = end - start;
+    };
+    int mine = 0;
+    for (int k = k0; k < k1; ++k) {
+        int st, ln;
+        run_of(k, st, ln);
+        mine += ln;
     }
-    const int v = block_exclusive_scan(len, tmp, &total);
+    const int vbase = block_exclusive_scan(mine, tmp, &total);   // group-relative row of bucket k0's run
     const int64_t grows = npix - g * GB < GB ? npix - g * GB : GB;
     int Q = chunk_rows;
     if (quantum_mode) {
         const int64_t q = (grows + ncta - 1) / ncta;
         Q = (int)(q > minq ? q : minq);
     }
-    int nck = 0;
-    if (len > 0) {
+    auto chunks_of = [&](int v, int len) {
+        if (len <= 0) return 0;
         if (quantum_mode) {
             const int inner = (v + len + Q - 1) / Q - 1 - v / Q;   // multiples of Q in (v, v + len)
-            nck = (inner > 0 ? inner : 0) + 1;
-        } else {
-            nck = (len + Q - 1) / Q;
+            return (inner > 0 ? inner : 0) + 1;
         }
+        return (len + Q - 1) / Q;
+    };
+    int nmine = 0;
+    for (int k = k0, v = vbase; k < k1; ++k) {
+        int st, ln;
+        run_of(k, st, ln);
+        nmine += chunks_of(v, ln);
+        v += ln;
     }
-    const int coff = block_exclusive_scan(nck, tmp, &total);
-    if (k < K) {
-        int j = coff;
+    const int cbase = block_exclusive_scan(nmine, tmp, &total);
+    int j = cbase;
+    for (int k = k0, v = vbase; k < k1; ++k) {
+        int start, len;
+        run_of(k, start, len);
         for (int r = v; r < v + len && j < cap; ++j) {
             int e = quantum_mode ? (r / Q + 1) * Q : r + Q;
             if (e > v + len) e = v + len;
             chunks[(int64_t)g * cap + j] = make_int4(k, start + (r - v), start + (e - v), quantum_mode ? r / Q : 0);
             r = e;
         }
+        v += len;
     }
-    if (k == 0) gcount[g] = total < cap ? total : cap;   // the capacity bounds the total by construction
+    if (threadIdx.x == 0) gcount[g] = total < cap ? total : cap;   // the capacity bounds the total by construction
 }
 
 // Stable scatter: pixels of a block are ranked in index order within their
 // bucket (warp match + per-warp counts), so the sorted list is deterministic.
+// K <= 256 (u8 maps).
 __global__ void __launch_bounds__(256) k_scatter(const uint8_t* __restrict__ bmap, int64_t npix, int K,
                                                  const int* __restrict__ offs, int* __restrict__ sorted) {
-    __shared__ int run[MDN_MAX_K];
-    __shared__ int wcnt[8][MDN_MAX_K];
+    constexpr int NK = 256;
+    __shared__ int run[NK];
+    __shared__ int wcnt[8][NK];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int k = threadIdx.x; k < K; k += blockDim.x) run[k] = offs[(int64_t)blockIdx.x * K + k];
     int64_t b0 = (int64_t)blockIdx.x * SORT_CHUNK;
     for (int64_t base = b0; base < b0 + SORT_CHUNK; base += blockDim.x) {
-        for (int i = threadIdx.x; i < 8 * MDN_MAX_K; i += blockDim.x) (&wcnt[0][0])[i] = 0;
+        for (int i = threadIdx.x; i < 8 * NK; i += blockDim.x) (&wcnt[0][0])[i] = 0;
         __syncthreads();
         int64_t i = base + threadIdx.x;
         bool valid = i < npix;
@@ -240,6 +262,34 @@ __global__ void __launch_bounds__(256) k_scatter(const uint8_t* __restrict__ bma
             run[kk] += s;
         }
         __syncthreads();
+    }
+}
+
+// The same stable scatter for K > 256 (u16 maps): one warp per block walks the
+// block's pixels 32 at a time in index order; lanes holding the same bucket
+// are ranked by lane, and the leader advances the bucket's run offset after
+// the warp has read it.
+__global__ void __launch_bounds__(32) k_scatter_wide(const uint16_t* __restrict__ bmap, int64_t npix, int K,
+                                                     const int* __restrict__ offs, int* __restrict__ sorted) {
+    __shared__ int run[MDN_MAX_K];
+    const int lane = threadIdx.x;
+    for (int k = lane; k < K; k += 32) run[k] = offs[(int64_t)blockIdx.x * K + k];
+    __syncwarp();
+    const int64_t b0 = (int64_t)blockIdx.x * SORT_CHUNK;
+    const int64_t e = b0 + SORT_CHUNK < npix ? b0 + SORT_CHUNK : npix;
+    for (int64_t base = b0; base < e; base += 32) {
+        const int64_t i = base + lane;
+        const bool valid = i < e;
+        const int k = valid ? (int)bmap[i] : 0x7fffffff - lane;   // invalid lanes never match a bucket
+        const unsigned m = __match_any_sync(0xffffffffu, k);
+        const int rank = __popc(m & ((1u << lane) - 1u));
+        const int pos = valid ? run[k] + rank : 0;
+        __syncwarp();
+        if (valid) {
+            sorted[pos] = (int)i;
+            if (rank == 0) run[k] += __popc(m);
+        }
+        __syncwarp();
     }
 }
 
@@ -553,11 +603,14 @@ int launch_gram(const TrainArgs& a, cudaStream_t s) {
     // sort: per-block histograms, bucket offsets, stable scatter
     const int seglen = (int)((nblk + SCAN_SEGS - 1) / SCAN_SEGS);
     const int nseg = (int)((nblk + seglen - 1) / seglen);
-    k_hist<<<(unsigned)nblk, TB, 0, s>>>(a.buckets, npix, a.K, blockhist);
+    const bool wide = a.K > 256;   // u16 bucket map
+    if (wide) k_hist<uint16_t><<<(unsigned)nblk, TB, 0, s>>>((const uint16_t*)a.buckets, npix, a.K, blockhist);
+    else k_hist<uint8_t><<<(unsigned)nblk, TB, 0, s>>>((const uint8_t*)a.buckets, npix, a.K, blockhist);
     k_segsum<<<nseg, TB, 0, s>>>(blockhist, (int)nblk, a.K, seglen, segsum);
     k_scan<<<1, TB, 0, s>>>(segsum, nseg, a.K, bstart, bcount, segoff);
     k_offs<<<nseg, TB, 0, s>>>(blockhist, segoff, (int)nblk, a.K, seglen, offs);
-    k_scatter<<<(unsigned)nblk, TB, 0, s>>>(a.buckets, npix, a.K, offs, sorted);
+    if (wide) k_scatter_wide<<<(unsigned)nblk, 32, 0, s>>>((const uint16_t*)a.buckets, npix, a.K, offs, sorted);
+    else k_scatter<<<(unsigned)nblk, TB, 0, s>>>((const uint8_t*)a.buckets, npix, a.K, offs, sorted);
     // chunk tables: tensor cores one CTA per SM, each taking a share of every group
     const int ncta = num_sms() < GRAM_MAX_CTAS ? num_sms() : GRAM_MAX_CTAS;
     k_chunks<<<gq.ngroups, TB, 0, s>>>(offs, bstart, bcount, a.K, (int)nblk, (int)(gq.GB / SORT_CHUNK), npix, gq.GB,

@@ -61,7 +61,7 @@ int scratch_address(void** out) {
 extern "C" int mdn_denoise_multiscale_static(const void* noisy, int32_t dtype, int64_t n, int64_t h, int64_t w,
                                              int32_t levels, const void* const* banks, int32_t bank_dtype,
                                              const mdn_geometry* geom, const mdn_bucket_params* bparams,
-                                             void* out, uint8_t* const* bucket_maps, void* stream) {
+                                             void* out, void* const* bucket_maps, void* stream) {
     using namespace mdn;
     if (levels < 1 || levels > 8) return fail(MDN_EINVAL, "denoise_multiscale_static: levels must be 1..8");
     if (n < 0 || h < 0 || w < 0) return fail(MDN_ESHAPE, "denoise_multiscale_static: negative size");

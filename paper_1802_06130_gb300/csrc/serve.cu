@@ -330,6 +330,9 @@ static int build_tables(mdn_server* s, const mdn_bankset* sets, int nsets, Table
             if (rc) return rc;
             tb->bank[nb] = (const __half*)bs.banks[l];
             tb->K[nb] = bs.bparams[l].n_angle * bs.bparams[l].n_strength * bs.bparams[l].n_coherence;
+            if (tb->K[nb] > 256)
+                return fail(MDN_ESHAPE, "server: a bank set level has more than 256 buckets (the serving "
+                                        "kernels hold the bank in shared memory)");
             tb->color[nb] = bs.color;
             s->Kmax = std::max(s->Kmax, tb->K[nb]);
             st.bank_index[l] = nb++;

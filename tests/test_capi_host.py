@@ -5,6 +5,7 @@ import ctypes as C
 import os
 import re
 
+import numpy as np
 import pytest
 
 import paper_1802_06130_gb300 as mdn
@@ -111,6 +112,52 @@ def test_bad_arguments_rejected_without_device(L):
     rc = L.mdn_augment_dihedral(C.c_void_p(16), C.c_void_p(24), C.byref(g1), C.byref(mdn.BucketParams(23)),
                                 C.c_void_p(32), C.c_void_p(48), None)
     assert rc == 1 and b"n_angle" in L.mdn_last_error()
+
+
+def test_wide_bucket_grids_host(L):
+    """Grids up to 4096 buckets: map element size, limits, workspace."""
+    assert [L.mdn_bucket_elem_bytes(k) for k in (0, 1, 216, 256, 257, 4096, 4097)] == [0, 1, 1, 1, 2, 2, 0]
+    bp = mdn.paper_grid_bparams(0)
+    assert (bp.n_angle, bp.n_strength, bp.n_coherence, bp.K) == (16, 16, 16, 4096)
+    too_many = mdn.paper_grid_bparams(0)
+    too_many.n_angle = 18                      # 18 x 16 x 16 = 4608 buckets
+    rc = L.mdn_select_buckets(C.c_void_p(16), 0, 1, 8, 8, C.byref(too_many), C.c_void_p(16), None)
+    assert rc == 1 and b"4096" in L.mdn_last_error()
+    bad = mdn.paper_grid_bparams(0)
+    bad.n_strength = 18                        # more thresholds than the struct holds
+    rc = L.mdn_select_buckets(C.c_void_p(16), 0, 1, 8, 8, C.byref(bad), C.c_void_p(16), None)
+    assert rc == 1 and b"1..17" in L.mdn_last_error()
+    g = mdn.Geometry(3, 2)
+    n, h, w = 2, 64, 48
+    wide = L.mdn_train_workspace_bytes(n, h, w, C.byref(g), 4096, mdn.GRAM_TF32)
+    narrow = L.mdn_train_workspace_bytes(n, h, w, C.byref(g), 216, mdn.GRAM_TF32)
+    assert wide > narrow + n * h * w           # u16 map and 4096-entry sort tables
+    assert L.mdn_gram_state_bytes(C.byref(g), 4096) == 4096 * 3 * 75 * 75 * 8
+    assert L.mdn_solve_workspace_bytes(C.byref(g), 4096) > 0
+
+
+def test_paper_grid_parameters_agree_with_the_oracle():
+    """The binding's and the oracle's 16 x 16 x 16 thresholds are the same
+    numbers (selector parameters, defined on each side)."""
+    import oracle as O
+    for level in range(4):
+        a, b = mdn.paper_grid_bparams(level), O.paper_grid_bparams(level)
+        assert a.K == b.K == 4096
+        assert np.allclose(list(a.strength_thr)[:15], b.strength_thr, rtol=1e-6)
+        assert np.allclose(list(a.coherence_thr)[:15], b.coherence_thr, rtol=1e-6)
+        assert all(np.diff(b.strength_thr) > 0) and all(np.diff(b.coherence_thr) > 0)
+
+
+def test_bucket_map_guard_rejects_wrong_type():
+    """The binding checks a caller's bucket map before the library writes
+    1 or 2 bytes per pixel into it."""
+    torch = pytest.importorskip("torch")
+    with pytest.raises(ValueError):
+        mdn._map(torch.empty((1, 4, 4), dtype=torch.uint8), 4096, 1, 4, 4, "m")
+    with pytest.raises(ValueError):
+        mdn._map(torch.empty((1, 4, 4), dtype=torch.int16), 216, 1, 4, 4, "m")
+    with pytest.raises(ValueError):
+        mdn._map(torch.empty((1, 4, 3), dtype=torch.int16), 4096, 1, 4, 4, "m")
 
 
 def test_product_path_has_no_oracle_dependency():

@@ -390,6 +390,45 @@ def test_planted_bank_recovered(geom):
     assert checked >= 5
 
 
+def test_wide_grid_bucket_decomposition():
+    """The 16 x 16 x 16 map is (a * 16 + s) * 16 + c with a, s and c each taken
+    from a grid that bins that feature alone; values above 255 survive (u16)."""
+    z, _ = synth.noisy_pair(96, 80, 61)
+    bp = O.paper_grid_bparams(0)
+    full, _, _ = O.select(z, bp)
+    assert full.dtype == np.uint16 and full.max() > 255
+    a, _, _ = O.select(z, O.BucketParams(16, (), ()))
+    s, _, _ = O.select(z, O.BucketParams(16, bp.strength_thr, ()))
+    c, _, _ = O.select(z, O.BucketParams(16, (), bp.coherence_thr))
+    a = a.astype(np.int64)
+    s = s.astype(np.int64) - 16 * a
+    c = c.astype(np.int64) - 16 * a
+    assert s.min() >= 0 and s.max() <= 15 and c.min() >= 0 and c.max() <= 15
+    assert np.array_equal(full.astype(np.int64), (a * 16 + s) * 16 + c)
+
+
+def test_planted_bank_recovered_above_256_buckets():
+    """Buckets numbered above 255 (4096-bucket bank, 7x7 + 5x5 taps): targets
+    made by a planted bank are fitted exactly at those buckets, so the filter
+    and the Gram sums index the same bank rows."""
+    rng = np.random.default_rng(12)
+    geom = O.Geometry(3, 2)
+    z, _ = synth.noisy_pair(96, 96, 33)
+    uc = O.pyramid_down(z)
+    used = np.array([7, 300, 1000, 4095])
+    bk = used[rng.integers(0, 4, (96, 96))].astype(np.uint16)
+    planted = rng.standard_normal((4096, 3, geom.D())) * 0.05
+    target = O.filter_level(z, uc, bk, planted, geom)
+    gram, counts = O.gram_accumulate(z, uc, target, bk, 4096, geom)
+    assert set(np.flatnonzero(counts)) == set(used)
+    D = geom.D()
+    for k in used:
+        for g in range(3):
+            h = O.cholesky_solve(gram[k, g, :D, :D], gram[k, g, :D, D:])
+            err = np.linalg.norm(h[:, 0] - planted[k, g]) / np.linalg.norm(planted[k, g])
+            assert err < 1e-8, (k, g, err)
+
+
 def test_cascade_with_identity_banks_returns_input():
     geom = O.Geometry(3, 3)
     z, _ = synth.noisy_pair(30, 26, 41)
