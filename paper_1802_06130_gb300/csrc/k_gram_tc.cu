@@ -21,8 +21,9 @@
 // rounding in the ridge solve.  TF32 operands are rounded to nearest.
 // Precisions: TF32 (kind::tf32), BF16 (kind::f16, BF16 operands) and split
 // BF16 (x = hi + lo, G ~ hi hi^T + hi lo^T + lo hi^T, three MMAs).  FP32
-// accumulation in TMEM; each chunk's upper triangle is written as an FP32
-// partial and reduced in FP64 by k_reduce_sum and k_center (k_train.cu).
+// accumulation in TMEM; each chunk's symmetric matrix is written as an FP32
+// partial (lower triangle, row-major) and reduced in FP64 by k_reduce_sum
+// and k_center (k_train.cu).
 //
 // Work split.  The sorted rows are walked in pixel groups (pixel-index ranges
 // whose working planes fit in L2); each group's rows are cut into one share
@@ -48,7 +49,12 @@
 //                 commits them to empty[s] (which frees stage and pixel slot
 //                 s); at a chunk end it commits acc_full
 //   warps 0..3    wait acc_full, read the accumulator (TMEM lane quarter w),
-//                 write the chunk's partial, arrive acc_empty
+//                 write the chunk's partial, arrive acc_empty.  Lane = row i
+//                 of the accumulator, so entry (i, j) goes to the lower
+//                 triangle at j * Dq + i: a warp's 32 rows are 32 consecutive
+//                 floats (one coalesced store per column).  The stores are
+//                 streaming (evict-first): with many buckets the partials of a
+//                 pixel group exceed L2 and must not evict the group's planes
 // Every wait is bounded by a time limit: on expiry the CTA raises a shared
 // abort flag that ends every role's loop, waits (bounded) for its issued MMAs,
 // frees its TMEM, and reports the error through g_gram_error.
@@ -627,7 +633,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                     for (int e = 0; e < 16; ++e) {
                         const int j = c0_ + e;
-                        if (row < Dq && j < Dq && row <= j) og[(size_t)row * Dq + j] = v[e];
+                        if (row < Dq && j < Dq && row <= j) __stcs(og + (size_t)j * Dq + row, v[e]);   // lanes: consecutive
                     }
                 }
                 if (two) {
@@ -638,7 +644,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                         for (int e = 0; e < 16; ++e) {
                             const int j = 128 + c0_ + e;
-                            if (i >= 128 && i < Dq && j < Dq && i <= j) og[(size_t)i * Dq + j] = v[e];
+                            if (i >= 128 && i < Dq && j < Dq && i <= j) __stcs(og + (size_t)j * Dq + i, v[e]);
                         }
                     }
                 }

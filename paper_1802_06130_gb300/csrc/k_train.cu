@@ -164,15 +164,18 @@ __global__ void __launch_bounds__(256) k_scan(const int* __restrict__ segsum, in
 // range [g * GB, (g + 1) * GB): since the sorted list is ordered by bucket and
 // then by pixel index, the group's rows of bucket k form one contiguous run.
 // Group g's chunks, in bucket order, go to chunks[g * cap ...], each
-// (k, begin, end, w): quantum mode (tensor cores) cuts the runs at every
-// multiple of Q = max(ceil(group rows / ncta), minq) of the group's virtual row
-// position and records w = the CTA that owns the chunk (position / Q);
-// otherwise runs are cut into pieces of at most chunk_rows rows (w = 0).
+// (k, begin, end, w), and crange[g][k] gets bucket k's chunk range.
+// Quantum mode (tensor cores) balances the CTAs by cost: a non-empty run costs
+// its rows plus run_cost rows (the fixed work of a chunk: draining and
+// reading back the accumulator), the runs are laid end to end in that cost
+// space, cut at every multiple of Q = max(ceil(total cost / ncta), minq), and
+// each chunk records w = the CTA that owns it (cost position of its first row
+// / Q).  Otherwise runs are cut into pieces of at most chunk_rows rows (w = 0).
 __global__ void __launch_bounds__(256) k_chunks(const int* __restrict__ offs, const int64_t* __restrict__ bstart,
                                                 const int64_t* __restrict__ bcount, int K, int nblk, int bpg,
-                                                int64_t npix, int64_t GB, int quantum_mode, int ncta, int minq,
+                                                int quantum_mode, int ncta, int minq, int run_cost,
                                                 int chunk_rows, int cap, int4* __restrict__ chunks,
-                                                int* __restrict__ gcount) {
+                                                int* __restrict__ gcount, int2* __restrict__ crange) {
     __shared__ int tmp[256];
     __shared__ int total;
     const int g = blockIdx.x;
@@ -180,24 +183,27 @@ __global__ void __launch_bounds__(256) k_chunks(const int* __restrict__ offs, co
     // thread t handles the contiguous buckets [k0, k1) (one bucket when K <= 256)
     const int per = (K + blockDim.x - 1) / blockDim.x;
     const int k0 = min((int)threadIdx.x * per, K), k1 = min(k0 + per, K);
+    const int A = quantum_mode ? run_cost : 0;
     auto run_of = [&](int k, int& start, int& len) {
         start = offs[(int64_t)b0 * K + k];
         const int end = b1 < nblk ? offs[(int64_t)b1 * K + k] : (int)(bstart[k] + bcount[k]);
         len = end - start;
     };
+    auto cost_of = [&](int len) { return len > 0 ? len + A : 0; };
     int mine = 0;
     for (int k = k0; k < k1; ++k) {
         int st, ln;
         run_of(k, st, ln);
-        mine += ln;
+        mine += cost_of(ln);
     }
-    const int vbase = block_exclusive_scan(mine, tmp, &total);   // group-relative row of bucket k0's run
-    const int64_t grows = npix - g * GB < GB ? npix - g * GB : GB;
+    const int vbase = block_exclusive_scan(mine, tmp, &total);   // cost position of bucket k0's run
+    const int ctot = total;
     int Q = chunk_rows;
     if (quantum_mode) {
-        const int64_t q = (grows + ncta - 1) / ncta;
-        Q = (int)(q > minq ? q : minq);
+        const int q = (ctot + ncta - 1) / ncta;
+        Q = q > minq ? q : minq;
     }
+    // a run's rows sit at cost positions [v, v + len), v = run start + A
     auto chunks_of = [&](int v, int len) {
         if (len <= 0) return 0;
         if (quantum_mode) {
@@ -207,24 +213,26 @@ __global__ void __launch_bounds__(256) k_chunks(const int* __restrict__ offs, co
         return (len + Q - 1) / Q;
     };
     int nmine = 0;
-    for (int k = k0, v = vbase; k < k1; ++k) {
+    for (int k = k0, c = vbase; k < k1; ++k) {
         int st, ln;
         run_of(k, st, ln);
-        nmine += chunks_of(v, ln);
-        v += ln;
+        nmine += chunks_of(c + A, ln);
+        c += cost_of(ln);
     }
     const int cbase = block_exclusive_scan(nmine, tmp, &total);
     int j = cbase;
-    for (int k = k0, v = vbase; k < k1; ++k) {
+    for (int k = k0, c = vbase; k < k1; ++k) {
         int start, len;
         run_of(k, start, len);
+        const int j0 = j, v = c + A;
         for (int r = v; r < v + len && j < cap; ++j) {
             int e = quantum_mode ? (r / Q + 1) * Q : r + Q;
             if (e > v + len) e = v + len;
             chunks[(int64_t)g * cap + j] = make_int4(k, start + (r - v), start + (e - v), quantum_mode ? r / Q : 0);
             r = e;
         }
-        v += len;
+        crange[(int64_t)g * K + k] = make_int2(g * cap + j0, g * cap + j);   // bucket k's chunks in group g
+        c += cost_of(len);
     }
     if (threadIdx.x == 0) gcount[g] = total < cap ? total : cap;   // the capacity bounds the total by construction
 }
@@ -296,7 +304,8 @@ __global__ void __launch_bounds__(32) k_scatter_wide(const uint16_t* __restrict_
 // ---------------------------------------------------------------- SIMT Gram
 
 // Gram of one chunk, FP32 products/accumulation, 4x4 register blocks of the
-// upper triangle of every group's Dp x Dp matrix.
+// upper triangle of every group's Dp x Dp matrix, written to the partial in the
+// lower-triangle layout k_reduce_sum reads.
 __global__ void __launch_bounds__(256) k_gram_simt(GatherArgs ga, const int4* __restrict__ chunks,
                                                     const int* __restrict__ nchunks, const int* __restrict__ sorted,
                                                     float* __restrict__ partial) {
@@ -357,42 +366,33 @@ __global__ void __launch_bounds__(256) k_gram_simt(GatherArgs ga, const int4* __
         for (int p = 0; p < 4; ++p)
             for (int q = 0; q < 4; ++q) {
                 int i = bi[m] * 4 + p, j = bj[m] * 4 + q;
-                if (i < Dq && j < Dq && i <= j) out[((size_t)bg[m] * Dq + i) * Dq + j] = acc[m][p * 4 + q];
+                if (i < Dq && j < Dq && i <= j) out[((size_t)bg[m] * Dq + j) * Dq + i] = acc[m][p * 4 + q];
             }
     }
 }
 
 // FP64 reduction of a bucket's chunk partials in group order, then chunk order
-// (deterministic), in two passes.  Partials are (Dq = Dp + 1)^2 upper
-// triangles of the shifted rows with the ones column last.  Group g's chunks
-// are chunks[g * cap, g * cap + gcount[g]), in bucket order.
-//   k_reduce_sum  S[k][g] = sum of the bucket's partials (upper triangle)
+// (deterministic), in two passes.  Partials are (Dq = Dp + 1)^2 symmetric
+// matrices of the shifted rows with the ones column last, of which the lower
+// triangle (row-major: entry (a, b), a >= b, at a * Dq + b) is written.
+// crange[g][k] = bucket k's chunk range in group g (from k_chunks).
+//   k_reduce_sum  S[k][g] = sum of the bucket's partials (lower triangle)
 //   k_center      the exact centring correction
 //                 G_ij = S_ij + c_i s_j + c_j s_i + n c_i c_j,
-//                 s_i = S_{i,ones}, n = S_{ones,ones}, added into gram[k][g]
-__global__ void k_reduce_sum(const float* __restrict__ partial, const int4* __restrict__ chunks,
-                             const int* __restrict__ gcount, int ngroups, int cap, int G, int Dq,
-                             double* __restrict__ S) {
+//                 s_i = S_{ones,i}, n = S_{ones,ones}, added into gram[k][g]
+__global__ void k_reduce_sum(const float* __restrict__ partial, const int2* __restrict__ crange, int ngroups,
+                             int K, int G, int Dq, double* __restrict__ S) {
     const int k = blockIdx.y;
     const int64_t entq = (int64_t)G * Dq * Dq;
-    __shared__ int lo_s[GRAM_MAX_GROUPS], hi_s[GRAM_MAX_GROUPS];
-    for (int g = threadIdx.x; g < ngroups; g += blockDim.x) {
-        const int base = g * cap, nc = gcount[g];
-        int lo = 0, hi = nc;
-        while (lo < hi) { int mid = (lo + hi) / 2; if (chunks[base + mid].x < k) lo = mid + 1; else hi = mid; }
-        const int c0 = lo;
-        hi = nc;
-        while (lo < hi) { int mid = (lo + hi) / 2; if (chunks[base + mid].x <= k) lo = mid + 1; else hi = mid; }
-        lo_s[g] = base + c0;
-        hi_s[g] = base + lo;
-    }
+    __shared__ int2 rg[GRAM_MAX_GROUPS];
+    for (int g = threadIdx.x; g < ngroups; g += blockDim.x) rg[g] = crange[(int64_t)g * K + k];
     __syncthreads();
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < entq; e += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)((e / Dq) % Dq), j = (int)(e % Dq);
-        if (i > j) continue;
+        const int a = (int)((e / Dq) % Dq), b = (int)(e % Dq);
+        if (a < b) continue;
         double acc = 0.0;
         for (int gr = 0; gr < ngroups; ++gr)
-            for (int c = lo_s[gr]; c < hi_s[gr]; ++c) acc += (double)partial[(size_t)c * entq + e];
+            for (int c = rg[gr].x; c < rg[gr].y; ++c) acc += (double)__ldcs(partial + (size_t)c * entq + e);
         S[(size_t)k * entq + e] = acc;
     }
 }
@@ -407,8 +407,8 @@ __global__ void k_center(const double* __restrict__ S, const int64_t* __restrict
         const int g = (int)(e / ((int64_t)Dp * Dp));
         const int i = (int)((e / Dp) % Dp), j = (int)(e % Dp);
         if (i > j) continue;
-        const double* Sq = S + ((size_t)k * G + g) * Dq * Dq;
-        const double sij = Sq[(size_t)i * Dq + j], si = Sq[(size_t)i * Dq + Dp], sj = Sq[(size_t)j * Dq + Dp];
+        const double* Sq = S + ((size_t)k * G + g) * Dq * Dq;   // lower triangle
+        const double sij = Sq[(size_t)j * Dq + i], si = Sq[(size_t)Dp * Dq + i], sj = Sq[(size_t)Dp * Dq + j];
         const double n = Sq[(size_t)Dp * Dq + Dp];
         const double ci = channel_center(feature_channel(i, g, D, rf, rc, cross), color);
         const double cj = channel_center(feature_channel(j, g, D, rf, rc, cross), color);
@@ -551,6 +551,7 @@ size_t train_ws_bytes(int64_t n, int64_t h, int64_t w, int P, bool coarse, int K
     b += align256(sizeof(int) * SCAN_SEGS * K) * 2;   // segsum, segoff
     b += align256(sizeof(int64_t) * K) * 2;           // bstart, bcount
     b += align256(sizeof(int4) * nent) + align256(sizeof(int) * gq.ngroups);   // chunk tables, counts
+    b += align256(sizeof(int2) * gq.ngroups * K);                                // per (group, bucket) chunk ranges
     b += align256(sizeof(int) * (npix > 0 ? npix : 1));   // sorted
     b += align256(sizeof(float) * nent * G * (Dp + 1) * (Dp + 1));  // partials (Dp + 1 with the ones column)
     b += align256(sizeof(double) * K * G * (Dp + 1) * (Dp + 1));    // FP64 bucket sums
@@ -582,6 +583,7 @@ int launch_gram(const TrainArgs& a, cudaStream_t s) {
     int64_t* bcount = (int64_t*)take(sizeof(int64_t) * a.K);
     int4* chunks = (int4*)take(sizeof(int4) * nent);
     int* gcount = (int*)take(sizeof(int) * gq.ngroups);
+    int2* crange = (int2*)take(sizeof(int2) * gq.ngroups * a.K);
     int* sorted = (int*)take(sizeof(int) * (npix > 0 ? npix : 1));
     float* partial = (float*)take(sizeof(float) * nent * a.G * (a.Dp + 1) * (a.Dp + 1));
     double* bsum = (double*)take(sizeof(double) * a.K * a.G * (a.Dp + 1) * (a.Dp + 1));
@@ -613,8 +615,9 @@ int launch_gram(const TrainArgs& a, cudaStream_t s) {
     else k_scatter<<<(unsigned)nblk, TB, 0, s>>>((const uint8_t*)a.buckets, npix, a.K, offs, sorted);
     // chunk tables: tensor cores one CTA per SM, each taking a share of every group
     const int ncta = num_sms() < GRAM_MAX_CTAS ? num_sms() : GRAM_MAX_CTAS;
-    k_chunks<<<gq.ngroups, TB, 0, s>>>(offs, bstart, bcount, a.K, (int)nblk, (int)(gq.GB / SORT_CHUNK), npix, gq.GB,
-                                       tensor ? 1 : 0, ncta, GRAM_MIN_QUANTUM, GRAM_CHUNK, gq.cap, chunks, gcount);
+    k_chunks<<<gq.ngroups, TB, 0, s>>>(offs, bstart, bcount, a.K, (int)nblk, (int)(gq.GB / SORT_CHUNK),
+                                       tensor ? 1 : 0, ncta, GRAM_MIN_QUANTUM, GRAM_RUN_COST, GRAM_CHUNK, gq.cap,
+                                       chunks, gcount, crange);
     int rc = check_launch("train: sort");
     if (rc) return rc;
 
@@ -638,7 +641,7 @@ int launch_gram(const TrainArgs& a, cudaStream_t s) {
     }
     const int Dq = a.Dp + 1;
     dim3 rg1((unsigned)((a.G * Dq * Dq + 255) / 256), (unsigned)a.K);
-    k_reduce_sum<<<rg1, 256, 0, s>>>(partial, chunks, gcount, gq.ngroups, gq.cap, a.G, Dq, bsum);
+    k_reduce_sum<<<rg1, 256, 0, s>>>(partial, crange, gq.ngroups, a.K, a.G, Dq, bsum);
     dim3 rg2((unsigned)((a.G * a.Dp * a.Dp + 255) / 256), (unsigned)a.K);
     k_center<<<rg2, 256, 0, s>>>(bsum, bcount, a.G, a.Dp, a.D, a.geom.r_fine, a.geom.r_coarse, a.geom.cross_channel,
                                  a.geom.color, a.gram, a.counts);

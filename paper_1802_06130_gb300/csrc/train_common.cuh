@@ -13,8 +13,15 @@ constexpr int GRAM_RB = 32;         // rows gathered per step (SIMT)
 constexpr int GRAM_MAX_DP = 160;
 constexpr int GRAM_MAX_CTAS = 160;  // tensor-core Gram: at most one CTA per SM, row quantum per CTA
 constexpr int GRAM_MIN_QUANTUM = 1024;
+// Fixed cost of one tensor-core chunk (accumulator drain and read-back) in
+// rows of gather work, used to balance the CTAs' shares of a pixel group.
+constexpr int GRAM_RUN_COST = 128;
 constexpr int GRAM_MAX_GROUPS = 64;  // pixel groups processed one after the other (L2-sized working set)
 constexpr double GRAM_GROUP_BYTES = 40e6;   // target working-plane bytes of one pixel group
+// Above 256 buckets every group has about K chunks, each with a fixed cost and
+// an FP32 partial: larger groups (fewer chunks) win until the planes leave L2
+// (16 x 1 MP, 4096 buckets, 7x7 + 5x5: 40 MB 22.0 ms, 100 MB 18.5, 250 MB 21.5).
+constexpr double GRAM_GROUP_BYTES_WIDE = 100e6;
 
 // Pixel groups of the Gram accumulation: the tensor-core path walks the
 // sorted rows group by group (pixel-index ranges of GB pixels, GB a multiple
@@ -35,7 +42,7 @@ inline GramGroups gram_groups(int64_t n, int64_t h, int64_t w, int P, bool coars
     }
     const double hw = (double)h * w, hc = (double)((h + 1) / 2), wc = (double)((w + 1) / 2);
     const double bpp = 12.0 * ((h + 2.0 * P) * (w + 2.0 * P) / hw + 1.0 + (coarse ? (hc + 2 * P) * (wc + 2 * P) / hw : 0.0));
-    int64_t gb = (int64_t)(GRAM_GROUP_BYTES / bpp) / SORT_CHUNK * SORT_CHUNK;
+    int64_t gb = (int64_t)((K > 256 ? GRAM_GROUP_BYTES_WIDE : GRAM_GROUP_BYTES) / bpp) / SORT_CHUNK * SORT_CHUNK;
     if (gb < SORT_CHUNK) gb = SORT_CHUNK;
     if ((npix + gb - 1) / gb > GRAM_MAX_GROUPS) gb = ((npix + GRAM_MAX_GROUPS - 1) / GRAM_MAX_GROUPS + SORT_CHUNK - 1) / SORT_CHUNK * SORT_CHUNK;
     q.GB = gb;
