@@ -211,3 +211,44 @@ def test_server_rejects_wide_bank_sets(mdn):
         mdn.Server([(banks, [mdn.paper_grid_bparams(0), mdn.paper_grid_bparams(1)])], budget_bytes=64 << 20,
                    autotune=False)
     assert ei.value.code == 2 and "256 buckets" in str(ei.value)
+
+
+# ------------------------------------------------------------ the u8 / u16 boundary
+
+def _edge_grid(K_target):
+    """16 x 4 x 4 = 256 buckets (the last u8 grid) or 2 x 12 x 11 = 264 (the
+    first u16 one), thresholds from the 16-bin tables."""
+    st, co = O.paper_grid_bparams(0).strength_thr, O.paper_grid_bparams(0).coherence_thr
+    if K_target == 256:
+        return O.BucketParams(16, st[3::4][:3], co[3::4][:3])
+    return O.BucketParams(2, st[2:13], co[3:13])
+
+
+@pytest.mark.parametrize("Kt", [256, 264])
+def test_bucket_map_type_boundary(mdn, Kt):
+    bp = _edge_grid(Kt)
+    assert bp.K == Kt
+    z, u = synth.noisy_pair(128, 96, 5800 + Kt)
+    ref, band, _ = O.select(z, bp, mirror32=True)
+    got_t = mdn.select_buckets(_tt(z, "f32")[None], _gbp(mdn, bp))[0]
+    assert got_t.dtype == (torch.uint8 if Kt <= 256 else torch.int16)
+    got = _map(got_t)
+    mism = got != ref.astype(np.int64)
+    assert not (mism & ~band).any()
+    assert got.max() >= 200      # the top of the range is used
+    # filter with a random bank of this K (shared-memory bank at 256, tile kernel above)
+    geom = O.Geometry(2, -1)
+    rng = np.random.default_rng(3)
+    bank = rng.standard_normal((Kt, 3, geom.D())) * 0.05
+    bank += (1.0 - bank.sum(axis=2, keepdims=True)) / geom.D()
+    out = mdn.filter_level(_tt(z, "f32")[None], None, _tt(bank, "f32"), _geom(mdn, geom), _gbp(mdn, bp))
+    refo = O.filter_level(z, None, ref, bank, geom)
+    assert max_abs(_np(out[0]), refo, ~mism) <= TOL["f32"]
+    # training: counts exact, Gram within the FP32 bar
+    gram, counts = O.gram_accumulate(z, None, u, ref, Kt, geom)
+    g, c, _ = mdn.train_level_filters(_tt(z, "f32")[None], None, _tt(u, "f32")[None], _geom(mdn, geom),
+                                      _gbp(mdn, bp), 1, solve=False)
+    torch.cuda.synchronize()
+    assert np.array_equal(c.cpu().numpy(), counts)
+    g = _np(g)
+    assert np.linalg.norm(g - gram) / np.linalg.norm(gram) < GRAM_TOL[1]
