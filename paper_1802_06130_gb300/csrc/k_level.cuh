@@ -122,9 +122,22 @@ __device__ __forceinline__ int bucket_of(float a, float b, float c, const SelPar
 
 // One output channel of the level filter for the pixel whose fine-patch
 // centre is zc (shared tile, working space) and coarse-patch centre uc.
+// Two consecutive taps of a bank row read from global memory as one 4-byte
+// (FP16) or 8-byte (FP32) load; the caller guarantees the alignment.
+__device__ __forceinline__ void ld_pair(const __half* p, float& a, float& b) {
+    const float2 f = __half22float2(__ldg(reinterpret_cast<const __half2*>(p)));
+    a = f.x; b = f.y;
+}
+__device__ __forceinline__ void ld_pair(const float* p, float& a, float& b) {
+    const float2 f = __ldg(reinterpret_cast<const float2*>(p));
+    a = f.x; b = f.y;
+}
+
+// pair_ok: the bank is read through the cache (SMEM = false) and every row
+// start is aligned for ld_pair (even D and an aligned base pointer).
 template <int RF, int RC, bool CROSS, typename TB, bool SMEM>
 __device__ __forceinline__ float apply_filter(const TB* __restrict__ hb, const float* __restrict__ zc,
-                                              const float* __restrict__ uc, int oc_const) {
+                                              const float* __restrict__ uc, int oc_const, bool pair_ok) {
     using G = Geo<RF, RC, CROSS>;
     constexpr int V = BankVec<TB>::V;
     constexpr int UW = Coarse<RC>::UW, UH = Coarse<RC>::UH;
@@ -147,6 +160,10 @@ __device__ __forceinline__ float apply_filter(const TB* __restrict__ hb, const f
                         h[2 * e] = f.x; h[2 * e + 1] = f.y;
                     }
                 }
+            } else if (G::D % 2 == 0 && pair_ok) {
+#pragma unroll
+                for (int e = 0; e < V; e += 2)
+                    if (t + e < G::D) ld_pair(hb + t + e, h[e], h[e + 1]);
             } else {
 #pragma unroll
                 for (int e = 0; e < V; ++e)
@@ -176,7 +193,7 @@ __global__ void __launch_bounds__(NT) k_level(const TS* __restrict__ z, const TS
                                               TS* __restrict__ out, void* __restrict__ bmap,
                                               const TB* __restrict__ bank, int H, int W, int Hc, int Wc,
                                               int nimg, int K, int color, SelParams sp, float w0, float w1,
-                                              float w2) {
+                                              float w2, bool pair_ok) {
     using G = Geo<RF, RC, CROSS>;
     using BL = BankLayout<TB, G::D>;
     constexpr int UW = Coarse<RC>::UW, UH = Coarse<RC>::UH;
@@ -307,7 +324,7 @@ __global__ void __launch_bounds__(NT) k_level(const TS* __restrict__ z, const TS
                 for (int oc = 0; oc < 3; ++oc) {
                     const TB* hb = SMEM ? bank_s + ((int64_t)k * 3 + oc) * BL::DP
                                         : bank + ((int64_t)k * 3 + oc) * G::D;
-                    o[oc] = apply_filter<RF, RC, CROSS, TB, SMEM>(hb, zc, uc, oc);
+                    o[oc] = apply_filter<RF, RC, CROSS, TB, SMEM>(hb, zc, uc, oc, pair_ok);
                 }
                 float R, Gc, B;
                 work_to_rgb(o[0], o[1], o[2], color, R, Gc, B);
@@ -350,7 +367,8 @@ int run(const LevelArgs& a, cudaStream_t s) {
     gauss5_weights(w);
     kern<<<(unsigned)grid, NT, bytes, s>>>((const TS*)a.z, (const TS*)a.coarse, (TS*)a.out, a.buckets,
                                            (const TB*)a.bank, (int)a.h, (int)a.w, (int)a.hc, (int)a.wc,
-                                           (int)a.n, a.K, a.geom.color, a.sel, w[0], w[1], w[2]);
+                                           (int)a.n, a.K, a.geom.color, a.sel, w[0], w[1], w[2],
+                                           G::D % 2 == 0 && (uintptr_t)a.bank % (2 * sizeof(TB)) == 0);
     return check_launch("k_level");
 }
 
