@@ -236,7 +236,8 @@ def buckets(feat, bp: BucketParams, band_eps: float = 1e-5):
 
 
 def select(z, bp: BucketParams, mirror32: bool = False, band_eps: float = 1e-5):
-    """s(i) for one level: (bucket map u8 [H][W], band mask, features)."""
+    """s(i) for one level: (bucket map [H][W], u8 up to 256 buckets else u16,
+    band mask, features)."""
     f = features(structure_tensor(z, mirror32), bp.coh_eps, mirror32)
     b, band = buckets(f, bp, band_eps)
     return b, band, f

@@ -45,3 +45,19 @@ def test_gram_round_trip_and_kind_check(tmp_path):
     bad.write_bytes(b'{"format": "other"}\n')
     with pytest.raises(ValueError):
         mdn.load_gram_state(bad, device="cpu")
+
+
+def test_paper_grid_bank_round_trip(tmp_path):
+    """A 4096-bucket bank set keeps its 15 + 15 thresholds per level."""
+    geom = mdn.Geometry(3, 2)
+    bps = [mdn.paper_grid_bparams(0), mdn.paper_grid_bparams(1)]
+    banks = [torch.zeros((4096, 3, 74), dtype=torch.float32) + l for l in range(2)]
+    p = tmp_path / "grid16.bank"
+    mdn.save_banks(p, banks, geom, bps)
+    b2, g2, bp2, _ = mdn.load_banks(p, device="cpu")
+    assert all(torch.equal(a, b) for a, b in zip(banks, b2))
+    assert (g2.r_fine, g2.r_coarse) == (3, 2)
+    for a, b in zip(bps, bp2):
+        assert b.K == 4096 and (b.n_strength, b.n_coherence) == (16, 16)
+        assert list(a.strength_thr) == list(b.strength_thr)
+        assert list(a.coherence_thr) == list(b.coherence_thr)
