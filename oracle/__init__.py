@@ -87,6 +87,8 @@ def lib():
                                           C.c_int, C.c_int, C.c_int, C.c_int, dp, i64p]
         L.orc_cholesky_solve.restype = C.c_int
         L.orc_cholesky_solve.argtypes = [dp, C.c_int, dp, C.c_int]
+        L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_max_threads.restype = C.c_int
         L.orc_solve_bank.restype = C.c_int
         L.orc_solve_bank.argtypes = [dp, i64p, C.c_int, C.c_int, C.c_int, C.c_double, dp]
         _lib = L
@@ -183,6 +185,15 @@ def paper_grid_bparams(level: int) -> BucketParams:
 def bucket_dtype(K: int):
     """Element type of a bucket map: u8 up to 256 buckets, else u16."""
     return np.uint8 if K <= 256 else np.uint16
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops (OpenMP)."""
+    lib().orc_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(lib().orc_max_threads())
 
 
 # ---------------------------------------------------------------- primitives
