@@ -48,3 +48,16 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.max_over_ranks(3.5, 1) == 3.5
     assert bench.whole_job_rate(2_000_000, 5, 1, 10.0) == pytest.approx(1000.0)
+
+
+def test_cpu_baseline_block_reports_threads_and_single_thread_leg():
+    """The bench's cpu_baseline: the oracle on all its threads (cores = the
+    OpenMP thread count it used) plus a one-thread leg; thread count restored."""
+    import bench
+    import oracle as O
+    before = O.max_threads()
+    blk = bench.cpu_baseline_block(1, 0)
+    assert blk["kind"] == "oracle" and blk["unit"] == "Mpix/s" and blk["value"] > 0
+    assert blk["cores"] == before and blk["single_thread"]["cores"] == 1
+    assert blk["single_thread"]["value"] > 0
+    assert O.max_threads() == before
