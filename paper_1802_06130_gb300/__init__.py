@@ -19,7 +19,7 @@ __all__ = ["build", "lib", "Geometry", "BucketParams", "default_bparams", "MdnEr
            "gram_state_shape", "train_status", "train_cascade", "Server", "F32", "F16", "YCBCR601", "RGB", "GRAM_FP32", "GRAM_TF32",
            "GRAM_BF16", "GRAM_SPLIT_BF16", "augment_dihedral", "dihedral", "estimate_noise", "nearest_level",
            "save_banks", "load_banks", "save_gram_state", "load_gram_state", "paper_grid_bparams",
-           "bucket_map_dtype", "MAX_K"]
+           "bucket_map_dtype", "MAX_K", "levels_for_sigma", "pyramid_noise_factor"]
 
 F32, F16 = 0, 1
 YCBCR601, RGB = 0, 1
@@ -662,6 +662,35 @@ def nearest_level(sigma: float, levels) -> int:
     """Index of the trained noise level closest to an estimate (host helper
     for choosing a bank set)."""
     return min(range(len(levels)), key=lambda i: abs(levels[i] - sigma))
+
+
+def pyramid_noise_factor(level: int) -> float:
+    """Standard deviation of white noise at pyramid level l relative to the
+    input (away from the clamped borders).  Level l is the input filtered by
+    the composed kernel c_l (c_1 = b = [1 4 6 4 1] / 16, c_{l+1}[m] =
+    sum_u b[u] c_l[m - 2^l u]) and subsampled; the 2-D kernel is separable,
+    so the factor is sum_m c_l[m]^2 (0.273, 0.123, 0.060, 0.030, ...)."""
+    b = [1 / 16, 4 / 16, 6 / 16, 4 / 16, 1 / 16]
+    c = [1.0]
+    for l in range(level):
+        step = 1 << l
+        nxt = [0.0] * (len(c) + 4 * step)
+        for u, bu in enumerate(b):
+            for m, cm in enumerate(c):
+                nxt[m + u * step] += bu * cm
+        c = nxt
+    return sum(v * v for v in c)
+
+
+def levels_for_sigma(sigma: float, coarsest: float = 2.0 / 255.0, max_levels: int = 8) -> int:
+    """Pyramid depth for input noise sigma: the fewest levels whose coarsest
+    level's noise (pyramid_noise_factor) is below `coarsest` (Section 5 sets
+    the depth so that the coarsest level's sigma is below 2 on the 0-255
+    scale), at least 2 and at most max_levels."""
+    L = 2
+    while L < max_levels and sigma * pyramid_noise_factor(L - 1) >= coarsest:
+        L += 1
+    return L
 
 
 def augment_dihedral(gram, counts, geom: Geometry, bp: BucketParams, stream=None):

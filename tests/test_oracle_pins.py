@@ -533,3 +533,24 @@ def test_noise_estimate_on_pure_noise():
     ramp = 0.002 * xx + 0.003 * yy
     assert abs(O.estimate_noise(noise + ramp[None]) - base) < 1e-9
     assert O.estimate_noise(np.ones((3, 9, 7))) == 0.0
+
+
+def test_pyramid_noise_factor_and_level_count():
+    """The noise of the oracle's pyramid of pure AWGN (measured away from the
+    clamped border) falls by the composed-kernel factors the depth rule uses
+    (70/256 at level 1, then about 0.45, 0.49, 0.5 per level: the noise is no
+    longer white after the first level), and the rule of Section 5 (coarsest
+    sigma below 2/255) gives 2 levels at sigma 5, 3 at 15, 4 at 25 and 5 at 50
+    (on the 0-255 scale)."""
+    import paper_1802_06130_gb300 as mdn
+    assert mdn.pyramid_noise_factor(0) == 1.0
+    assert abs(mdn.pyramid_noise_factor(1) - 70 / 256) < 1e-15
+    n = np.random.default_rng(5).standard_normal((3, 1024, 1024)) * 0.1
+    zs = O.pyramid(n, 4)
+    s0 = n[:, 16:-16, 16:-16].std()
+    for l in (1, 2, 3):
+        e = 16 >> l
+        ratio = zs[l][:, e:-e, e:-e].std() / s0
+        assert abs(ratio / mdn.pyramid_noise_factor(l) - 1) < 0.02, (l, ratio)
+    assert [mdn.levels_for_sigma(s / 255) for s in (5, 15, 25, 50)] == [2, 3, 4, 5]
+    assert mdn.levels_for_sigma(1 / 255) == 2 and mdn.levels_for_sigma(1e6, max_levels=5) == 5
