@@ -379,15 +379,22 @@ def cholesky_solve(A, B):
 
 
 def train_cascade(noisy_list, clean_list, geom: Geometry, levels: int, bparams=None,
-                  lam: float = 1e-3, mirror32: bool = False, storage: str = "f64"):
+                  lam: float = 1e-3, mirror32: bool = False, storage: str = "f64", level_targets=None):
     """Section 4 training: level L-2 first (its coarse input is z^{L-1}), then
-    every finer level using the trained coarser levels' outputs."""
+    every finer level using the trained coarser levels' outputs.
+
+    The target of level l is level l of the clean image's pyramid, unless
+    level_targets (one list [u^0 .. u^{L-1}] per pair) gives it directly: a
+    hook for tests that plant a different target at every level."""
     nb = max(levels - 1, 1)
     L = 1 if geom.r_coarse < 0 else levels
     if bparams is None:
         bparams = [default_bparams(l) for l in range(nb)]
     zp = [pyramid(z, L, storage, mirror32) for z in noisy_list]
-    up = [pyramid(u, L, storage, mirror32) for u in clean_list]
+    if level_targets is not None:
+        up = [[_d(t) for t in ts] for ts in level_targets]
+    else:
+        up = [pyramid(u, L, storage, mirror32) for u in clean_list]
     cur = [p[L - 1] for p in zp]           # u-hat at level l+1, per pair
     banks = [None] * nb
     stats = [None] * nb

@@ -359,6 +359,107 @@ def test_gram_path_equals_lstsq():
             np.testing.assert_allclose(bank[k, c], h, rtol=1e-8, atol=1e-10)
 
 
+def _ridge_lstsq(X, Y, lam):
+    """LAPACK least squares of the stacked ridge system [X; sqrt(n lam) I] h =
+    [Y; 0] (n = rows of X), the normalised ridge of reading 12."""
+    n, D = X.shape
+    A = np.vstack([X, math.sqrt(n * lam) * np.eye(D)])
+    rhs = np.concatenate([Y, np.zeros((D,) + Y.shape[1:])])
+    return np.linalg.lstsq(A, rhs, rcond=None)[0]
+
+
+@pytest.mark.parametrize("cross", [0, 1])
+def test_empty_buckets_take_pooled_ridge_solution(cross):
+    """Reading 13 (the paper is silent on empty buckets): a bucket with no
+    pixels takes the pooled filter, the ridge solution over every pixel of the
+    level, (sum_k G_k / N + lam I) h = sum_k b_k / N with N = sum_k n_k.  It
+    equals LAPACK lstsq of all pixels' stacked patches, whichever buckets they
+    fall in; buckets 0..2 of 6 are used, 3..5 are empty."""
+    rng = np.random.default_rng(19)
+    geom = O.Geometry(2, -1, cross=cross)
+    z, u = synth.noisy_pair(30, 34, 23)
+    bk = rng.integers(0, 3, (30, 34)).astype(np.uint8)
+    lam = 2e-3
+    gram, counts = O.gram_accumulate(z, None, u, bk, 6, geom)
+    assert list(counts[3:]) == [0, 0, 0] and counts.sum() == 30 * 34
+    bank = O.solve_bank(gram, counts, geom, lam)
+    zw, _ = _ycc(z)
+    uw, _ = _ycc(u)
+    P = _patches_numpy(zw, 2).reshape(30 * 34, 3, 25)
+    Y = uw.reshape(3, -1).T
+    if cross:
+        pooled = _ridge_lstsq(P.reshape(-1, 75), Y, lam).T        # [3][75]
+    else:
+        pooled = np.stack([_ridge_lstsq(P[:, c, :], Y[:, c], lam) for c in range(3)])
+    for k in (3, 4, 5):
+        np.testing.assert_allclose(bank[k], pooled, rtol=1e-8, atol=1e-10)
+    # a used bucket keeps its own solution, not the pooled one
+    assert np.abs(bank[0] - pooled).max() > 1e-3
+
+
+def _filter_numpy(zw, uw, bk, bank, rf, rc):
+    """Brute force of the multiscale equation in working space ([C][H][W]
+    arrays, per-channel regressors: coarse patch at floor(i/2), then fine)."""
+    H, W = zw.shape[1:]
+    Pz = _patches_numpy(zw, rf)
+    Pu = _patches_numpy(uw, rc)
+    pc = (2 * rc + 1) ** 2
+    out = np.zeros_like(zw)
+    for y in range(H):
+        for x in range(W):
+            h = bank[bk[y, x]]
+            for c in range(3):
+                out[c, y, x] = h[c, :pc] @ Pu[y // 2, x // 2, c] + h[c, pc:] @ Pz[y, x, c]
+    return out
+
+
+def test_cascade_feeds_trained_coarser_output():
+    """Section 4's training cascade: level l regresses on the output u-hat^{l+1}
+    of the coarser level trained just before it, not on z^{l+1} or on the
+    clean target of level l+1.  Planted construction, lambda = 0, 3 levels:
+    level 1's target t1 is an arbitrary image, so its least-squares fit B1
+    (computed here with LAPACK) leaves a residual and u-hat^1 = B1 applied to
+    (z^2, z^1) differs from t1 and from z^1; level 0's target is a planted
+    bank P0 applied to (u-hat^1, z^0), computed here by brute force.  The
+    cascade must give B1 and recover P0; feeding z^1 or t1 to level 0 leaves
+    P0 outside the span of the regressors."""
+    rng = np.random.default_rng(77)
+    geom = O.Geometry(1, 1)                                  # D = 9 + 9 per channel
+    bps = [O.BucketParams(n_angle=2, strength_thr=(), coherence_thr=()) for _ in range(2)]
+    z, _ = synth.noisy_pair(64, 60, 91)
+    zs = O.pyramid(z, 3)
+    t1 = rng.uniform(0, 1, zs[1].shape)
+    b1, _, _ = O.select(zs[1], bps[1])
+    b0, _, _ = O.select(zs[0], bps[0])
+    assert set(np.unique(b1)) == {0, 1} and set(np.unique(b0)) == {0, 1}
+    # level 1 by LAPACK: per bucket and working channel, [coarse z^2 ; fine z^1] -> t1
+    zw1, Minv = _ycc(zs[1])
+    zw2, _ = _ycc(zs[2])
+    tw1, _ = _ycc(t1)
+    Pz, Pu = _patches_numpy(zw1, 1), _patches_numpy(zw2, 1)
+    H1, W1 = zs[1].shape[1:]
+    yy, xx = np.mgrid[0:H1, 0:W1]
+    Xall = np.concatenate([Pu[yy // 2, xx // 2], Pz], axis=3)   # [H1][W1][3][18]
+    B1 = np.zeros((2, 3, 18))
+    for k in range(2):
+        m = b1 == k
+        for c in range(3):
+            B1[k, c] = np.linalg.lstsq(Xall[m][:, c, :], tw1[c][m], rcond=None)[0]
+    uhat1_w = np.einsum("hwcd,hwcd->chw", B1[b1], Xall)
+    uhat1 = np.einsum("ij,jhw->ihw", Minv, uhat1_w)
+    assert np.abs(uhat1 - t1).max() > 0.1 and np.abs(uhat1 - zs[1]).max() > 0.1
+    # level 0: planted bank on (u-hat^1, z^0)
+    P0 = rng.standard_normal((2, 3, 18)) * 0.1
+    zw0, _ = _ycc(zs[0])
+    t0 = np.einsum("ij,jhw->ihw", Minv, _filter_numpy(zw0, uhat1_w, b0, P0, 1, 1))
+    banks, counts = O.train_cascade([z], None, geom, 3, bparams=bps, lam=0.0,
+                                    level_targets=[[t0, t1, zs[2]]])
+    np.testing.assert_allclose(banks[1], B1, rtol=1e-8, atol=1e-10)
+    err = np.linalg.norm(banks[0] - P0) / np.linalg.norm(P0)
+    assert err < 1e-8, err
+    assert list(counts[0]) == [int((b0 == k).sum()) for k in range(2)]
+
+
 @pytest.mark.parametrize("geom", [O.Geometry(2, -1), O.Geometry(3, 3), O.Geometry(3, -1, cross=1)])
 def test_planted_bank_recovered(geom):
     """Noise-free targets made by a planted bank (selector computed on z) are
