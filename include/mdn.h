@@ -7,7 +7,10 @@
  * ---------------------------------------
  * - Images are planar RGB, row-major: [n][3][h][w], values nominally in
  *   [0, 1], stored as FP32 (MDN_F32) or FP16 (MDN_F16).  Level l of a pyramid
- *   has size ceil(h / 2^l) x ceil(w / 2^l).
+ *   has size ceil(h / 2^l) x ceil(w / 2^l).  Sizes are limited to h, w <=
+ *   2^20 and n * 3 * h * w < 2^31 elements (checked without overflow): larger
+ *   images are rejected with MDN_ESHAPE, and the *_bytes size queries return
+ *   SIZE_MAX for them.
  * - Every data pointer is a DEVICE pointer unless stated otherwise; the caller
  *   owns every buffer (images, banks, maps, Gram state, workspace).  The
  *   library never allocates or frees on these paths; the only state it keeps
@@ -186,8 +189,10 @@ int mdn_denoise_multiscale(const void* noisy, int32_t dtype, int64_t n, int64_t 
  * call is made.  Images whose mdn_denoise_workspace_bytes() exceeds the array
  * are rejected with MDN_EWORKSPACE (e.g. one 12 MP FP16 frame at 3 levels
  * fits, eight do not).  The first call on a device, with that device
- * current, looks up the array's address and caches it: make that first call
- * before any stream capture.  All calls on a device share the array and it
+ * current, looks up the array's address and caches it per device ordinal:
+ * make that first call before any stream capture, and do not call this entry
+ * point again on a device after cudaDeviceReset (the cached address belongs
+ * to the context that the reset ended).  All calls on a device share the array and it
  * keeps the previous call's contents (nothing needs clearing: each call
  * writes every scratch element before reading it), so calls whose GPU work
  * overlaps (different streams or host threads) race: serialise them. */
@@ -225,6 +230,22 @@ int mdn_train_level_filters(const void* noisy_lvl, const void* coarse_out, const
                             int32_t gram_precision, int32_t accumulate, double* gram,
                             int64_t* counts, double lambda, float* bank_out, void* ws,
                             size_t ws_bytes, void* stream);
+
+/* Bound, in nanoseconds, of every wait inside the tensor-core Gram kernel
+ * (mbarrier hand-offs between its warp roles) for launches made after the
+ * call, on every device; 0 restores the default of 2 s.  A wait that runs
+ * out makes the kernel stop its roles, wait (with the default bound) for
+ * its issued tensor-core operations, free its tensor memory and return;
+ * mdn_train_status then reports 1.  Always returns MDN_OK. */
+int mdn_set_gram_wait_limit(uint64_t ns);
+
+/* Failure-detection test without a GPU fault: when enable != 0, the next
+ * tensor-core Gram launch (any precision but MDN_GRAM_FP32) starts with a
+ * wait on a barrier phase that nothing completes, so the wait runs out after
+ * the wait limit and the launch takes the abort path above (no tensor-core
+ * operation issued, partial sums not written).  One-shot: cleared by that
+ * launch.  Always returns MDN_OK. */
+int mdn_gram_expire_next_wait(int32_t enable);
 
 /* Reads and clears the device-side error flag of the tensor-core Gram
  * kernels (synchronous, host pointer): *flag = 1 if a bounded wait inside a
@@ -274,6 +295,32 @@ int mdn_dihedral_images(const void* in, int32_t dtype, int64_t n, int64_t h, int
 size_t mdn_noise_workspace_bytes(int64_t n);
 int mdn_estimate_noise(const void* img, int32_t dtype, int64_t n, int64_t h, int64_t w, float* sigma_out,
                        void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* Pyramid depth (Section 5: enough levels that the coarsest level's   */
+/* noise is below 2 on the 0-255 scale)                                */
+/* ------------------------------------------------------------------ */
+
+/* Standard deviation of white noise at pyramid level `level` (0..7) relative
+ * to the input, for this library's pyramid (mdn_build_pyramid: the binomial
+ * [1 4 6 4 1]/16 kernel; the paper's bicubic downsampling would give other
+ * factors), away from the clamped borders: level l is the input filtered by
+ * the composed kernel c_l (c_0 = delta, c_{l+1}[m] = sum_u b[u] c_l[m - 2^l u])
+ * and subsampled, and the separable 2-D kernel gives the factor
+ * sum_m c_l[m]^2: 1, 0.273, 0.123, 0.060, 0.030, ...  (after level 1 the
+ * noise is correlated and falls by ~0.45-0.5 per level, not 0.5 squared).
+ * Returns -1 for a level outside 0..7.  Host-only arithmetic. */
+double mdn_pyramid_noise_factor(int32_t level);
+
+/* Section 5's depth rule: the fewest levels L >= 1 whose coarsest level's
+ * noise, sigma * mdn_pyramid_noise_factor(L - 1), is below coarsest_sigma
+ * (2/255 in the paper, on [0, 1] images), then clamped to [min_levels,
+ * max_levels] (max_levels <= 8).  The rule gives L = 1 (single-scale) when
+ * sigma itself is below coarsest_sigma; a caller whose bank sets are all
+ * multiscale passes min_levels = 2.  Returns -1 on bad arguments (sigma < 0,
+ * coarsest_sigma <= 0, min_levels < 1, max_levels > 8, min > max).
+ * Host-only arithmetic. */
+int32_t mdn_levels_for_sigma(double sigma, double coarsest_sigma, int32_t min_levels, int32_t max_levels);
 
 /* Ridge solve per bucket and group in FP64 on the GPU:
  * h = (G_xx / n_k + lambda I)^{-1} (G_xy / n_k) by Cholesky; buckets with

@@ -19,7 +19,8 @@ __all__ = ["build", "lib", "Geometry", "BucketParams", "default_bparams", "MdnEr
            "gram_state_shape", "train_status", "train_cascade", "Server", "F32", "F16", "YCBCR601", "RGB", "GRAM_FP32", "GRAM_TF32",
            "GRAM_BF16", "GRAM_SPLIT_BF16", "augment_dihedral", "dihedral", "estimate_noise", "nearest_level",
            "save_banks", "load_banks", "save_gram_state", "load_gram_state", "paper_grid_bparams",
-           "bucket_map_dtype", "MAX_K", "levels_for_sigma", "pyramid_noise_factor"]
+           "bucket_map_dtype", "MAX_K", "levels_for_sigma", "pyramid_noise_factor", "set_gram_wait_limit",
+           "gram_expire_next_wait"]
 
 F32, F16 = 0, 1
 YCBCR601, RGB = 0, 1
@@ -158,6 +159,10 @@ def lib():
                                                   C.c_double, vp, vp, sz, vp]),
             "mdn_solve_workspace_bytes": (sz, [G, i32]),
             "mdn_train_status": (C.c_int, [C.POINTER(C.c_int32)]),
+            "mdn_set_gram_wait_limit": (C.c_int, [C.c_uint64]),
+            "mdn_gram_expire_next_wait": (C.c_int, [i32]),
+            "mdn_pyramid_noise_factor": (C.c_double, [i32]),
+            "mdn_levels_for_sigma": (i32, [C.c_double, C.c_double, i32, i32]),
             "mdn_solve_bank": (C.c_int, [vp, vp, G, i32, C.c_double, vp, vp, vp, sz, vp]),
             "mdn_augment_dihedral": (C.c_int, [vp, vp, G, B, vp, vp, vp]),
             "mdn_noise_workspace_bytes": (sz, [i64]),
@@ -360,6 +365,19 @@ def train_status() -> int:
     v = C.c_int32(0)
     _check(lib().mdn_train_status(C.byref(v)))
     return v.value
+
+
+def set_gram_wait_limit(ns: int = 0):
+    """Bound of every wait inside the tensor-core Gram kernel for later
+    launches, in ns (0 = the default 2 s) (mdn_set_gram_wait_limit)."""
+    _check(lib().mdn_set_gram_wait_limit(int(ns)))
+
+
+def gram_expire_next_wait(enable: bool = True):
+    """Makes the next tensor-core Gram launch wait on a barrier phase that
+    nothing completes, so that its bounded wait runs out (failure-detection
+    test; mdn_gram_expire_next_wait)."""
+    _check(lib().mdn_gram_expire_next_wait(int(enable)))
 
 
 class Server:
@@ -665,31 +683,22 @@ def nearest_level(sigma: float, levels) -> int:
 
 
 def pyramid_noise_factor(level: int) -> float:
-    """Standard deviation of white noise at pyramid level l relative to the
-    input (away from the clamped borders).  Level l is the input filtered by
-    the composed kernel c_l (c_1 = b = [1 4 6 4 1] / 16, c_{l+1}[m] =
-    sum_u b[u] c_l[m - 2^l u]) and subsampled; the 2-D kernel is separable,
-    so the factor is sum_m c_l[m]^2 (0.273, 0.123, 0.060, 0.030, ...)."""
-    b = [1 / 16, 4 / 16, 6 / 16, 4 / 16, 1 / 16]
-    c = [1.0]
-    for l in range(level):
-        step = 1 << l
-        nxt = [0.0] * (len(c) + 4 * step)
-        for u, bu in enumerate(b):
-            for m, cm in enumerate(c):
-                nxt[m + u * step] += bu * cm
-        c = nxt
-    return sum(v * v for v in c)
+    """White-noise standard deviation at pyramid level l relative to the input,
+    for this library's binomial pyramid (mdn_pyramid_noise_factor)."""
+    v = lib().mdn_pyramid_noise_factor(level)
+    if v < 0:
+        raise ValueError("level must be 0..7")
+    return v
 
 
-def levels_for_sigma(sigma: float, coarsest: float = 2.0 / 255.0, max_levels: int = 8) -> int:
-    """Pyramid depth for input noise sigma: the fewest levels whose coarsest
-    level's noise (pyramid_noise_factor) is below `coarsest` (Section 5 sets
-    the depth so that the coarsest level's sigma is below 2 on the 0-255
-    scale), at least 2 and at most max_levels."""
-    L = 2
-    while L < max_levels and sigma * pyramid_noise_factor(L - 1) >= coarsest:
-        L += 1
+def levels_for_sigma(sigma: float, coarsest: float = 2.0 / 255.0, min_levels: int = 1,
+                     max_levels: int = 8) -> int:
+    """Section 5's depth rule (mdn_levels_for_sigma): the fewest levels whose
+    coarsest level's noise is below `coarsest` (2/255), clamped to
+    [min_levels, max_levels]; pass min_levels = 2 for multiscale bank sets."""
+    L = lib().mdn_levels_for_sigma(sigma, coarsest, min_levels, max_levels)
+    if L < 0:
+        raise ValueError("bad arguments to levels_for_sigma")
     return L
 
 

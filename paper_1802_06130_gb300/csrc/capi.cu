@@ -83,12 +83,20 @@ static int check_geom(const mdn_geometry* g) {
     return MDN_OK;
 }
 
-static int check_img(const void* p, int dtype, int64_t n, int64_t h, int64_t w, const char* what) {
-    if (!p && n * h * w > 0) return fail(MDN_EINVAL, std::string(what) + ": null pointer");
+bool dims_ok(int64_t n, int64_t h, int64_t w) {
+    // each factor is bounded before any product is formed: h, w <= 2^20 keeps
+    // 3*h*w below 2^63, and n is then bounded by division
+    if (n < 0 || h < 0 || w < 0 || h > (int64_t(1) << 20) || w > (int64_t(1) << 20)) return false;
+    const int64_t per = 3 * h * w;
+    return per == 0 || n <= ((int64_t(1) << 31) - 1) / per;
+}
+
+int check_img(const void* p, int dtype, int64_t n, int64_t h, int64_t w, const char* what) {
     if (dtype != MDN_F32 && dtype != MDN_F16) return fail(MDN_EINVAL, std::string(what) + ": bad dtype");
     if (n < 0 || h < 0 || w < 0) return fail(MDN_ESHAPE, std::string(what) + ": negative size");
-    if (h > (1 << 20) || w > (1 << 20) || n * 3 * h * w >= (int64_t(1) << 31))
-        return fail(MDN_ESHAPE, std::string(what) + ": image too large (n*3*h*w must be < 2^31)");
+    if (!dims_ok(n, h, w))
+        return fail(MDN_ESHAPE, std::string(what) + ": image too large (h, w <= 2^20 and n*3*h*w < 2^31)");
+    if (!p && n * h * w > 0) return fail(MDN_EINVAL, std::string(what) + ": null pointer");
     return MDN_OK;
 }
 
@@ -127,6 +135,7 @@ int mdn_regressor_len(const mdn_geometry* geom) {
 int mdn_bucket_elem_bytes(int32_t K) { return K < 1 || K > MDN_MAX_K ? 0 : bucket_bytes(K); }
 
 size_t mdn_pyramid_bytes(int64_t n, int64_t h, int64_t w, int32_t levels, int32_t dtype) {
+    if (!dims_ok(n, h, w) || levels > 8) return SIZE_MAX;   // no size is large enough: calls will be rejected
     size_t tot = 0;
     for (int l = 1; l < levels; ++l) {
         h = (h + 1) / 2;
@@ -195,6 +204,7 @@ int mdn_filter_level(const void* z, const void* coarse, int32_t dtype, int64_t n
 
 size_t mdn_denoise_workspace_bytes(int64_t n, int64_t h, int64_t w, int32_t levels, int32_t dtype) {
     // pyramid levels 1..L-1 plus outputs u^1..u^{L-2}
+    if (!dims_ok(n, h, w) || levels > 8) return SIZE_MAX;
     size_t tot = mdn_pyramid_bytes(n, h, w, levels, dtype);
     int64_t hh = h, ww = w;
     for (int l = 1; l <= levels - 2; ++l) {
@@ -362,6 +372,45 @@ int mdn_solve_bank(const double* gram, const int64_t* counts, const mdn_geometry
     int G = geom->cross_channel ? 1 : 3, T = geom->cross_channel ? 3 : 1;
     if (ws_bytes < solve_ws_bytes(K, G, D, T) || !ws) return fail(MDN_EWORKSPACE, "solve_bank: workspace too small");
     return launch_solve(gram, counts, K, G, D, T, lambda, bank_out, status_out, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int mdn_set_gram_wait_limit(uint64_t ns) {
+    gram_tc_set_wait((unsigned long long)ns);
+    return MDN_OK;
+}
+
+int mdn_gram_expire_next_wait(int32_t enable) {
+    gram_tc_expire_next(enable);
+    return MDN_OK;
+}
+
+double mdn_pyramid_noise_factor(int32_t level) {
+    if (level < 0 || level > 7) return -1.0;
+    // composed kernel of `level` binomial downsamplings, in input samples:
+    // c_0 = delta, c_{l+1}[m] = sum_u b[u] c_l[m - 2^l u], b = [1 4 6 4 1] / 16
+    static const double b[5] = {1.0 / 16, 4.0 / 16, 6.0 / 16, 4.0 / 16, 1.0 / 16};
+    double c[1024] = {1.0}, nxt[1024];
+    int len = 1;
+    for (int l = 0; l < level; ++l) {
+        const int step = 1 << l, nlen = len + 4 * step;
+        for (int m = 0; m < nlen; ++m) nxt[m] = 0.0;
+        for (int u = 0; u < 5; ++u)
+            for (int m = 0; m < len; ++m) nxt[m + u * step] += b[u] * c[m];
+        for (int m = 0; m < nlen; ++m) c[m] = nxt[m];
+        len = nlen;
+    }
+    // separable 2-D kernel: the variance factor is (sum_m c[m]^2)^2, its root sum_m c[m]^2
+    double ss = 0.0;
+    for (int m = 0; m < len; ++m) ss += c[m] * c[m];
+    return ss;
+}
+
+int32_t mdn_levels_for_sigma(double sigma, double coarsest_sigma, int32_t min_levels, int32_t max_levels) {
+    if (!(sigma >= 0.0) || !(coarsest_sigma > 0.0) || min_levels < 1 || max_levels > 8 || min_levels > max_levels)
+        return -1;
+    int32_t L = 1;
+    while (L < max_levels && sigma * mdn_pyramid_noise_factor(L - 1) >= coarsest_sigma) ++L;
+    return L < min_levels ? min_levels : L;
 }
 
 int mdn_train_status(int32_t* flag) {

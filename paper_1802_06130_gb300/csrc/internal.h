@@ -83,6 +83,9 @@ int launch_solve(const double* gram, const int64_t* counts, int K, int G, int D,
                  cudaStream_t s);
 
 int num_sms();
+// image sizes: h, w <= 2^20 and n * 3 * h * w < 2^31, checked without overflow
+bool dims_ok(int64_t n, int64_t h, int64_t w);
+int check_img(const void* p, int dtype, int64_t n, int64_t h, int64_t w, const char* what);
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // bytes per pixel of a bucket map of K buckets
 inline int bucket_bytes(int K) { return K <= 256 ? 1 : 2; }

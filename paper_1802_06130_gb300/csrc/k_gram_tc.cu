@@ -58,6 +58,8 @@
 // Every wait is bounded by a time limit: on expiry the CTA raises a shared
 // abort flag that ends every role's loop, waits (bounded) for its issued MMAs,
 // frees its TMEM, and reports the error through g_gram_error.
+#include <atomic>
+
 #include <cuda_bf16.h>
 
 #include "train_common.cuh"
@@ -74,7 +76,7 @@ constexpr int NG = NTHREADS / 32 - GATHER0;   // gather warps
 constexpr int TMEM_COLS = 512;
 constexpr int PGS = 8;                        // 16-byte chunks (pixel groups) per 128-byte K atom
 constexpr int MAX_STAGES = 4;
-constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s per wait
+constexpr unsigned long long WAIT_NS = 2000000000ull;   // default bound of one wait: 2 s
 
 __device__ int g_gram_error;   // set to 1 when a bounded wait expired
 __device__ float g_one = 1.0f;                 // the ones column reads this value
@@ -137,12 +139,12 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Bounded wait for the completion of phase `parity`: gives up after WAIT_NS
+// Bounded wait for the completion of phase `parity`: gives up after limit_ns
 // (and raises the abort flag), or, when honour_abort is set, as soon as
 // another role raised it.  sleep_ns > 0 backs off between polls (for roles
 // whose waits are long and not latency-critical).
-__device__ __noinline__ bool wait_bar(uint32_t mbar, uint32_t parity, volatile int* abortf, bool honour_abort = true,
-                                      unsigned sleep_ns = 0) {
+__device__ __noinline__ bool wait_bar(uint32_t mbar, uint32_t parity, volatile int* abortf,
+                                      unsigned long long limit_ns, bool honour_abort = true, unsigned sleep_ns = 0) {
     unsigned long long t0 = 0;   // the clock is read only once a wait is long
     for (unsigned it = 0; it < (1u << 30); ++it) {
         if (try_wait(mbar, parity)) return true;
@@ -152,7 +154,7 @@ __device__ __noinline__ bool wait_bar(uint32_t mbar, uint32_t parity, volatile i
             if ((it & 255) == 255) {
                 const unsigned long long t = global_ns();
                 if (t0 == 0) t0 = t;
-                else if (t - t0 > WAIT_NS) break;
+                else if (t - t0 > limit_ns) break;
             }
         }
     }
@@ -240,7 +242,8 @@ template <int MODE> __host__ __device__ inline Layout layout(int G, int rows, in
 template <int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_gram_tc(GatherArgs ga, const int4* __restrict__ chunks, const int* __restrict__ gcount, int ngroups, int cap,
-              const int* __restrict__ sorted, float* __restrict__ partial, int rows, int S) {
+              const int* __restrict__ sorted, float* __restrict__ partial, int rows, int S,
+              unsigned long long wait_ns, int expire_test) {
     using C = Cfg<MODE>;
     constexpr int KB = C::KB, BSTR = C::BSTR;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -385,7 +388,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 if (!nx.done()) { const int4 ch = chunks[nx.c]; r1 = ch.y; z_n = ch.z; }
             }
             if (!nx.done()) fetch(r1, z_n, nxt);
-            if (T >= S && !wait_bar(smem_u32(&empty[s]), ph ^ 1u, abortf)) break;
+            if (T >= S && !wait_bar(smem_u32(&empty[s]), ph ^ 1u, abortf, wait_ns)) break;
             int* pb = pix + s * C::SLOT_INTS;
 #pragma unroll
             for (int j = 0; j < PL; ++j) {
@@ -442,7 +445,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (ChunkIter it = cit0; !it.done() && ok; it.next()) {
                 const int4 ch = chunks[it.c];
                 for (int r0 = ch.y; r0 < ch.z; r0 += KB) {
-                    if (!wait_bar(smem_u32(&pixfull[s]), ph, abortf)) { ok = false; break; }
+                    if (!wait_bar(smem_u32(&pixfull[s]), ph, abortf, wait_ns)) { ok = false; break; }
                     const int* pb = pix + s * C::SLOT_INTS;
                     const int nv = pb[4 * BSTR];
                     const uint32_t stage = smem_u32(smem + s * L.stage_bytes);
@@ -482,7 +485,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (ChunkIter it = cit0; !it.done() && ok; it.next()) {
                 const int4 ch = chunks[it.c];
                 for (int r0 = ch.y; r0 < ch.z; r0 += KB) {
-                    if (!wait_bar(smem_u32(&pixfull[s]), ph, abortf)) { ok = false; break; }
+                    if (!wait_bar(smem_u32(&pixfull[s]), ph, abortf, wait_ns)) { ok = false; break; }
                     const int* pb = pix + s * C::SLOT_INTS;
                     const int nv = pb[4 * BSTR];
                     unsigned char* stage = smem + s * L.stage_bytes;
@@ -573,14 +576,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             uint32_t ph = 0;
             bool ok = true;
             int q = 0;
+            // failure-detection test: wait on phase 0 of `fin`, on which nothing
+            // arrives before this thread's own commit below, so the wait runs
+            // out after wait_ns and takes the abort path (no MMA issued yet)
+            if (expire_test && !wait_bar(smem_u32(fin), 0u, abortf, wait_ns)) ok = false;
             for (ChunkIter it = cit0; !it.done() && ok; it.next(), ++q) {
                 const int4 ch = chunks[it.c];
                 if (q > 0) {
-                    if (!wait_bar(smem_u32(acc_empty), (uint32_t)((q - 1) & 1), abortf)) break;
+                    if (!wait_bar(smem_u32(acc_empty), (uint32_t)((q - 1) & 1), abortf, wait_ns)) break;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 }
                 for (int r0 = ch.y; r0 < ch.z; r0 += KB) {
-                    if (!wait_bar(smem_u32(&full[s]), ph, abortf)) { ok = false; break; }
+                    if (!wait_bar(smem_u32(&full[s]), ph, abortf, wait_ns)) { ok = false; break; }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t sbase = smem_u32(smem + s * L.stage_bytes);
                     const bool first = r0 == ch.y;
@@ -612,16 +619,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 if (!ok) break;
                 commit(smem_u32(acc_full));
             }
-            // all issued MMAs complete before TMEM is released
+            // all issued MMAs complete before TMEM is released (always with the
+            // default 2 s bound, whatever the wait limit of the launch)
             commit(smem_u32(fin));
-            wait_bar(smem_u32(fin), 0u, abortf, false);
+            wait_bar(smem_u32(fin), 0u, abortf, WAIT_NS, false);
         }
     } else {
         // ---------------------------------------------------------- read-back (warps 0..3)
         const int row = 32 * warp + lane;   // TMEM lane = accumulator row
         int q = 0;
         for (ChunkIter it = cit0; !it.done(); it.next(), ++q) {
-            if (!wait_bar(smem_u32(acc_full), (uint32_t)(q & 1), abortf, true, 500)) break;
+            if (!wait_bar(smem_u32(acc_full), (uint32_t)(q & 1), abortf, wait_ns, true, 500)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             float* out = partial + (size_t)it.c * G * Dq * Dq;
             for (int g = 0; g < G; ++g) {
@@ -664,6 +672,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
 }
 
+// Wait bound of the next launches (0 = the default) and the one-shot
+// expiry test (see mdn_set_gram_wait_limit / mdn_gram_expire_next_wait).
+static std::atomic<unsigned long long> g_wait_ns{0};
+static std::atomic<int> g_expire_next{0};
+
 template <int MODE>
 int run(const GatherArgs& ga, const int4* chunks, const int* gcount, int ngroups, int cap, const int* sorted,
         float* partial, int ncta, cudaStream_t s) {
@@ -684,7 +697,10 @@ int run(const GatherArgs& ga, const int4* chunks, const int* gcount, int ngroups
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return cuda_fail(e, "k_gram_tc: smem attribute");
     if (ncta <= 0 || ngroups <= 0) return MDN_OK;
-    kern<<<(unsigned)ncta, NTHREADS, bytes, s>>>(ga, chunks, gcount, ngroups, cap, sorted, partial, rows, S);
+    const unsigned long long wait_ns = g_wait_ns.load() ? g_wait_ns.load() : WAIT_NS;
+    const int expire = g_expire_next.exchange(0);
+    kern<<<(unsigned)ncta, NTHREADS, bytes, s>>>(ga, chunks, gcount, ngroups, cap, sorted, partial, rows, S, wait_ns,
+                                                 expire);
     return check_launch("k_gram_tc");
 }
 
@@ -701,6 +717,9 @@ int launch_gram_tc(const GatherArgs& ga, int precision, const int4* chunks, cons
         default: return fail(MDN_EINVAL, "train: bad Gram precision");
     }
 }
+
+void gram_tc_set_wait(unsigned long long ns) { tc::g_wait_ns.store(ns); }
+void gram_tc_expire_next(int enable) { tc::g_expire_next.store(enable ? 1 : 0); }
 
 int gram_tc_error(int* out) {
     int v = 0, zero = 0;

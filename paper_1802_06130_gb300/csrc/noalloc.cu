@@ -14,8 +14,11 @@
 //  * g_scratch is MDN_STATIC_SCRATCH_BYTES (48 MiB) on EVERY device that loads
 //    the library, held until the process exits;
 //  * the first call on a device, with that device current, looks up the
-//    array's device address (cudaGetSymbolAddress) and caches it; make that
-//    first call before any stream capture;
+//    array's device address (cudaGetSymbolAddress) and caches it per device
+//    ordinal; make that first call before any stream capture.  The cache is
+//    not told about cudaDeviceReset: a process that resets a device (which
+//    ends its context and every device address in it) must not call this
+//    entry point on that device again;
 //  * every call on a device shares the same array, which keeps the previous
 //    call's contents: calls whose work overlaps on the GPU (other streams,
 //    other host threads) race and corrupt each other's results.  Nothing in
@@ -64,15 +67,16 @@ extern "C" int mdn_denoise_multiscale_static(const void* noisy, int32_t dtype, i
                                              void* out, void* const* bucket_maps, void* stream) {
     using namespace mdn;
     if (levels < 1 || levels > 8) return fail(MDN_EINVAL, "denoise_multiscale_static: levels must be 1..8");
-    if (n < 0 || h < 0 || w < 0) return fail(MDN_ESHAPE, "denoise_multiscale_static: negative size");
-    if (dtype != MDN_F32 && dtype != MDN_F16) return fail(MDN_EINVAL, "denoise_multiscale_static: bad dtype");
+    // sizes first (bounded without overflow), then the workspace arithmetic
+    int rc = check_img(noisy, dtype, n, h, w, "denoise_multiscale_static");
+    if (rc) return rc;
     const size_t need = mdn_denoise_workspace_bytes(n, h, w, levels, dtype);
     if (need > kStaticScratchBytes)
         return fail(MDN_EWORKSPACE, "denoise_multiscale_static: this image needs " + std::to_string(need) +
                                         " bytes of scratch, more than the 48 MiB static array; use "
                                         "mdn_denoise_multiscale with a caller workspace");
     void* scratch = nullptr;
-    int rc = scratch_address(&scratch);
+    rc = scratch_address(&scratch);
     if (rc) return rc;
     return mdn_denoise_multiscale(noisy, dtype, n, h, w, levels, banks, bank_dtype, geom, bparams, out,
                                   bucket_maps, scratch, kStaticScratchBytes, stream);

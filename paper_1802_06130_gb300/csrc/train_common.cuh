@@ -149,6 +149,8 @@ __device__ __forceinline__ void gather_rows(const GatherArgs& ga, const int* col
 inline int gram_border(const mdn_geometry& g) { return g.r_coarse > g.r_fine ? g.r_coarse : g.r_fine; }
 
 int gram_tc_error(int* out);
+void gram_tc_set_wait(unsigned long long ns);
+void gram_tc_expire_next(int enable);
 // Tensor-core Gram over the per-group chunk tables: CTA b accumulates, group
 // after group, the chunks whose owner field (w) is b; ncta CTAs.
 int launch_gram_tc(const GatherArgs& ga, int precision, const int4* chunks, const int* gcount, int ngroups, int cap,

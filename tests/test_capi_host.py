@@ -168,3 +168,72 @@ def test_product_path_has_no_oracle_dependency():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in txt.lower().replace("oracle-free", ""), f
+
+
+def test_oversized_images_rejected_without_overflow(L):
+    """Sizes are bounded factor by factor before any product is formed: an n
+    whose n * 3 * h * w wraps a signed 64-bit product to 0 is still rejected
+    (and the null-pointer check is not skipped by a wrapped product)."""
+    SIZE_MAX = 2 ** 64 - 1
+    big = 1 << 20
+    n_wrap = 1 << 26                       # 3 * 2^26 * 2^40 wraps int64 to 0... times 3 does not, 2^66 does
+    for n, h, w in [(n_wrap, big, big), (1 << 24, big, big), (1, big + 1, 8), (2, 32768, 32768), (-1, 8, 8)]:
+        rc = L.mdn_filter_level(None, None, 0, n, h, w, C.c_void_p(48), 0, C.byref(mdn.Geometry(3, -1)),
+                                C.byref(mdn.default_bparams(0)), C.c_void_p(32), None, None)
+        assert rc == 2, (n, h, w, rc)
+        if n >= 0:
+            assert L.mdn_denoise_workspace_bytes(n, h, w, 3, mdn.F16) == SIZE_MAX
+            assert L.mdn_pyramid_bytes(n, h, w, 3, mdn.F16) == SIZE_MAX
+    # the largest accepted batch: n * 3 * h * w = 2^31 - 1 rounded down
+    h = w = 1024
+    n_max = (2 ** 31 - 1) // (3 * h * w)
+    assert L.mdn_denoise_workspace_bytes(n_max, h, w, 3, mdn.F16) < SIZE_MAX
+    assert L.mdn_denoise_workspace_bytes(n_max + 1, h, w, 3, mdn.F16) == SIZE_MAX
+
+
+def test_static_entry_checks_sizes_before_scratch_arithmetic(L):
+    """mdn_denoise_multiscale_static validates the image sizes before it
+    computes the scratch it would need, so an overflowing size is a shape
+    error, not a size that happens to fit the static array."""
+    raw = C.CDLL(mdn.build())
+    f = raw.mdn_denoise_multiscale_static
+    f.restype = C.c_int
+    f.argtypes = [C.c_void_p, C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_int32, C.POINTER(C.c_void_p),
+                  C.c_int32, C.POINTER(mdn.Geometry), C.POINTER(mdn.BucketParams), C.c_void_p,
+                  C.POINTER(C.c_void_p), C.c_void_p]
+    bp = mdn.default_bparams(0)
+    barr = (C.c_void_p * 2)(16, 16)
+    parr = (mdn.BucketParams * 2)(bp, bp)
+    rc = f(C.c_void_p(16), mdn.F16, 1 << 26, 1 << 20, 1 << 20, 3, barr, mdn.F16, C.byref(mdn.Geometry(3, 3)), parr,
+           C.c_void_p(32), None, None)
+    assert rc == 2 and b"too large" in L.mdn_last_error()
+    rc = f(None, mdn.F16, 1, 64, 64, 3, barr, mdn.F16, C.byref(mdn.Geometry(3, 3)), parr, C.c_void_p(32), None, None)
+    assert rc == 1 and b"null" in L.mdn_last_error()
+
+
+def test_depth_rule_behind_the_c_abi(L):
+    """Section 5's depth rule and its noise factors are library calls: exact
+    factors of the composed binomial kernels (70/256 at level 1), the level
+    counts 1 (sigma already below 2/255), 2, 3, 4, 5 at sigma 1, 5, 15, 25,
+    50 (0-255 scale), the clamps, and argument errors."""
+    assert L.mdn_pyramid_noise_factor(0) == 1.0
+    assert abs(L.mdn_pyramid_noise_factor(1) - 70 / 256) < 1e-15
+    # level 2 by hand: c_2 = b * (b upsampled by 2), sum of squares
+    b = np.array([1, 4, 6, 4, 1]) / 16
+    b2 = np.zeros(9)
+    b2[::2] = b
+    c2 = np.convolve(b, b2)
+    assert abs(L.mdn_pyramid_noise_factor(2) - (c2 ** 2).sum()) < 1e-15
+    f = [L.mdn_pyramid_noise_factor(l) for l in range(8)]
+    assert all(f[i + 1] < f[i] for i in range(7))
+    assert L.mdn_pyramid_noise_factor(8) == -1.0 and L.mdn_pyramid_noise_factor(-1) == -1.0
+    got = [L.mdn_levels_for_sigma(s / 255, 2 / 255, 1, 8) for s in (1, 5, 15, 25, 50)]
+    assert got == [1, 2, 3, 4, 5]
+    assert L.mdn_levels_for_sigma(1 / 255, 2 / 255, 2, 8) == 2
+    assert L.mdn_levels_for_sigma(1e6, 2 / 255, 1, 5) == 5
+    for bad in [(-1.0, 2 / 255, 1, 8), (0.1, 0.0, 1, 8), (0.1, 2 / 255, 0, 8), (0.1, 2 / 255, 1, 9),
+                (0.1, 2 / 255, 5, 4)]:
+        assert L.mdn_levels_for_sigma(*bad) == -1
+    assert mdn.levels_for_sigma(15 / 255) == 3 and mdn.levels_for_sigma(1 / 255, min_levels=2) == 2
+    with pytest.raises(ValueError):
+        mdn.pyramid_noise_factor(9)

@@ -642,8 +642,10 @@ def test_pyramid_noise_factor_and_level_count():
     (70/256 at level 1, then about 0.45, 0.49, 0.5 per level: the noise is no
     longer white after the first level), and the rule of Section 5 (coarsest
     sigma below 2/255) gives 2 levels at sigma 5, 3 at 15, 4 at 25 and 5 at 50
-    (on the 0-255 scale)."""
+    (on the 0-255 scale).  The factors and the rule are the library's
+    (mdn_pyramid_noise_factor, mdn_levels_for_sigma; host arithmetic)."""
     import paper_1802_06130_gb300 as mdn
+    mdn.build()
     assert mdn.pyramid_noise_factor(0) == 1.0
     assert abs(mdn.pyramid_noise_factor(1) - 70 / 256) < 1e-15
     n = np.random.default_rng(5).standard_normal((3, 1024, 1024)) * 0.1
@@ -653,5 +655,5 @@ def test_pyramid_noise_factor_and_level_count():
         e = 16 >> l
         ratio = zs[l][:, e:-e, e:-e].std() / s0
         assert abs(ratio / mdn.pyramid_noise_factor(l) - 1) < 0.02, (l, ratio)
-    assert [mdn.levels_for_sigma(s / 255) for s in (5, 15, 25, 50)] == [2, 3, 4, 5]
-    assert mdn.levels_for_sigma(1 / 255) == 2 and mdn.levels_for_sigma(1e6, max_levels=5) == 5
+    assert [mdn.levels_for_sigma(s / 255) for s in (1, 5, 15, 25, 50)] == [1, 2, 3, 4, 5]
+    assert mdn.levels_for_sigma(1 / 255, min_levels=2) == 2 and mdn.levels_for_sigma(1e6, max_levels=5) == 5
