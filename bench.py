@@ -194,6 +194,147 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- accuracy
+
+def _dilate(mask, r):
+    """Binary dilation by a (2r+1)^2 square (bookkeeping for the band rule)."""
+    if r <= 0:
+        return mask.copy()
+    h, w = mask.shape
+    out = np.zeros_like(mask)
+    for dy in range(-r, r + 1):
+        for dx in range(-r, r + 1):
+            ys, xs = slice(max(dy, 0), h + min(dy, 0)), slice(max(dx, 0), w + min(dx, 0))
+            yd, xd = slice(max(-dy, 0), h + min(-dy, 0)), slice(max(-dx, 0), w + min(-dx, 0))
+            out[yd, xd] |= mask[ys, xs]
+    return out
+
+
+def _affected(mism, r_coarse, shapes):
+    """Finest-level pixels whose output depends on a bucket that differs from
+    the oracle's (own bucket, or the coarser output within r_coarse)."""
+    aff = mism[-1].copy()
+    for l in range(len(mism) - 2, -1, -1):
+        h, w = shapes[l]
+        up = np.repeat(np.repeat(_dilate(aff, max(r_coarse, 0)), 2, 0), 2, 1)[:h, :w]
+        aff = mism[l] | up
+    return aff
+
+
+def accuracy_headline(mdn, frame, banks32, dev, crop=128, margin=64):
+    """Headline path (3 levels, 4032x3024) against the FP64 oracle on crops of
+    one benchmark frame: max-abs error per path at pixels whose buckets (and
+    coarser dependencies) agree with the oracle's, plus the threshold-band and
+    mismatch counts.  The oracle gets the banks unrounded (the FP32 values the
+    FP16 device banks were rounded from) and, separately, FP16-rounded (the
+    kernel's arithmetic alone)."""
+    import torch
+    import oracle as O
+    Hf, Wf = frame.shape[1:]
+    geom_o, geom = O.Geometry(3, 3), mdn.Geometry(3, 3)
+    bps = [mdn.default_bparams(0), mdn.default_bparams(1)]
+    banks64 = [b.astype(np.float64) for b in banks32]
+    banks16 = [O.round_storage(b, "f16") for b in banks64]
+    dbanks = {"f16": [torch.tensor(b, dtype=torch.float16, device=dev) for b in banks32],
+              "f32": [torch.tensor(b, dtype=torch.float32, device=dev) for b in banks32]}
+    crops = [(0, 0), (0, Wf - crop), (Hf - crop, 0), (Hf - crop, Wf - crop), (1504, 2000), (752, 3136)]
+    out = {"crops": f"{len(crops)} crops of {crop}x{crop} (corners and interior) of frame 0, oracle run on the "
+                    f"crop plus a {margin}-pixel margin; errors at pixels not affected by a bucket that differs "
+                    "from the oracle's (those differ only in the 1e-5 threshold band)", "paths": {}}
+    for storage, tdt, bank_dt in [("f16", torch.float16, "f16"), ("f32", torch.float32, "f16"),
+                                  ("f32", torch.float32, "f32")]:
+        z = O.round_storage(frame.astype(np.float64), storage)
+        zt = torch.tensor(z, dtype=tdt, device=dev)[None]
+        maps = [torch.empty((1, Hf, Wf), dtype=torch.uint8, device=dev),
+                torch.empty((1, (Hf + 1) // 2, (Wf + 1) // 2), dtype=torch.uint8, device=dev)]
+        y = mdn.denoise_multiscale(zt, dbanks[bank_dt], geom, bps, bucket_maps=maps)[0].float().cpu().numpy()
+        gmaps = [m[0].cpu().numpy() for m in maps]
+        pairs = [("unrounded", banks64), ("f16_rounded", banks16)] if bank_dt == "f16" else [("unrounded", banks64)]
+        for bank_name, bo in pairs:
+            worst, band, aff_n, mism_out, npx = 0.0, 0, 0, 0, 0
+            for (y0, x0) in crops:
+                cy0, cx0 = max(y0 - margin, 0), max(x0 - margin, 0)
+                cy1, cx1 = min(y0 + crop + margin, Hf), min(x0 + crop + margin, Wf)
+                ref = O.denoise_multiscale(z[:, cy0:cy1, cx0:cx1], bo, geom_o, storage=storage, mirror32=True)
+                mism = []
+                for l in range(2):
+                    s_ = 2 ** l
+                    g = gmaps[l][cy0 // s_: cy0 // s_ + ref.buckets[l].shape[0],
+                                 cx0 // s_: cx0 // s_ + ref.buckets[l].shape[1]]
+                    m = g != ref.buckets[l]
+                    inner = np.zeros_like(m)
+                    b_ = 16 // s_
+                    inner[b_ if cy0 else 0: m.shape[0] - (b_ if cy1 < Hf else 0),
+                          b_ if cx0 else 0: m.shape[1] - (b_ if cx1 < Wf else 0)] = True
+                    mism_out += int((m & ~ref.bands[l] & inner).sum())
+                    band += int((ref.bands[l] & inner).sum())
+                    mism.append(m & inner)
+                aff = _affected(mism, 3, [r.shape[1:] for r in ref.pyramid])
+                ry, rx = y0 - cy0, x0 - cx0
+                keep = ~aff[ry:ry + crop, rx:rx + crop]
+                d = np.abs(y[:, y0:y0 + crop, x0:x0 + crop] - ref.out[:, ry:ry + crop, rx:rx + crop]).max(axis=0)
+                worst = max(worst, float(d[keep].max()) if keep.any() else 0.0)
+                aff_n += int((~keep).sum())
+                npx += crop * crop
+            bar = 2e-3 if storage == "f16" else 1e-4
+            rec = {"max_abs": float(f"{worst:.3g}"), "bar": bar, "within_bar": worst <= bar, "pixels": npx,
+                   "pixels_excluded_affected": aff_n, "band_pixels": band, "bucket_mismatches_outside_band": mism_out}
+            if storage == "f32" and bank_dt == "f16" and bank_name == "unrounded":
+                rec["note"] = ("FP16 bank rounding alone exceeds the FP32 path's 1e-4 bar: the FP32 path is held to it "
+                               "with FP32 banks (next entry) or against the FP16-rounded banks")
+            out["paths"][f"{storage}_storage_{bank_dt}_banks_vs_oracle_{bank_name}_banks"] = rec
+    return out
+
+
+def accuracy_training(mdn, dev, n=4, size=1024):
+    """Config-3 training precisions against the FP64 oracle on a subset of n
+    of the benchmark's pairs: Gram and bank relative Frobenius (whole bank and
+    per bucket with n_k >= 10 D), and the denoised-output max-abs error of each
+    precision's bank on a held-out 1024x1024 image (single-level cross-channel
+    7x7x3 filter) at pixels whose bucket agrees with the oracle's."""
+    import torch
+    import oracle as O
+    import synth
+    geom_o, geom = O.Geometry(3, -1, cross=1), mdn.Geometry(3, -1, 1)
+    bp_o, bp = O.default_bparams(0), mdn.default_bparams(0)
+    pairs = [synth.noisy_pair(size, size, 30000 + i) for i in range(n)]
+    t0 = time.perf_counter()
+    gram = counts = None
+    for z, u in pairs:
+        b, _, _ = O.select(z, bp_o, mirror32=True)
+        gram, counts = O.gram_accumulate(z, None, u, b, 216, geom_o, gram, counts)
+    bank_o = O.solve_bank(gram, counts, geom_o, 1e-3)
+    t_oracle = time.perf_counter() - t0
+    zt, ut = synth.noisy_pair(size, size, 39999)
+    bt, band_t, _ = O.select(zt, bp_o, mirror32=True)
+    ref_out = O.filter_level(zt, None, bt, bank_o, geom_o)
+    Z = torch.tensor(np.stack([p[0] for p in pairs]), device=dev)
+    U = torch.tensor(np.stack([p[1] for p in pairs]), device=dev)
+    xt = torch.tensor(zt, dtype=torch.float32, device=dev)[None]
+    D = geom_o.D()
+    big = np.nonzero(counts >= 10 * D)[0]
+    res = {"subset": f"{n} of the 256 config-3 pairs ({n * size * size} patches); oracle Gram + solve "
+                     f"{t_oracle:.1f} s on the host", "buckets_compared": int(len(big)), "precisions": {}}
+    for prec, name in [(0, "fp32_simt"), (1, "tf32"), (2, "bf16"), (3, "split_bf16")]:
+        g, c, bank = mdn.train_level_filters(Z, None, U, geom, bp, prec, lam=1e-3)
+        m = torch.empty((1, size, size), dtype=torch.uint8, device=dev)
+        y = mdn.filter_level(xt, None, bank, geom, bp, buckets_out=m)
+        torch.cuda.synchronize()
+        gn, cn, bn = g.cpu().numpy(), c.cpu().numpy(), bank.cpu().numpy().astype(np.float64)
+        per = [np.linalg.norm(bn[k] - bank_o[k]) / np.linalg.norm(bank_o[k]) for k in big]
+        keep = m[0].cpu().numpy() == bt
+        d = np.abs(y[0].cpu().numpy().astype(np.float64) - ref_out).max(axis=0)
+        res["precisions"][name] = {
+            "gram_rel": float(f"{np.linalg.norm(gn - gram) / np.linalg.norm(gram):.3g}"),
+            "bank_rel": float(f"{np.linalg.norm(bn - bank_o) / np.linalg.norm(bank_o):.3g}"),
+            "bank_rel_per_bucket_median": float(f"{np.median(per):.3g}"),
+            "bank_rel_per_bucket_max": float(f"{np.max(per):.3g}"),
+            "bank_bar": 1e-3, "bank_within_bar": bool(np.max(per) <= 1e-3),
+            "counts_equal": bool(np.array_equal(cn, counts)),
+            "output_max_abs": float(f"{d[keep].max():.3g}"), "output_pixels_excluded": int((~keep).sum())}
+    return res
+
+
 # ---------------------------------------------------------------- GPU arm
 
 def run_variants(mdn, x, geom, dev, stream, reps=10):
@@ -308,18 +449,25 @@ def run_gpu(args, rank, world, frames):
     lv1 = [e[1].elapsed_time(e[2]) for e in evs]
     lv0 = [e[2].elapsed_time(e[3]) for e in evs]
 
-    # ---- end to end: pinned host frames -> device -> denoise -> host ----
+    # ---- end to end: pinned host frames -> device -> denoise -> host, through
+    # mdn_denoise_multiscale_pipelined (chunks of e2e_chunk frames: uploads,
+    # kernels and downloads of consecutive chunks overlap on three streams)
     host_in = torch.empty((n, 3, H, W), dtype=torch.float16, pin_memory=True)
     host_in.copy_(torch.from_numpy(frames.astype(np.float16)))
     host_out = torch.empty_like(host_in, pin_memory=True)
     xin = torch.empty_like(x)
-    ws = torch.empty(mdn.denoise_workspace_bytes(n, H, W, LEVELS, mdn.F16), dtype=torch.uint8, device=dev)
+    dout = torch.empty_like(x)
+    chunk = max(1, min(args.e2e_chunk, n))
+    ws = torch.empty(mdn.denoise_workspace_bytes(chunk, H, W, LEVELS, mdn.F16), dtype=torch.uint8, device=dev)
+    streams = (torch.cuda.Stream(device=dev), stream, torch.cuda.Stream(device=dev))
 
     def e2e_step():
-        xin.copy_(host_in, non_blocking=True)
-        mdn.denoise_multiscale(xin, banks, geom, bps, out=out, ws=ws)
-        host_out.copy_(out, non_blocking=True)
+        mdn.denoise_multiscale_pipelined(host_in, banks, geom, bps, host_out, chunk=chunk, dev_in=xin, dev_out=dout,
+                                         ws=ws, streams=streams)
 
+    e2e_step()
+    torch.cuda.synchronize()
+    assert torch.equal(host_out, ref.cpu()), "pipelined host path differs from the device path"
     for _ in range(max(1, args.warmup)):
         e2e_step()
     torch.cuda.synchronize()
@@ -380,7 +528,8 @@ def run_gpu(args, rank, world, frames):
                      "note": "bound on chip by shared-memory wavefronts and issue (see profiles/); at 768 FLOP per "
                              "13.5 B the kernel's HBM roof is about 5x its FP32 ALU roof"},
         "e2e": {"value": round(e2e_value, 2), "unit": "Mpix/s", "h2d_bytes_per_step": int(pix * 3 * 2),
-                "d2h_bytes_per_step": int(pix * 3 * 2)},
+                "d2h_bytes_per_step": int(pix * 3 * 2), "api": "mdn_denoise_multiscale_pipelined",
+                "chunk_frames": chunk, "ms_per_step": round(ems / e2e_steps, 4)},
         "clocks": {"sm_mhz": clk_summary["sm_mhz"], "sm_max_mhz": clk_summary["sm_max_mhz"],
                    "reasons": clk_summary["reasons"]},
     }
@@ -390,6 +539,10 @@ def run_gpu(args, rank, world, frames):
         line["training"] = run_training(args, dev)
     if args.serve and world == 1:
         line["serving"] = serving_subprocess(args)
+    if args.accuracy and world == 1:
+        line["accuracy"] = {"headline": accuracy_headline(mdn, frames[0], random_banks(7), dev)}
+        if args.train:
+            line["accuracy"]["training_vs_oracle"] = accuracy_training(mdn, dev)
     if args.cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline_block(12, 1)
     print(json.dumps(line), flush=True)
@@ -724,6 +877,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--e2e-chunk", type=int, default=2, help="frames per chunk of the pipelined end-to-end path")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-serve", dest="serve", action="store_false")
     ap.add_argument("--serve-requests", type=int, default=2000)
@@ -731,6 +885,7 @@ def main():
     ap.add_argument("--serve-only", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-train", dest="train", action="store_false")
     ap.add_argument("--no-variants", dest="variants", action="store_false")
+    ap.add_argument("--no-accuracy", dest="accuracy", action="store_false")
     ap.add_argument("--train-images", type=int, default=256)
     ap.add_argument("--train-only", action="store_true", help="only the training section (profiling driver)")
     ap.add_argument("--quality", action="store_true", help="whole-pipeline PSNR sanity check (configs 1 and 2), then exit")

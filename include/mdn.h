@@ -177,6 +177,31 @@ int mdn_denoise_multiscale(const void* noisy, int32_t dtype, int64_t n, int64_t 
                            void* out, void* const* bucket_maps, void* ws, size_t ws_bytes,
                            void* stream);
 
+/* mdn_denoise_multiscale for a batch held in HOST memory, with copies and
+ * kernels overlapped (a deployment layer: the paper describes per-image
+ * inference only).  The batch is cut into chunks of `chunk` images; chunk c
+ * is copied host_noisy -> dev_in on streams[0] (upload), denoised dev_in ->
+ * dev_out on streams[1] (compute) with the same kernels and results as
+ * mdn_denoise_multiscale, and copied dev_out -> host_out on streams[2]
+ * (download); each stage of a chunk waits for the previous stage of that
+ * chunk only, so consecutive chunks' uploads, kernels and downloads overlap.
+ * host_noisy, host_out: HOST [n][3][h][w] buffers of dtype (page-locked
+ * memory is needed for the copies to overlap); dev_in, dev_out: device
+ * [n][3][h][w] buffers; ws: device workspace of at least
+ * mdn_denoise_workspace_bytes(min(chunk, n), h, w, levels, dtype) (chunks run
+ * one after the other on the compute stream and share it); streams: HOST
+ * array of three distinct cudaStream_t.  The uploads and downloads start
+ * after the work already queued on streams[1]; the call is asynchronous and
+ * host_out is complete once streams[1] is synchronised.  Allocates no device
+ * memory (it creates and releases three CUDA events per call).  Bucket maps
+ * are not written.  MDN_EINVAL / MDN_ESHAPE / MDN_EWORKSPACE as for
+ * mdn_denoise_multiscale, and MDN_EINVAL for chunk < 1 or equal streams. */
+int mdn_denoise_multiscale_pipelined(const void* host_noisy, int32_t dtype, int64_t n, int64_t h, int64_t w,
+                                     int32_t levels, const void* const* banks, int32_t bank_dtype,
+                                     const mdn_geometry* geom, const mdn_bucket_params* bparams, void* host_out,
+                                     int64_t chunk, void* dev_in, void* dev_out, void* ws, size_t ws_bytes,
+                                     void* const* streams);
+
 /* Same as mdn_denoise_multiscale, for callers that cannot allocate device
  * memory: a plug-in inside a host application that owns every device
  * allocation, or a real-time pipeline where an allocation (which may

@@ -19,7 +19,7 @@ __all__ = ["build", "lib", "Geometry", "BucketParams", "default_bparams", "MdnEr
            "gram_state_shape", "train_status", "train_cascade", "Server", "F32", "F16", "YCBCR601", "RGB", "GRAM_FP32", "GRAM_TF32",
            "GRAM_BF16", "GRAM_SPLIT_BF16", "augment_dihedral", "dihedral", "estimate_noise", "nearest_level",
            "save_banks", "load_banks", "save_gram_state", "load_gram_state", "paper_grid_bparams",
-           "bucket_map_dtype", "MAX_K", "levels_for_sigma", "pyramid_noise_factor", "set_gram_wait_limit",
+           "bucket_map_dtype", "MAX_K", "levels_for_sigma", "denoise_multiscale_pipelined", "pyramid_noise_factor", "set_gram_wait_limit",
            "gram_expire_next_wait"]
 
 F32, F16 = 0, 1
@@ -153,6 +153,8 @@ def lib():
             "mdn_denoise_workspace_bytes": (sz, [i64, i64, i64, i32, i32]),
             "mdn_denoise_multiscale": (C.c_int, [vp, i32, i64, i64, i64, i32, C.POINTER(vp), i32, G, B, vp,
                                                  C.POINTER(vp), vp, sz, vp]),
+            "mdn_denoise_multiscale_pipelined": (C.c_int, [vp, i32, i64, i64, i64, i32, C.POINTER(vp), i32, G, B,
+                                                           vp, i64, vp, vp, vp, sz, C.POINTER(vp)]),
             "mdn_gram_state_bytes": (sz, [G, i32]),
             "mdn_train_workspace_bytes": (sz, [i64, i64, i64, G, i32, i32]),
             "mdn_train_level_filters": (C.c_int, [vp, vp, vp, i32, i64, i64, i64, G, B, i32, i32, vp, vp,
@@ -332,8 +334,51 @@ def denoise_multiscale(noisy, banks, geom: Geometry, bparams, out=None, bucket_m
     return out if noisy.dim() == 4 else out[0]
 
 
+def denoise_multiscale_pipelined(host_noisy, banks, geom: Geometry, bparams, host_out, chunk: int = 2,
+                                 dev_in=None, dev_out=None, ws=None, streams=None):
+    """Multiscale denoise of a batch in (pinned) host memory with the copies and
+    kernels of consecutive chunks overlapped on three streams
+    (mdn_denoise_multiscale_pipelined).  host_noisy, host_out: [n][3][h][w]
+    CPU tensors; dev_in, dev_out: matching CUDA tensors (allocated if None);
+    ws: workspace for `chunk` images; streams: (upload, compute, download)
+    torch streams (compute defaults to the current stream).  Asynchronous:
+    host_out is complete once the compute stream is synchronised.
+    Returns (dev_in, dev_out, ws, streams) for reuse."""
+    torch = _torch()
+    x = _img(host_noisy)
+    n, _, h, w = x.shape
+    if x.is_cuda or host_out.is_cuda or host_out.shape != x.shape or host_out.dtype != x.dtype:
+        raise ValueError("host_noisy/host_out: matching [n][3][h][w] CPU tensors")
+    if not x.is_contiguous() or not host_out.is_contiguous():
+        raise ValueError("host tensors must be contiguous")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    levels = 1 if geom.r_coarse < 0 else len(banks) + 1
+    nb = len(banks)
+    if len(bparams) != nb:
+        raise ValueError("need one BucketParams per bank")
+    if dev_in is None:
+        dev_in = torch.empty(x.shape, dtype=x.dtype, device=dev)
+    if dev_out is None:
+        dev_out = torch.empty(x.shape, dtype=x.dtype, device=dev)
+    c = max(1, min(chunk, n))
+    need = denoise_workspace_bytes(c, h, w, levels, _dtype_code(x))
+    if ws is None:
+        ws = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    if streams is None:
+        streams = (torch.cuda.Stream(device=dev), torch.cuda.current_stream(dev), torch.cuda.Stream(device=dev))
+    sarr = (C.c_void_p * 3)(*[st.cuda_stream for st in streams])
+    barr = (C.c_void_p * nb)(*[b.data_ptr() for b in banks])
+    parr = (BucketParams * nb)(*bparams)
+    _check(lib().mdn_denoise_multiscale_pipelined(C.c_void_p(x.data_ptr()), _dtype_code(x), n, h, w, levels, barr,
+                                                  _dtype_code(banks[0]), C.byref(geom), parr,
+                                                  C.c_void_p(host_out.data_ptr()), chunk, _dev(dev_in, "dev_in"),
+                                                  _dev(dev_out, "dev_out"), _dev(ws, "ws"),
+                                                  ws.numel() * ws.element_size(), sarr))
+    return dev_in, dev_out, ws, streams
+
+
 def train_level_filters(noisy_lvl, coarse_out, clean_lvl, geom: Geometry, bp: BucketParams,
-                        gram_precision: int = GRAM_FP32, gram=None, counts=None, accumulate=False,
+                        gram_precision: int = GRAM_SPLIT_BF16, gram=None, counts=None, accumulate=False,
                         lam: float = 1e-3, solve: bool = True, ws=None, stream=None):
     """One level of training (mdn_train_level_filters).
 
@@ -468,7 +513,7 @@ def dihedral(img, t: int, stream=None):
     return out
 
 
-def train_cascade(noisy, clean, geom: Geometry, levels: int, bparams=None, gram_precision: int = GRAM_FP32,
+def train_cascade(noisy, clean, geom: Geometry, levels: int, bparams=None, gram_precision: int = GRAM_SPLIT_BF16,
                   lam: float = 1e-3, chunk: int = 0, augment: bool = False, checkpoint: str = None, stream=None):
     """Section 4 training cascade on the GPU: pyramids of the noisy and clean
     images, then for l = L-2 .. 0 (single-scale: l = 0 only) the bucketed

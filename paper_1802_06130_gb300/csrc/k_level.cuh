@@ -405,14 +405,16 @@ namespace v2 {
 template <int NT_, int PY_> struct Shape {
     static constexpr int TW = 32, NT = NT_, PY = PY_, NW = NT / 32, TH = NW * PY;
     static constexpr int HZ = 3;
-    static constexpr int ZW = TW + 2 * HZ, ZH = TH + 2 * HZ;
+    static constexpr int ZW = TW + 2 * HZ + 1, ZH = TH + 2 * HZ;   // row stride 39 (column 38 unused)
     static constexpr int PW = TW + 4, PH = TH + 4;
 };
 using DefShape = Shape<MDN_V2_NT, MDN_V2_PY>;
 
 template <class SH, int RC> struct Coarse {
-    static constexpr int UW = RC >= 0 ? SH::TW / 2 + 2 * RC : 0;
+    static constexpr int UWD = RC >= 0 ? SH::TW / 2 + 2 * RC : 0;   // columns staged
+    static constexpr int UW = RC >= 0 ? 27 : 0;                     // row stride (see the v3 consumer)
     static constexpr int UH = RC >= 0 ? SH::TH / 2 + 2 * RC : 0;
+    static_assert(UWD <= 27, "coarse tile wider than its row stride");
 };
 
 template <int RF, int RC, bool CROSS> struct Slots {
@@ -516,10 +518,22 @@ __device__ __forceinline__ void build_bucket_placement(const SelParams& sp, int 
     }
 }
 
+}  // namespace v2
+namespace v3 {
+template <int RF, int RC, bool CROSS, typename TB>
+__device__ __forceinline__ void filter_group(const float* __restrict__ zb, int zpl, int zst,
+                                             const float* __restrict__ ub, int upl, int ust,
+                                             const unsigned char* __restrict__ bank_s, uint2 kb, int j, float o[3]);
+}  // namespace v3
+namespace v2 {
+
 // One TW x TH tile at (x0, y0) of one image: stage, select, filter, store.
+// ROWS = false: strip filter on the column-slot bank (load_bank_slots);
+// ROWS = true: the lane-group filter of v3 (v3::filter_group) on the row-slot
+// bank (v3::load_bank_rows), whose outputs are bit-identical to k_level3's.
 // smem: tile buffers (tile_bytes<SH, RC>()); bank_s: the bank's slots.
 // zi/ci/oi: this image's planes; bmap_img: its bucket map or nullptr.
-template <class SH, int RF, int RC, bool CROSS, typename TS, typename TB>
+template <class SH, int RF, int RC, bool CROSS, typename TS, typename TB, bool ROWS = false>
 __device__ __forceinline__ void tile_v2(unsigned char* smem, const unsigned char* bank_s, const TS* __restrict__ zi,
                                         const TS* __restrict__ ci, TS* __restrict__ oi, uint8_t* __restrict__ bmap_img,
                                         int H, int W, int Hc, int Wc, int x0, int y0, int K, int color,
@@ -543,15 +557,17 @@ __device__ __forceinline__ void tile_v2(unsigned char* smem, const unsigned char
         zs[i] = ld_f(zi, ((int64_t)c * H + gy) * W + gx);
     }
     if constexpr (RC >= 0) {
+        constexpr int UWD = Coarse<SH, RC>::UWD;
         const int cx0 = x0 / 2 - RC, cy0 = y0 / 2 - RC;
-        for (int i = tid; i < UH * UW; i += NT) {
-            int r = i / UW, q = i % UW;
+        for (int i = tid; i < UH * UWD; i += NT) {
+            int r = i / UWD, q = i % UWD;
             int gy = clampi(cy0 + r, 0, Hc - 1), gx = clampi(cx0 + q, 0, Wc - 1);
             int64_t o = (int64_t)gy * Wc + gx;
             float a, b, c;
             rgb_to_work(ld_f(ci, o), ld_f(ci, o + (int64_t)Hc * Wc), ld_f(ci, o + 2 * (int64_t)Hc * Wc), color, a, b,
                         c);
-            us[i] = a; us[UH * UW + i] = b; us[2 * UH * UW + i] = c;
+            const int e = r * UW + q;
+            us[e] = a; us[UH * UW + e] = b; us[2 * UH * UW + e] = c;
         }
     }
     __syncthreads();
@@ -610,6 +626,30 @@ __device__ __forceinline__ void tile_v2(unsigned char* smem, const unsigned char
         if (bmap_img && gy < H && gx < W) bmap_img[(int64_t)gy * W + gx] = (uint8_t)k;
     }
     __syncthreads();
+    if constexpr (ROWS) {
+        // ---- filtering: warps cover 2 rows x 16 columns per pass, lane groups of 8 ----
+        constexpr int NW = NT / 32;
+        static_assert(NW % 2 == 0 && TH % NW == 0, "passes of NW rows must cover the tile");
+        const int g = lane >> 3, j = lane & 7, ro = g >> 1, c0 = 16 * (warp & 1) + 8 * (g & 1);
+#pragma unroll 1
+        for (int pass = 0; pass < TH / NW; ++pass) {
+            const int r = 2 * ((warp >> 1) + (NW / 2) * pass) + ro;
+            const uint2 kb = *reinterpret_cast<const uint2*>(bk + r * TW + c0);
+            float o[3];
+            v3::filter_group<RF, RC, CROSS, TB>(zs + (r + HZ - RF) * ZW + c0 + HZ - RF, ZH * ZW, ZW,
+                                                 us + (r / 2) * UW + c0 / 2, UH * UW, UW, bank_s, kb, j, o);
+            const int gy = y0 + r, gx = x0 + c0 + j;
+            if (gy < H && gx < W) {
+                float R, Gc, B;
+                work_to_rgb(o[0], o[1], o[2], color, R, Gc, B);
+                const int64_t po = (int64_t)gy * W + gx;
+                st_f(oi, po, R);
+                st_f(oi, (int64_t)H * W + po, Gc);
+                st_f(oi, 2 * (int64_t)H * W + po, B);
+            }
+        }
+        return;
+    }
     // ---- filtering: lane = column, warp = strip of PY rows ----
     const int q = lane, r0 = warp * PY;
     const unsigned char* hb[PY];
@@ -729,10 +769,27 @@ int run2(const LevelArgs& a, cudaStream_t s) {
 }  // namespace v2
 
 // ==========================================================================
-// Warp-specialised variant (v3).  Producer warps (4) stage tile t+1 (global
+// Warp-specialised variant (v3).  Producer warps (8) stage tile t+1 (global
 // loads, tensor, features, buckets, RGB -> working space) into one of two
 // shared-memory stages while consumer warps (8) filter tile t from the other
-// stage, exactly as in v2.  Hand-off uses named barriers:
+// stage.
+//
+// Consumer mapping (conflict-free by construction).  A consumer warp covers
+// 2 tile rows x 16 columns; its 4 groups of 8 lanes take (row offset g >> 1,
+// columns 8 (g & 1) .. + 7), and lane j of a group is filter row dy = j - r
+// of a block of radius r (lanes j > 2r idle).  The bank holds one 16-byte
+// ROW slot per (bucket, output channel, block, dy) with the 2r+1 taps of
+// that row (dx = -r..r), so at every coefficient load the active lanes of a
+// group read consecutive 16-byte slots of one bucket -- one wavefront per
+// group whatever the buckets of the neighbouring pixels.  Each lane keeps its
+// patch row (8 + 2r values; coarse: 4 + 2r) in registers for the group's 8
+// pixels; the row strides (39 fine, 27 coarse floats) put the rows and
+// column groups a warp reads in distinct banks, and the two row offsets of a
+// warp read the same coarse row (broadcast).  The per-lane partial sums of
+// the 8 pixels x 3 channels are reduce-scattered over the group with
+// shuffles, leaving pixel j's three channels in lane j, so a warp's stores
+// cover 2 rows x 16 consecutive columns.
+// Hand-off uses named barriers:
 //   FULL[s]  : producers bar.arrive, consumers bar.sync   (128 + 256 threads)
 //   EMPTY[s] : consumers bar.arrive, producers bar.sync   (256 + 128 threads)
 //   PROD     : producer-internal bar.sync (128 threads)
@@ -744,13 +801,14 @@ int run2(const LevelArgs& a, cudaStream_t s) {
 // ==========================================================================
 namespace v3 {
 
-constexpr int TW = 32, TH = 32, PY = 4;
+constexpr int TW = 32, TH = 32;
 constexpr int NCW = 8, NPW = 8;                 // consumer / producer warps
 constexpr int NC = NCW * 32, NP = NPW * 32, NT = NC + NP;
 constexpr int HZ = 3;
-constexpr int ZW = TW + 2 * HZ, ZH = TH + 2 * HZ;
+constexpr int ZW = TW + 2 * HZ + 1, ZH = TH + 2 * HZ;   // row stride 39 (odd; column 38 is not read)
 constexpr int PW = TW + 4, PH = TH + 4;
-static_assert(NCW * PY == TH, "consumer strips must cover the tile");
+constexpr int PX = 8;                           // pixels per lane group
+static_assert(NCW * 32 == 8 * TW && TH % 8 == 0, "a consumer pass (8 warps x 2 rows x 16 columns) covers 8 tile rows");
 
 enum { BAR_FULL0 = 1, BAR_EMPTY0 = 3, BAR_PROD = 5 };
 
@@ -758,9 +816,153 @@ __device__ __forceinline__ void bar_sync(int id, int n) { asm volatile("bar.sync
 __device__ __forceinline__ void bar_arrive(int id, int n) { asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 
 template <int RC> struct Coarse {
-    static constexpr int UW = RC >= 0 ? TW / 2 + 2 * RC : 0;
+    static constexpr int UWD = RC >= 0 ? TW / 2 + 2 * RC : 0;   // columns staged
+    static constexpr int UW = RC >= 0 ? 27 : 0;                 // row stride (conflict-free coarse rows)
     static constexpr int UH = RC >= 0 ? TH / 2 + 2 * RC : 0;
+    static_assert(UWD <= 27, "coarse radius too large for the row stride");
 };
+
+// Row-slot bank layout: for bucket k, output channel oc, the coarse blocks of
+// the input channels, then their fine blocks; one slot per block row dy
+// holding taps dx = -r..r (zero padded to 8 elements).
+template <int RF, int RC, bool CROSS> struct RowSlots {
+    static constexpr int NCH = CROSS ? 3 : 1;
+    static constexpr int NCR = RC >= 0 ? 2 * RC + 1 : 0, NFR = 2 * RF + 1;
+    static constexpr int PER_OC = NCH * (NCR + NFR);
+    static constexpr int S = 3 * PER_OC;                  // slots per bucket
+};
+template <int RF, int RC, bool CROSS, typename TB> constexpr int bucket_bytes_rows() {
+    return RowSlots<RF, RC, CROSS>::S * v2::SlotBytes<TB>::B;
+}
+
+template <int RF, int RC, bool CROSS, typename TB>
+__device__ __forceinline__ void load_bank_rows(const TB* __restrict__ bank, int K, unsigned char* bank_s, int tid,
+                                               int nthreads) {
+    using G = Geo<RF, RC, CROSS>;
+    using SL = RowSlots<RF, RC, CROSS>;
+    constexpr int SB = v2::SlotBytes<TB>::B;
+    constexpr int E = SB / (int)sizeof(TB);   // 8 elements per slot
+    constexpr int BB = bucket_bytes_rows<RF, RC, CROSS, TB>();
+    const int total = K * SL::S * E;
+    for (int i = tid; i < total; i += nthreads) {
+        const int e = i % E, slot = (i / E) % SL::S, k = i / (E * SL::S);
+        const int oc = slot / SL::PER_OC, sr = slot % SL::PER_OC;
+        int src = -1;
+        if (sr < SL::NCH * SL::NCR) {              // coarse block of channel cc, row dyi
+            const int cc = sr / (SL::NCR > 0 ? SL::NCR : 1), dyi = sr % (SL::NCR > 0 ? SL::NCR : 1);
+            if (e < SL::NCR) src = cc * G::PC + dyi * SL::NCR + e;
+        } else {
+            const int t = sr - SL::NCH * SL::NCR;
+            const int cc = t / SL::NFR, dyi = t % SL::NFR;
+            if (e < SL::NFR) src = SL::NCH * G::PC + cc * G::PF + dyi * SL::NFR + e;
+        }
+        const TB v = src >= 0 ? bank[((int64_t)k * 3 + oc) * G::D + src] : TB(0.f);
+        reinterpret_cast<TB*>(bank_s + (size_t)k * BB + slot * SB)[e] = v;
+    }
+}
+
+
+// Filter of one lane group (8 consecutive pixels of one row, the calling
+// lane being j = lane & 7): the per-lane partial sums over each block row
+// dy = j - r, then a reduce-scatter over the group with shuffles, after which
+// o[] holds the three working-space outputs of pixel j.  Every lane of the
+// warp must call it (the shuffles use the full mask).
+//   zb:  fine plane of input channel 0 at (patch row 0, patch column 0) of the
+//        group's first pixel, i.e. (row r - RF, column c0 - RF) of the pixel
+//        grid; zpl: plane stride; zst: row stride (floats, working space)
+//   ub:  coarse plane of channel 0 at (row r/2, column c0/2) of the coarse
+//        stage (whose origin is RC rows and columns before the coarse pixel of
+//        the tile origin); upl, ust: plane and row strides
+//   kb:  the 8 pixels' buckets (one byte each, pixel p in byte p)
+// The arithmetic (FMA order within a lane, reduction tree) is fixed, so any
+// kernel calling this gives bit-identical outputs for the same inputs.
+template <int RF, int RC, bool CROSS, typename TB>
+__device__ __forceinline__ void filter_group(const float* __restrict__ zb, int zpl, int zst,
+                                             const float* __restrict__ ub, int upl, int ust,
+                                             const unsigned char* __restrict__ bank_s, uint2 kb, int j, float o[3]) {
+    using SL = RowSlots<RF, RC, CROSS>;
+    constexpr int SB = v2::SlotBytes<TB>::B;
+    constexpr int BSTRIDE = bucket_bytes_rows<RF, RC, CROSS, TB>();
+    const unsigned FULL = 0xffffffffu;
+    const unsigned char* hb[PX];
+#pragma unroll
+    for (int p = 0; p < PX; ++p)
+        hb[p] = bank_s + (size_t)(((p < 4 ? kb.x : kb.y) >> (8 * (p & 3))) & 0xffu) * BSTRIDE;
+    float acc[3][PX];
+#pragma unroll
+    for (int oc = 0; oc < 3; ++oc)
+#pragma unroll
+        for (int p = 0; p < PX; ++p) acc[oc][p] = 0.f;
+#pragma unroll
+    for (int oc = 0; oc < 3; ++oc) {
+        int slot = oc * SL::PER_OC;
+        if constexpr (RC >= 0) {
+            constexpr int NCOL = PX / 2 + 2 * RC;
+#pragma unroll
+            for (int cc = 0; cc < SL::NCH; ++cc, slot += SL::NCR) {
+                const int c = CROSS ? cc : oc;
+                if (j < SL::NCR) {
+                    // coarse row r/2 + RC + dy (dy = j - RC); tap dx of pixel p at column k = p/2 + RC + dx
+                    const float* src = ub + c * upl + j * ust;
+                    float col[NCOL];
+#pragma unroll
+                    for (int k = 0; k < NCOL; ++k) col[k] = src[k];
+#pragma unroll
+                    for (int p = 0; p < PX; ++p) {
+                        float h[8];
+                        v2::load_slot<TB>(hb[p] + (slot + j) * SB, h);
+#pragma unroll
+                        for (int d = 0; d < SL::NCR; ++d) acc[oc][p] = fmaf(h[d], col[p / 2 + d], acc[oc][p]);
+                    }
+                }
+            }
+        }
+        constexpr int NCOL = PX + 2 * RF;
+#pragma unroll
+        for (int cc = 0; cc < SL::NCH; ++cc, slot += SL::NFR) {
+            const int c = CROSS ? cc : oc;
+            if (j < SL::NFR) {
+                // fine row r + dy (dy = j - RF); tap dx of pixel p at column k = p + RF + dx
+                const float* src = zb + c * zpl + j * zst;
+                float col[NCOL];
+#pragma unroll
+                for (int k = 0; k < NCOL; ++k) col[k] = src[k];
+#pragma unroll
+                for (int p = 0; p < PX; ++p) {
+                    float h[8];
+                    v2::load_slot<TB>(hb[p] + (slot + j) * SB, h);
+#pragma unroll
+                    for (int d = 0; d < SL::NFR; ++d) acc[oc][p] = fmaf(h[d], col[p + d], acc[oc][p]);
+                }
+            }
+        }
+    }
+    // reduce-scatter over the group's 8 lanes: lane j keeps pixel j
+    float w4[3][4], w2[3][2];
+    const bool b2 = j & 4, b1 = j & 2, b0 = j & 1;
+#pragma unroll
+    for (int oc = 0; oc < 3; ++oc)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float keep = b2 ? acc[oc][q + 4] : acc[oc][q];
+            const float send = b2 ? acc[oc][q] : acc[oc][q + 4];
+            w4[oc][q] = keep + __shfl_xor_sync(FULL, send, 4);
+        }
+#pragma unroll
+    for (int oc = 0; oc < 3; ++oc)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const float keep = b1 ? w4[oc][q + 2] : w4[oc][q];
+            const float send = b1 ? w4[oc][q] : w4[oc][q + 2];
+            w2[oc][q] = keep + __shfl_xor_sync(FULL, send, 2);
+        }
+#pragma unroll
+    for (int oc = 0; oc < 3; ++oc) {
+        const float keep = b0 ? w2[oc][1] : w2[oc][0];
+        const float send = b0 ? w2[oc][0] : w2[oc][1];
+        o[oc] = keep + __shfl_xor_sync(FULL, send, 1);
+    }
+}
 
 template <int RC> constexpr size_t stage_bytes() {
     return sizeof(float) * (3 * ZH * ZW + 3 * Coarse<RC>::UH * Coarse<RC>::UW) + TH * TW;
@@ -770,7 +972,7 @@ template <int RC> constexpr size_t front_bytes() {
     return ((2 * stage_bytes<RC>() + scratch_bytes()) + 15) & ~size_t(15);
 }
 template <int RF, int RC, bool CROSS, typename TB> size_t smem_need(int K) {
-    return front_bytes<RC>() + (size_t)K * v2::bucket_units<RF, RC, CROSS, TB>() * 16;
+    return front_bytes<RC>() + (size_t)K * bucket_bytes_rows<RF, RC, CROSS, TB>();
 }
 
 template <int RF, int RC, bool CROSS, typename TS, typename TB>
@@ -779,11 +981,10 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
                                                   const TB* __restrict__ bank, int H, int W, int Hc, int Wc,
                                                   int nimg, int K, int color, SelParams sp, float w0, float w1,
                                                   float w2) {
-    using G = Geo<RF, RC, CROSS>;
-    using SL = v2::Slots<RF, RC, CROSS>;
-    constexpr int UW = Coarse<RC>::UW, UH = Coarse<RC>::UH;
+    using SL = RowSlots<RF, RC, CROSS>;
+    constexpr int UW = Coarse<RC>::UW, UH = Coarse<RC>::UH, UWD = Coarse<RC>::UWD;
     constexpr int SB = v2::SlotBytes<TB>::B;
-    constexpr int BSTRIDE = v2::bucket_units<RF, RC, CROSS, TB>() * 16;
+    constexpr int BSTRIDE = bucket_bytes_rows<RF, RC, CROSS, TB>();
     constexpr size_t SBY = stage_bytes<RC>();
     extern __shared__ __align__(16) unsigned char smem[];
     float* ps = reinterpret_cast<float*>(smem + 2 * SBY);   // producer scratch [3][PH][PW]
@@ -791,10 +992,7 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
     unsigned char* bank_s = smem + front_bytes<RC>();
     const int tid = threadIdx.x;
 
-    __shared__ uint8_t bpos[256];   // bucket -> slot block (bank-group aware)
-    v2::build_bucket_placement(sp, K, bpos, tid, NT);
-    __syncthreads();
-    v2::load_bank_slots<RF, RC, CROSS, TB>(bank, K, bank_s, tid, NT, bpos);   // once per persistent CTA
+    load_bank_rows<RF, RC, CROSS, TB>(bank, K, bank_s, tid, NT);   // once per persistent CTA
     __syncthreads();
 
     const int tiles_x = (W + TW - 1) / TW, tiles_y = (H + TH - 1) / TH;
@@ -816,7 +1014,7 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
         constexpr int NZV = (3 * ZH * NCHUNK + NP - 1) / NP;
         constexpr int NZS = (3 * ZH * ZW + NP - 1) / NP;
         constexpr int NZ = NZV * 4 > NZS ? NZV * 4 : NZS;
-        constexpr int NU = RC >= 0 ? (UH * UW + NP - 1) / NP : 0;
+        constexpr int NU = RC >= 0 ? (UH * UWD + NP - 1) / NP : 0;
         float zreg[NZ];
         float ureg[NU > 0 ? NU : 1][3];
         // vector loads need 4-element-aligned rows and an aligned image base
@@ -856,8 +1054,8 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
 #pragma unroll
                 for (int j = 0; j < NU; ++j) {
                     const int e = pt + j * NP;
-                    if (e < UH * UW) {
-                        int r = e / UW, q = e % UW;
+                    if (e < UH * UWD) {
+                        int r = e / UWD, q = e % UWD;
                         int gy = clampi(cy0 + r, 0, Hc - 1), gx = clampi(cx0 + q, 0, Wc - 1);
                         int64_t o = (int64_t)gy * Wc + gx;
                         ureg[j][0] = ld_f(ci, o);
@@ -905,10 +1103,11 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
 #pragma unroll
                 for (int j = 0; j < NU; ++j) {
                     const int e = pt + j * NP;
-                    if (e < UH * UW) {
+                    if (e < UH * UWD) {
                         float a, b, c;
                         rgb_to_work(ureg[j][0], ureg[j][1], ureg[j][2], color, a, b, c);
-                        us[e] = a; us[UH * UW + e] = b; us[2 * UH * UW + e] = c;
+                        const int o = (e / UWD) * UW + e % UWD;
+                        us[o] = a; us[UH * UW + o] = b; us[2 * UH * UW + o] = c;
                     }
                 }
             }
@@ -984,7 +1183,7 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
                 }
                 int k = bucket_of(t3[0], t3[1], t3[2], sp);
                 k = k < K ? k : K - 1;
-                bk[r * TW + lane] = bpos[k];   // consumers only need the bank block
+                bk[r * TW + lane] = (uint8_t)k;
                 const int gy = y0 + r, gx = x0 + lane;
                 if (bmap && gy < H && gx < W) bmap[((int64_t)img * H + gy) * W + gx] = (uint8_t)k;
             }
@@ -992,7 +1191,8 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
         }
     } else {
         // =============================== consumer ===============================
-        const int q = lane, r0 = warp * PY;
+        const int g = lane >> 3, j = lane & 7;
+        const int ro = g >> 1, c0 = 16 * (warp & 1) + 8 * (g & 1);   // row offset, first column of the group
         for (int64_t i = 0; i < T; ++i) {
             const int s = (int)(i & 1);
             bar_sync(BAR_FULL0 + s, NT);
@@ -1003,69 +1203,20 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
             const int img = (int)(tile / ((int64_t)tiles_x * tiles_y));
             const int trem = (int)(tile % ((int64_t)tiles_x * tiles_y));
             const int x0 = (trem % tiles_x) * TW, y0 = (trem / tiles_x) * TH;
-            const unsigned char* hb[PY];
-#pragma unroll
-            for (int p = 0; p < PY; ++p) hb[p] = bank_s + (size_t)bk[(r0 + p) * TW + q] * BSTRIDE;
-            float o[3][PY];
-#pragma unroll
-            for (int oc = 0; oc < 3; ++oc) {
-                float acc[PY];
-#pragma unroll
-                for (int p = 0; p < PY; ++p) acc[p] = 0.f;
-                int slot = oc * SL::PER_OC;
-                if constexpr (RC >= 0) {
-                    constexpr int NCR = PY / 2 + 2 * RC;
-#pragma unroll
-                    for (int cc = 0; cc < G::NCH; ++cc) {
-                        const int c = CROSS ? cc : oc;
-                        const float* ub = us + c * UH * UW + (r0 / 2) * UW + (q / 2) + RC;
-#pragma unroll
-                        for (int dx = -RC; dx <= RC; ++dx, ++slot) {
-                            float col[NCR];
-#pragma unroll
-                            for (int j = 0; j < NCR; ++j) col[j] = ub[j * UW + dx];
-#pragma unroll
-                            for (int p = 0; p < PY; ++p) {
-                                float h[8];
-                                v2::load_slot<TB>(hb[p] + slot * SB, h);
-#pragma unroll
-                                for (int dy = 0; dy < 2 * RC + 1; ++dy) acc[p] = fmaf(h[dy], col[p / 2 + dy], acc[p]);
-                            }
-                        }
-                    }
-                }
-#pragma unroll
-                for (int cc = 0; cc < G::NCH; ++cc) {
-                    const int c = CROSS ? cc : oc;
-                    const float* zb = zs + c * ZH * ZW + (r0 + HZ - RF) * ZW + q + HZ;
-#pragma unroll
-                    for (int dx = -RF; dx <= RF; ++dx, ++slot) {
-                        float col[PY + 2 * RF];
-#pragma unroll
-                        for (int j = 0; j < PY + 2 * RF; ++j) col[j] = zb[j * ZW + dx];
-#pragma unroll
-                        for (int p = 0; p < PY; ++p) {
-                            float h[8];
-                            v2::load_slot<TB>(hb[p] + slot * SB, h);
-#pragma unroll
-                            for (int dy = 0; dy < 2 * RF + 1; ++dy) acc[p] = fmaf(h[dy], col[p + dy], acc[p]);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int p = 0; p < PY; ++p) o[oc][p] = acc[p];
-            }
-            // stage s is no longer read: hand it back (only if the producer will reuse it)
-            if (i + 2 < T) bar_arrive(BAR_EMPTY0 + s, NT);
             TS* oi = out + (int64_t)img * 3 * H * W;
-            const int gx = x0 + q;
-#pragma unroll
-            for (int p = 0; p < PY; ++p) {
-                const int gy = y0 + r0 + p;
+#pragma unroll 1
+            for (int pass = 0; pass < TH / 8; ++pass) {
+                const int r = 2 * ((warp >> 1) + 4 * pass) + ro;          // tile row of this group
+                const uint2 kb = *reinterpret_cast<const uint2*>(bk + r * TW + c0);
+                float o[3];
+                filter_group<RF, RC, CROSS, TB>(zs + (r + HZ - RF) * ZW + c0 + HZ - RF, ZH * ZW, ZW,
+                                                 us + (r / 2) * UW + c0 / 2, UH * UW, UW, bank_s, kb, j, o);
+                if (pass == TH / 8 - 1 && i + 2 < T) bar_arrive(BAR_EMPTY0 + s, NT);   // stage s no longer read
+                const int gy = y0 + r, gx = x0 + c0 + j;
                 if (gy < H && gx < W) {
                     float R, Gc, B;
-                    work_to_rgb(o[0][p], o[1][p], o[2][p], color, R, Gc, B);
-                    int64_t po = (int64_t)gy * W + gx;
+                    work_to_rgb(o[0], o[1], o[2], color, R, Gc, B);
+                    const int64_t po = (int64_t)gy * W + gx;
                     st_f(oi, po, R);
                     st_f(oi, (int64_t)H * W + po, Gc);
                     st_f(oi, 2 * (int64_t)H * W + po, B);

@@ -115,13 +115,14 @@ __global__ void __launch_bounds__(SH::NT, 1) k_serve_level(const WorkList* __res
         __syncthreads();   // previous tile finished with the shared buffers
         if (it.bank != cur_bank) {
             // items are sorted by bank: a CTA's contiguous tile range rarely switches
-            v2::load_bank_slots<RF, RC, CROSS, __half>(tb->bank[it.bank], tb->K[it.bank], bank_s, threadIdx.x, SH::NT);
+            lvl::v3::load_bank_rows<RF, RC, CROSS, __half>(tb->bank[it.bank], tb->K[it.bank], bank_s, threadIdx.x,
+                                                           SH::NT);
             if (threadIdx.x == 0) sp = tb->sel[it.bank];
             cur_bank = it.bank;
             __syncthreads();
         }
         const int lt = t - it.tile_start;
-        v2::tile_v2<SH, RF, RC, CROSS, __half, __half>(smem, bank_s, it.z, it.coarse, it.out, nullptr, it.H, it.W,
+        v2::tile_v2<SH, RF, RC, CROSS, __half, __half, true>(smem, bank_s, it.z, it.coarse, it.out, nullptr, it.H, it.W,
                                                        it.Hc, it.Wc, (lt % it.tiles_x) * SH::TW,
                                                        (lt / it.tiles_x) * SH::TH, tb->K[it.bank],
                                                        tb->color[it.bank], sp, wv);
@@ -148,7 +149,8 @@ using S1 = v2::Shape<384, 4>;
 using S2 = v2::Shape<512, 2>;
 
 template <class SH> size_t level_smem(int Kmax) {
-    return v2::smem_need_s<SH, RF, RC, CROSS, __half>(Kmax);
+    return ((v2::tile_bytes<SH, RC>() + 15) & ~size_t(15)) +
+           (size_t)Kmax * lvl::v3::bucket_bytes_rows<RF, RC, CROSS, __half>();
 }
 
 template <class SH> int launch_level(const WorkList* wl, const Tables* tb, int Kmax, int stage, cudaStream_t s) {

@@ -444,3 +444,24 @@ def test_train_cascade_matches_oracle(mdn, case):
     out = mdn.denoise_multiscale(_tt(z, "f32")[None], banks, _geom(mdn, geom),
                                  [mdn.default_bparams(l) for l in range(len(banks))])
     assert np.mean((_np(out[0]) - u) ** 2) < 0.3 * np.mean((z - u) ** 2)
+
+
+# ------------------------------------------------------------ host-to-host pipeline
+
+@pytest.mark.parametrize("chunk", [1, 2, 5])
+def test_pipelined_host_path_equals_device_path(mdn, chunk):
+    """mdn_denoise_multiscale_pipelined (host buffers, chunks overlapped on
+    three streams) gives the device path's results exactly, for chunk sizes
+    that divide the batch, leave a ragged last chunk and exceed it."""
+    frames = np.stack([synth.noisy_pair(97, 130, 800 + i)[0] for i in range(4)])
+    geom = mdn.Geometry(3, 3)
+    bps = [mdn.default_bparams(0), mdn.default_bparams(1)]
+    banks = [torch.tensor(_bank(216, O.Geometry(3, 3), 60 + l, "f16"), dtype=torch.float16, device="cuda")
+             for l in range(2)]
+    x = torch.tensor(frames, dtype=torch.float16)
+    ref = mdn.denoise_multiscale(x.cuda(), banks, geom, bps).cpu()
+    host_in = x.pin_memory()
+    host_out = torch.full_like(host_in, float("nan")).pin_memory()
+    mdn.denoise_multiscale_pipelined(host_in, banks, geom, bps, host_out, chunk=chunk)
+    torch.cuda.current_stream().synchronize()
+    assert torch.equal(host_out, ref)
