@@ -82,9 +82,9 @@ def lib():
         L.orc_regressor_len.restype = C.c_int
         L.orc_regressor_len.argtypes = [C.c_int, C.c_int, C.c_int]
         L.orc_filter_level.argtypes = [dp, C.c_int, C.c_int, dp, C.c_int, C.c_int, i32p, dp, C.c_int,
-                                       C.c_int, C.c_int, C.c_int, C.c_int, dp]
+                                       C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, dp]
         L.orc_gram_accumulate.argtypes = [dp, C.c_int, C.c_int, dp, C.c_int, C.c_int, dp, i32p, C.c_int,
-                                          C.c_int, C.c_int, C.c_int, C.c_int, dp, i64p]
+                                          C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, dp, i64p]
         L.orc_cholesky_solve.restype = C.c_int
         L.orc_cholesky_solve.argtypes = [dp, C.c_int, dp, C.c_int]
         L.orc_set_threads.argtypes = [C.c_int]
@@ -108,11 +108,15 @@ def _p(a, t=C.c_double):
 @dataclass
 class Geometry:
     """Filter footprint: fine radius, coarse radius (-1 = single level),
-    cross-channel regressors, colour space (0 = YCbCr BT.601, 1 = RGB)."""
+    cross-channel regressors, colour space (0 = YCbCr BT.601, 1 = RGB), and
+    the coarse sampling: align = 0 takes the coarse patch at floor(i/2) (the
+    reading of the paper's i/2), align = 1 samples it bilinearly at i/2 (the
+    half-pixel-aligned variant of the multiscale equation of Section 4)."""
     r_fine: int = 3
     r_coarse: int = 3
     cross: int = 0
     color: int = 0
+    align: int = 0
 
     def D(self) -> int:
         return lib().orc_regressor_len(self.r_fine, self.r_coarse, self.cross)
@@ -285,7 +289,7 @@ def filter_level(z, uc, bucket, bank, geom: Geometry):
         Hc = Wc = 0
         ucp = None
     lib().orc_filter_level(_p(z), H, W, ucp, Hc, Wc, _p(bucket, C.c_int32), _p(bank), K,
-                           geom.r_fine, geom.r_coarse, geom.cross, geom.color, _p(out))
+                           geom.r_fine, geom.r_coarse, geom.cross, geom.color, geom.align, _p(out))
     return out
 
 
@@ -348,7 +352,7 @@ def gram_accumulate(z, uc, target, bucket, K: int, geom: Geometry, gram=None, co
         Hc = Wc = 0
         ucp = None
     lib().orc_gram_accumulate(_p(z), H, W, ucp, Hc, Wc, _p(target), _p(bucket, C.c_int32), K,
-                              geom.r_fine, geom.r_coarse, geom.cross, geom.color,
+                              geom.r_fine, geom.r_coarse, geom.cross, geom.color, geom.align,
                               _p(gram), _p(counts, C.c_int64))
     return gram, counts
 

@@ -22,7 +22,9 @@
  * central-difference gradients; 5x5 normalised Gaussian (sigma 1.5) spatial
  * weights on clamped product fields; orientation = minor-eigenvector angle in
  * [0, pi) with x to the right and y down; lower-inclusive thresholds;
- * coherence := 0 when sqrt(l1)+sqrt(l2) < coh_eps; coarse index floor(i/2);
+ * coherence := 0 when sqrt(l1)+sqrt(l2) < coh_eps; coarse index floor(i/2)
+ * (or, with `align`, the coarse patch sampled bilinearly at i/2: the
+ * half-pixel-aligned variant of the coarse term);
  * ridge (G/n + lambda I) h = b/n; empty buckets take the pooled filter.
  *
  * Precision modes.  Everything is FP64 unless `mirror32` is set, in which
@@ -374,23 +376,40 @@ void orc_from_work(const double* w, long HW, int color, double* out)
 /* Section 4)                                                          */
 /* ------------------------------------------------------------------ */
 
+/* Coarse sample of channel plane u (Hc x Wc) for fine pixel (y, x) and tap
+ * (dy, dx).  align = 0: u at (floor(y/2) + dy, floor(x/2) + dx) (reading of
+ * the paper's i/2).  align = 1: u sampled bilinearly at (y/2 + dy, x/2 + dx)
+ * -- coarse pixel (Y, X) sits at fine (2Y, 2X), so an odd fine coordinate
+ * falls half way between two coarse samples and takes their mean; each of the
+ * (up to four) samples is clamped to the plane on its own. */
+static double coarse_sample(const double* u, int Hc, int Wc, int y, int x, int dy, int dx, int align)
+{
+    int y0 = y / 2 + dy, x0 = x / 2 + dx;
+    int ny = (align && (y & 1)) ? 2 : 1, nx = (align && (x & 1)) ? 2 : 1;
+    double s = 0.0;
+    for (int a = 0; a < ny; ++a)
+        for (int b = 0; b < nx; ++b)
+            s += u[clampl(y0 + a, 0, Hc - 1) * Wc + clampl(x0 + b, 0, Wc - 1)];
+    return s / (double)(ny * nx);
+}
+
 /* Regressor for output channel oc at pixel (y, x): coarse taps first (when
  * rc >= 0), then fine taps.  Within each block: (channel, dy, dx) row-major,
  * the channel loop covering the output channel only (per-channel geometry) or
  * all three (cross-channel).  zw is the working-space (YCbCr or RGB) image of
- * level l, uw the working-space image of level l+1 of size Hc x Wc. */
+ * level l, uw the working-space image of level l+1 of size Hc x Wc; align
+ * selects the coarse sampling (coarse_sample). */
 static int regressor(const double* zw, int H, int W, const double* uw, int Hc, int Wc,
-                     int rf, int rc, int cross, int oc, int y, int x, double* r)
+                     int rf, int rc, int cross, int align, int oc, int y, int x, double* r)
 {
     int n = 0;
     long HW = (long)H * W, HWc = (long)Hc * Wc;
     int c0 = cross ? 0 : oc, c1 = cross ? 3 : oc + 1;
     if (rc >= 0) {
-        int yc = y / 2, xc = x / 2;
         for (int c = c0; c < c1; ++c)
             for (int dy = -rc; dy <= rc; ++dy)
                 for (int dx = -rc; dx <= rc; ++dx)
-                    r[n++] = uw[c * HWc + clampl(yc + dy, 0, Hc - 1) * Wc + clampl(xc + dx, 0, Wc - 1)];
+                    r[n++] = coarse_sample(uw + c * HWc, Hc, Wc, y, x, dy, dx, align);
     }
     for (int c = c0; c < c1; ++c)
         for (int dy = -rf; dy <= rf; ++dy)
@@ -414,7 +433,7 @@ int orc_regressor_len(int rf, int rc, int cross)
  * rc < 0; bank: [K][3][D] (D = orc_regressor_len). */
 void orc_filter_level(const double* z, int H, int W, const double* uc, int Hc, int Wc,
                       const int32_t* bucket, const double* bank, int K,
-                      int rf, int rc, int cross, int color, double* out)
+                      int rf, int rc, int cross, int color, int align, double* out)
 {
     long HW = (long)H * W;
     int D = orc_regressor_len(rf, rc, cross);
@@ -435,7 +454,7 @@ void orc_filter_level(const double* z, int H, int W, const double* uc, int Hc, i
                 int k = bucket[(long)y * W + x];
                 if (k >= K) k = K - 1;
                 for (int oc = 0; oc < 3; ++oc) {
-                    regressor(zw, H, W, uw, Hc, Wc, rf, rc, cross, oc, y, x, r);
+                    regressor(zw, H, W, uw, Hc, Wc, rf, rc, cross, align, oc, y, x, r);
                     const double* h = bank + ((long)k * 3 + oc) * D;
                     double s = 0.0;
                     for (int j = 0; j < D; ++j) s += h[j] * r[j];
@@ -461,7 +480,7 @@ void orc_filter_level(const double* z, int H, int W, const double* uc, int Hc, i
  * target: level-l clean RGB image. */
 void orc_gram_accumulate(const double* z, int H, int W, const double* uc, int Hc, int Wc,
                          const double* target, const int32_t* bucket, int K,
-                         int rf, int rc, int cross, int color, double* gram, int64_t* counts)
+                         int rf, int rc, int cross, int color, int align, double* gram, int64_t* counts)
 {
     long HW = (long)H * W;
     int D = orc_regressor_len(rf, rc, cross);
@@ -482,7 +501,7 @@ void orc_gram_accumulate(const double* z, int H, int W, const double* uc, int Hc
             if (k >= K) continue;
             counts[k] += 1;
             for (int g = 0; g < G; ++g) {
-                regressor(zw, H, W, uw, Hc, Wc, rf, rc, cross, g, y, x, a);
+                regressor(zw, H, W, uw, Hc, Wc, rf, rc, cross, align, g, y, x, a);
                 if (cross) for (int t = 0; t < 3; ++t) a[D + t] = tw[t * HW + (long)y * W + x];
                 else a[D] = tw[g * HW + (long)y * W + x];
                 double* Gm = gram + ((long)k * G + g) * Dp * Dp;

@@ -657,3 +657,108 @@ def test_pyramid_noise_factor_and_level_count():
         assert abs(ratio / mdn.pyramid_noise_factor(l) - 1) < 0.02, (l, ratio)
     assert [mdn.levels_for_sigma(s / 255) for s in (1, 5, 15, 25, 50)] == [1, 2, 3, 4, 5]
     assert mdn.levels_for_sigma(1 / 255, min_levels=2) == 2 and mdn.levels_for_sigma(1e6, max_levels=5) == 5
+
+
+# ------------------------------------------------------------ phase-aware coarse patch (next row f1)
+
+def test_aligned_coarse_patch_upsamples_a_ramp_exactly():
+    """The half-pixel-aligned coarse term (coarse patch sampled bilinearly at
+    i/2; coarse pixel (Y, X) sits at fine (2Y, 2X)) with a coarse delta bank
+    reproduces a linear ramp u(Y, X) = a + bX + cY at fine resolution,
+    a + b x/2 + c y/2, away from the clamped right and bottom edges; the
+    floor(i/2) coarse term gives the staircase a + b floor(x/2) + c floor(y/2)."""
+    Hc, Wc, H, W = 9, 11, 17, 21
+    Y, X = np.mgrid[0:Hc, 0:Wc].astype(np.float64)
+    coef = [(0.1, 0.02, 0.03), (0.5, -0.01, 0.04), (0.3, 0.05, -0.02)]
+    uc = np.stack([a + b * X + c * Y for a, b, c in coef])
+    z = np.zeros((3, H, W))
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    for align, yy, xx in [(1, y / 2, x / 2), (0, np.floor(y / 2), np.floor(x / 2))]:
+        geom = O.Geometry(1, 1, color=1, align=align)
+        bank = _delta_bank(216, geom, coarse_center=1.0, fine_center=0.0)
+        out = O.filter_level(z, uc, np.zeros((H, W), np.uint8), bank, geom)
+        ref = np.stack([a + b * xx + c * yy for a, b, c in coef])
+        np.testing.assert_allclose(out[:, :H - 1, :W - 1], ref[:, :H - 1, :W - 1], atol=1e-13)
+
+
+def test_aligned_coarse_patch_brute_force():
+    """Brute force of the aligned multiscale equation on a 9x8 image: coarse
+    patches from the mean of edge-padded shifted copies (two rows or columns
+    at odd fine coordinates), fine patches as before; and at even-even pixels
+    the aligned and floor(i/2) terms coincide."""
+    rng = np.random.default_rng(14)
+    geom = O.Geometry(3, 2, align=1)
+    z = rng.uniform(0, 1, (3, 9, 8))
+    uc = rng.uniform(0, 1, (3, 5, 4))
+    bk = rng.integers(0, 216, (9, 8)).astype(np.uint8)
+    bank = rng.standard_normal((216, 3, geom.D())) * 0.05
+    zw, Minv = _ycc(z)
+    uw, _ = _ycc(uc)
+    Pz = _patches_numpy(zw, 3)
+    # patches at integer coarse positions 0..Hc (0..Wc): the image gains one
+    # edge-replicated row and column, so that every sample is clamped on its own
+    Pu = _patches_numpy(np.pad(uw, ((0, 0), (0, 1), (0, 1)), mode="edge"), 2)
+    ow = np.zeros((3, 9, 8))
+    for yy in range(9):
+        for xx in range(8):
+            ys = [yy // 2, yy // 2 + 1] if yy % 2 else [yy // 2]
+            xs = [xx // 2, xx // 2 + 1] if xx % 2 else [xx // 2]
+            pu = np.mean([Pu[a, b] for a in ys for b in xs], axis=0)
+            h = bank[bk[yy, xx]]
+            for c in range(3):
+                ow[c, yy, xx] = h[c, :25] @ pu[c] + h[c, 25:] @ Pz[yy, xx, c]
+    ref = np.einsum("ij,jhw->ihw", Minv, ow)
+    out = O.filter_level(z, uc, bk, bank, geom)
+    np.testing.assert_allclose(out, ref, atol=1e-12)
+    floor = O.filter_level(z, uc, bk, bank, O.Geometry(3, 2, align=0))
+    np.testing.assert_array_equal(out[:, ::2, ::2], floor[:, ::2, ::2])
+    assert np.abs(out[:, 1::2, 1::2] - floor[:, 1::2, 1::2]).max() > 1e-3
+
+
+def test_aligned_planted_bank_recovered():
+    """Least squares with the aligned coarse regressor (lambda = 0) recovers a
+    planted bank exactly: the Gram sums and the filter use the same samples."""
+    rng = np.random.default_rng(16)
+    geom = O.Geometry(2, 2, align=1)
+    z, _ = synth.noisy_pair(128, 120, 35)
+    uc = O.pyramid_down(z)
+    bk, _, _ = O.select(z, O.default_bparams(0))
+    planted = rng.standard_normal((216, 3, geom.D())) * 0.05
+    target = O.filter_level(z, uc, bk, planted, geom)
+    gram, counts = O.gram_accumulate(z, uc, target, bk, 216, geom)
+    D = geom.D()
+    checked = 0
+    for k in range(216):
+        if counts[k] < 4 * D:
+            continue
+        for g in range(3):
+            A = gram[k, g, :D, :D]
+            if np.linalg.cond(A) > 1e8:
+                continue
+            h = O.cholesky_solve(A, gram[k, g, :D, D:])[:, 0]
+            assert np.linalg.norm(h - planted[k, g]) / np.linalg.norm(planted[k, g]) < 1e-8, (k, g)
+            checked += 1
+    assert checked >= 5
+
+
+def test_phase_study_aligned_vs_floor_coarse_term(capsys):
+    """Measurement behind the decision on the phase-aware coarse term (the
+    numbers are printed; run with -s): a 2-level 7x7 + 7x7 cascade trained by
+    the oracle on 4 synthetic 192x192 pairs at sigma 25/255 with the floor(i/2)
+    and the half-pixel-aligned coarse patch, PSNR on 2 held-out frames.  The
+    assertions are sanity only (both denoise by more than 6 dB)."""
+    pairs = [synth.noisy_pair(192, 192, 3000 + i) for i in range(4)]
+    tests = [synth.noisy_pair(192, 192, 3100 + i) for i in range(2)]
+    res = {}
+    for align in (0, 1):
+        geom = O.Geometry(3, 3, align=align)
+        banks, _ = O.train_cascade([p[0] for p in pairs], [p[1] for p in pairs], geom, 2)
+        ps = []
+        for z, u in tests:
+            out = O.denoise_multiscale(z, banks, geom).out
+            ps.append((10 * np.log10(1 / np.mean((z - u) ** 2)), 10 * np.log10(1 / np.mean((out - u) ** 2))))
+        res[align] = np.mean(ps, axis=0)
+    with capsys.disabled():
+        print(f"\nphase study: noisy {res[0][0]:.2f} dB, floor(i/2) {res[0][1]:.2f} dB, aligned {res[1][1]:.2f} dB "
+              f"(delta {res[1][1] - res[0][1]:+.3f} dB)")
+    assert res[0][1] > res[0][0] + 6 and res[1][1] > res[1][0] + 6
