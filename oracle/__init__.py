@@ -77,6 +77,7 @@ def lib():
         L.orc_structure_tensor.argtypes = [dp, C.c_int, C.c_int, C.c_int, dp]
         L.orc_features.argtypes = [dp, C.c_int, C.c_int, C.c_int, C.c_float, dp]
         L.orc_buckets.argtypes = [dp, C.c_int, C.c_int, C.POINTER(_BParams), C.c_double, i32p, u8p]
+        L.orc_buckets_fp32.argtypes = [dp, C.c_int, C.c_int, C.POINTER(_BParams), i32p]
         L.orc_to_work.argtypes = [dp, C.c_long, C.c_int, dp]
         L.orc_from_work.argtypes = [dp, C.c_long, C.c_int, dp]
         L.orc_regressor_len.restype = C.c_int
@@ -250,11 +251,28 @@ def buckets(feat, bp: BucketParams, band_eps: float = 1e-5):
     return b.astype(bucket_dtype(bp.K)), band.astype(bool)
 
 
+def buckets_fp32(T, bp: BucketParams):
+    """Bucket map decided in FP32 on the tensor by the squared-domain
+    comparisons of orc_buckets_fp32 (equivalent to thresholding the features
+    in exact arithmetic)."""
+    T = _d(T)
+    _, H, W = T.shape
+    b = np.empty((H, W), dtype=np.int32)
+    cb = bp.c()
+    lib().orc_buckets_fp32(_p(T), H, W, C.byref(cb), _p(b, C.c_int32))
+    return b.astype(bucket_dtype(bp.K))
+
+
 def select(z, bp: BucketParams, mirror32: bool = False, band_eps: float = 1e-5):
     """s(i) for one level: (bucket map [H][W], u8 up to 256 buckets else u16,
-    band mask, features)."""
-    f = features(structure_tensor(z, mirror32), bp.coh_eps, mirror32)
+    band mask, features).  mirror32: the tensor in the documented FP32 order
+    and the FP32 bucket decisions of buckets_fp32 (the band mask and the
+    returned features stay those of the FP32-order tensor's features)."""
+    T = structure_tensor(z, mirror32)
+    f = features(T, bp.coh_eps, mirror32)
     b, band = buckets(f, bp, band_eps)
+    if mirror32:
+        b = buckets_fp32(T, bp)
     return b, band, f
 
 

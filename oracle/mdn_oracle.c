@@ -333,6 +333,61 @@ void orc_buckets(const double* feat, int H, int W, const orc_bparams* bp, double
     }
 }
 
+/* FP32 bucket decisions (the `mirror32` reading used to pin the GPU's bucket
+ * maps bit for bit).  The strength and coherence bins are decided on the
+ * FP32 tensor (a, b, c) without square roots or divisions, by comparisons
+ * that are equivalent in exact arithmetic to thresholding the features:
+ *   ht = (a + c) / 2, hd = (a - c) / 2, d2 = hd^2 + b^2 (= disc^2), so
+ *   lambda1 = ht + disc and lambda2 = ht - disc;
+ *   sqrt(lambda1) >= T  <=>  disc >= T^2 - ht
+ *                       <=>  u <= 0  or  d2 >= u^2,   u = T^2 - ht;
+ *   coherence >= C (0 <= C < 1)  <=>  disc >= ht * 2C / (1 + C^2)
+ *                       <=>  d2 >= (ht R)^2,          R = 2C / (1 + C^2)
+ *   (C = 1: R = 1; C > 1 never passes);
+ *   coherence := 0 (bin 0) when lambda1 < eps^2 <=> v > 0 and d2 < v^2, v = eps^2 - ht.
+ * Every quantity is an FP32 operation in this order (T^2, R and eps^2 are
+ * computed in FP64 from the FP32 thresholds and rounded to FP32), so a
+ * decision differs from thresholding the exact features only for features
+ * within a few ulps of a threshold.  The angle bin is floor(n_angle theta/pi)
+ * with theta from atan2 in FP64 on the FP32 pair (a - c, 2b). */
+void orc_buckets_fp32(const double* T, int H, int W, const orc_bparams* bp, int32_t* bucket)
+{
+    long HW = (long)H * W;
+    int ns = bp->n_strength - 1, nc = bp->n_coherence - 1;
+    float q[16], r[16];
+    for (int t = 0; t < ns; ++t) q[t] = (float)((double)bp->strength_thr[t] * (double)bp->strength_thr[t]);
+    for (int t = 0; t < nc; ++t) {
+        double C = (double)bp->coherence_thr[t];
+        r[t] = C < 1.0 ? (float)(2.0 * C / (1.0 + C * C)) : (C == 1.0 ? 1.0f : INFINITY);
+    }
+    const float e2 = (float)((double)bp->coh_eps * (double)bp->coh_eps);
+    for (long i = 0; i < HW; ++i) {
+        float af = (float)T[i], bf = (float)T[HW + i], cf = (float)T[2 * HW + i];
+        float ht = (af + cf) * 0.5f, hd = (af - cf) * 0.5f;
+        float d2 = fmaf(hd, hd, bf * bf);
+        int s = 0, c = 0;
+        for (int t = 0; t < ns; ++t) {
+            float u = q[t] - ht;
+            if (u <= 0.0f || d2 >= u * u) ++s;
+        }
+        float v = e2 - ht;
+        int zero = v > 0.0f && d2 < v * v;
+        if (!zero)
+            for (int t = 0; t < nc; ++t) {
+                float w = ht * r[t];
+                if (d2 >= w * w) ++c;
+            }
+        float X = af - cf, Y = bf + bf;
+        double th = 0.5 * atan2((double)Y, (double)X) + M_PI / 2.0;
+        if (th >= M_PI) th -= M_PI;
+        if (th < 0) th += M_PI;
+        int a = (int)floor(th / M_PI * bp->n_angle);
+        if (a >= bp->n_angle) a = bp->n_angle - 1;
+        if (a < 0) a = 0;
+        bucket[i] = (a * bp->n_strength + s) * bp->n_coherence + c;
+    }
+}
+
 /* ------------------------------------------------------------------ */
 /* Colour transform (Section 3 footnote 1): zero-offset ITU-R BT.601   */
 /* ------------------------------------------------------------------ */

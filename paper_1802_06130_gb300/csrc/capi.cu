@@ -66,6 +66,12 @@ int make_sel_params(const mdn_bucket_params* bp, SelParams* sp) {
     for (int i = 0; i < sp->nthr_s; ++i) sp->strength_thr[i] = bp->strength_thr[i];
     for (int i = 0; i < sp->nthr_c; ++i) sp->coherence_thr[i] = bp->coherence_thr[i];
     sp->coh_eps = bp->coh_eps;
+    for (int i = 0; i < sp->nthr_s; ++i) sp->strength_q[i] = (float)((double)bp->strength_thr[i] * bp->strength_thr[i]);
+    for (int i = 0; i < sp->nthr_c; ++i) {
+        const double C = (double)bp->coherence_thr[i];
+        sp->coherence_r[i] = C < 1.0 ? (float)(2.0 * C / (1.0 + C * C)) : (C == 1.0 ? 1.0f : INFINITY);
+    }
+    sp->eps2 = (float)((double)bp->coh_eps * bp->coh_eps);
     const double PI = 3.14159265358979323846;
     for (int k = 1; k < bp->n_angle / 2; ++k) {
         double a = 2.0 * PI * k / bp->n_angle;

@@ -37,6 +37,12 @@ struct SelParams {
     // (cos, sin) of 2 pi k / n_angle for k = 1 .. n_angle/2 - 1
     float bcos[32];
     float bsin[32];
+    // squared-domain forms of the thresholds (FP32 roundings of FP64 values):
+    // strength_q = T^2, coherence_r = 2C / (1 + C^2) (1 for C = 1, +inf above),
+    // eps2 = coh_eps^2
+    float strength_q[MDN_MAX_THR];
+    float coherence_r[MDN_MAX_THR];
+    float eps2;
 };
 int make_sel_params(const mdn_bucket_params* bp, SelParams* out);
 

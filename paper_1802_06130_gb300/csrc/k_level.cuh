@@ -16,7 +16,9 @@
 //   H = w0*P[x-2], fma(w1,P[x-1]) ... fma(w4,P[x+2]);  T = same over rows;
 //   ht = (a+c)*0.5, hd = (a-c)*0.5, disc = sqrt(fma(hd,hd,b*b)),
 //   l1 = ht+disc, l2 = max(ht-disc, 0), s1 = sqrt(l1), s2 = sqrt(l2),
-//   coherence = (s1-s2)/(s1+s2) or 0 if s1+s2 < coh_eps, strength = s1.
+//   coherence = (s1-s2)/(s1+s2) or 0 if s1+s2 < coh_eps, strength = s1
+//   (IEEE round-to-nearest square roots and division throughout, so that the
+//   FP32 reference evaluated in the same order gives the same buckets).
 // Orientation bin: the doubled angle psi = 2 theta of the minor eigenvector
 // is the angle of v = (c-a, -2b); psi is placed in one of n_angle sectors of
 // width 2 pi / n_angle by sign tests against the sector boundary vectors (no
@@ -82,42 +84,81 @@ __device__ __forceinline__ void work_to_rgb(float y, float cb, float cr, int col
     b = y + 1.772f * cb;
 }
 
-// Orientation/strength/coherence -> bucket index, arithmetic as documented
-// in the file header.
-__device__ __forceinline__ int bucket_of(float a, float b, float c, const SelParams& sp) {
-    float ht = __fmul_rn(__fadd_rn(a, c), 0.5f);
-    float hd = __fmul_rn(__fsub_rn(a, c), 0.5f);
-    float disc = __fsqrt_rn(__fmaf_rn(hd, hd, __fmul_rn(b, b)));
-    float l1 = __fadd_rn(ht, disc);
-    float l2 = __fsub_rn(ht, disc);
-    l2 = l2 < 0.f ? 0.f : l2;
-    float s1 = __fsqrt_rn(l1), s2 = __fsqrt_rn(l2);
-    float den = __fadd_rn(s1, s2);
-    float coh = den < sp.coh_eps ? 0.f : __fdiv_rn(__fsub_rn(s1, s2), den);
-    // orientation sector of v = (c - a, -(b + b))
-    float vx = __fsub_rn(c, a), vy = -__fadd_rn(b, b);
-    int abin;
+// Orientation/strength/coherence -> bucket index for N pixels at once (the
+// N computations are independent and free of branches and divisions, so
+// they overlap).  Strength and coherence bins are decided in the squared
+// domain, equivalent in exact arithmetic to thresholding the features:
+//   ht = (a+c)/2, hd = (a-c)/2, d2 = hd^2 + b^2 = disc^2
+//   (lambda1 = ht + disc, lambda2 = ht - disc);
+//   sqrt(lambda1) >= T      <=>  u <= 0 or d2 >= u^2, u = T^2 - ht;
+//   coherence >= C (C < 1)  <=>  d2 >= (ht R)^2, R = 2C / (1 + C^2);
+//   coherence := 0 when lambda1 < eps^2 <=> v > 0 and d2 < v^2, v = eps^2 - ht
+// (T^2, R, eps^2: FP32 roundings of FP64 values, made on the host).  Each
+// step is the FP32 operation shown, so a decision differs from thresholding
+// the exact features only for features within a few ulps of a threshold.
+// Orientation: the doubled angle of the minor eigenvector is the angle of
+// v = (c - a, -2b); it is placed in one of n_angle sectors by counting the
+// sector boundaries b_k (k < n_angle/2 - 1) with cross(b_k, v) >= 0, after
+// folding v into the upper half plane; v = 0 gives theta = pi/2.
+template <int N>
+__device__ __forceinline__ void buckets_of(const float (&a)[N], const float (&b)[N], const float (&c)[N],
+                                           const SelParams& sp, int (&k)[N]) {
+    float ht[N], d2[N], vx[N], vy[N];
+    int ab[N], sb[N], cb[N];
+    bool zero[N];
     const int half = sp.n_angle >> 1;
-    if (vx == 0.f && vy == 0.f) {
-        abin = half;                            // theta = pi/2
-    } else {
-        bool upper = (vy > 0.f) || (vy == 0.f && vx > 0.f);
-        if (!upper) { vx = -vx; vy = -vy; }
-        // number of boundaries k+1 (k < half-1) with cross(b_k, v) >= 0, i.e.
-        // psi >= boundary; the test is monotone in k (boundaries are 2 pi /
-        // n_angle apart), so a binary search finds the first failing k
-        int lo = 0, hi = half - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            const float cr = __fmaf_rn(sp.bcos[mid], vy, -__fmul_rn(sp.bsin[mid], vx));
-            if (cr >= 0.f) lo = mid + 1; else hi = mid;
-        }
-        abin = (upper ? 0 : half) + lo;
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+        ht[n] = __fmul_rn(__fadd_rn(a[n], c[n]), 0.5f);
+        const float hd = __fmul_rn(__fsub_rn(a[n], c[n]), 0.5f);
+        d2[n] = __fmaf_rn(hd, hd, __fmul_rn(b[n], b[n]));
+        float x = __fsub_rn(c[n], a[n]), y = -__fadd_rn(b[n], b[n]);
+        const bool upper = (y > 0.f) || (y == 0.f && x > 0.f);
+        const bool vz = (x == 0.f && y == 0.f);
+        vx[n] = upper ? x : -x;
+        vy[n] = upper ? y : -y;
+        ab[n] = vz ? half : (upper ? 0 : half);
+        zero[n] = vz;
+        sb[n] = 0;
+        cb[n] = 0;
     }
-    int sb = 0, cb = 0;
-    for (int t = 0; t < sp.nthr_s; ++t) sb += (sp.strength_thr[t] <= s1) ? 1 : 0;
-    for (int t = 0; t < sp.nthr_c; ++t) cb += (sp.coherence_thr[t] <= coh) ? 1 : 0;
-    return (abin * sp.n_strength + sb) * sp.n_coherence + cb;
+    for (int t = 0; t < half - 1; ++t) {
+        const float bc = sp.bcos[t], bs = sp.bsin[t];
+#pragma unroll
+        for (int n = 0; n < N; ++n) {
+            const float cr = __fmaf_rn(bc, vy[n], -__fmul_rn(bs, vx[n]));
+            ab[n] += (!zero[n] && cr >= 0.f) ? 1 : 0;
+        }
+    }
+    for (int t = 0; t < sp.nthr_s; ++t) {
+        const float q = sp.strength_q[t];
+#pragma unroll
+        for (int n = 0; n < N; ++n) {
+            const float u = __fsub_rn(q, ht[n]);
+            sb[n] += (u <= 0.f || d2[n] >= __fmul_rn(u, u)) ? 1 : 0;
+        }
+    }
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+        const float v = __fsub_rn(sp.eps2, ht[n]);
+        zero[n] = v > 0.f && d2[n] < __fmul_rn(v, v);
+    }
+    for (int t = 0; t < sp.nthr_c; ++t) {
+        const float r = sp.coherence_r[t];
+#pragma unroll
+        for (int n = 0; n < N; ++n) {
+            const float w = __fmul_rn(ht[n], r);
+            cb[n] += (!zero[n] && d2[n] >= __fmul_rn(w, w)) ? 1 : 0;
+        }
+    }
+#pragma unroll
+    for (int n = 0; n < N; ++n) k[n] = (ab[n] * sp.n_strength + sb[n]) * sp.n_coherence + cb[n];
+}
+__device__ __forceinline__ int bucket_of(float a, float b, float c, const SelParams& sp) {
+    const float A[1] = {a}, B[1] = {b}, Cc[1] = {c};
+    int k[1];
+    buckets_of<1>(A, B, Cc, sp, k);
+    return k[0];
 }
 
 // One output channel of the level filter for the pixel whose fine-patch
@@ -344,18 +385,12 @@ int run(const LevelArgs& a, cudaStream_t s) {
     auto kern = k_level<RF, RC, CROSS, TS, TB, SMEM, FILTER>;
     size_t bytes = ((tile_bytes<RC>() + 15) & ~size_t(15));
     if (FILTER && SMEM) bytes += sizeof(TB) * (size_t)a.K * 3 * BL::DP;
-    static int configured_dev = -1;
-    static int occ = 1;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (configured_dev != dev) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
-        if (e != cudaSuccess) return cuda_fail(e, "k_level: set smem attribute");
-        configured_dev = dev;
-    }
+    int occ = 1;
     {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "k_level: set smem attribute");
         int o = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, NT, bytes);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, NT, bytes);
         if (e != cudaSuccess) return cuda_fail(e, "k_level: occupancy");
         if (o < 1) return fail(MDN_ESHAPE, "k_level: shared memory footprint too large");
         occ = o;
@@ -379,7 +414,9 @@ template <int RF, int RC, bool CROSS, typename TB> size_t smem_need(int K) {
     return ((tile_bytes<RC>() + 15) & ~size_t(15)) + sizeof(TB) * (size_t)K * 3 * BL::DP;
 }
 
-constexpr size_t SMEM_LIMIT = 232448;
+// dynamic shared memory a kernel may use: the 227 KB opt-in maximum less
+// what the kernels declare statically (sector boundary tables)
+constexpr size_t SMEM_LIMIT = 232448 - 512;
 
 // ==========================================================================
 // Strip variant (v2): same selector stage; the filter stage gives every
@@ -1113,23 +1150,46 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
             }
             if (i + 1 < T) fetch(tile + gridDim.x);
             bar_sync(BAR_PROD, NP);
-            // products of central-difference gradients, one row per warp pass,
-            // lanes along x (two passes for the 36 columns)
-            for (int r = pw; r < PH; r += NPW) {
+            // products of central-difference gradients at the PH x PW positions,
+            // spread flat over the producer threads (consecutive lanes along x).
+            // Interior tiles: a thread takes the two positions (2m, q), (2m+1, q),
+            // whose gradients share four of their twelve staged values
+            auto prod = [&](const float (&gx)[3], const float (&gy)[3], int e) {
+                float pxx = __fmul_rn(gx[0], gx[0]), pxy = __fmul_rn(gx[0], gy[0]), pyy = __fmul_rn(gy[0], gy[0]);
 #pragma unroll
-                for (int qq = 0; qq < 2; ++qq) {
-                    const int q = lane + 32 * qq;
-                    if (q >= PW) continue;
-                    int ly, lx, lxm, lxp, lym, lyp;
-                    if (inner) {
-                        ly = r + 1; lx = q + 1;
-                        lxm = lx - 1; lxp = lx + 1; lym = ly - 1; lyp = ly + 1;
-                    } else {
-                        const int cy = clampi(y0 - 2 + r, 0, H - 1), cx = clampi(x0 - 2 + q, 0, W - 1);
-                        ly = cy - (y0 - HZ); lx = cx - (x0 - HZ);
-                        lxm = clampi(cx - 1, 0, W - 1) - (x0 - HZ); lxp = clampi(cx + 1, 0, W - 1) - (x0 - HZ);
-                        lym = clampi(cy - 1, 0, H - 1) - (y0 - HZ); lyp = clampi(cy + 1, 0, H - 1) - (y0 - HZ);
+                for (int c = 1; c < 3; ++c) {
+                    pxx = __fmaf_rn(gx[c], gx[c], pxx);
+                    pxy = __fmaf_rn(gx[c], gy[c], pxy);
+                    pyy = __fmaf_rn(gy[c], gy[c], pyy);
+                }
+                ps[e] = pxx; ps[PH * PW + e] = pxy; ps[2 * PH * PW + e] = pyy;
+            };
+            if (inner) {
+                static_assert(PH % 2 == 0, "row pairs");
+                for (int e0 = pt; e0 < (PH / 2) * PW; e0 += NP) {
+                    const int m = e0 / PW, q = e0 - m * PW;
+                    const int ly = 2 * m + 1, lx = q + 1;   // staged position of product (2m, q)
+                    float gx0[3], gy0[3], gx1[3], gy1[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const float* zc = zs + c * ZH * ZW + ly * ZW + lx;
+                        const float um = zc[-ZW], c0v = zc[0], c1v = zc[ZW], dn = zc[2 * ZW];
+                        gx0[c] = __fmul_rn(__fsub_rn(zc[1], zc[-1]), 0.5f);
+                        gy0[c] = __fmul_rn(__fsub_rn(c1v, um), 0.5f);
+                        gx1[c] = __fmul_rn(__fsub_rn(zc[ZW + 1], zc[ZW - 1]), 0.5f);
+                        gy1[c] = __fmul_rn(__fsub_rn(dn, c0v), 0.5f);
                     }
+                    prod(gx0, gy0, 2 * m * PW + q);
+                    prod(gx1, gy1, (2 * m + 1) * PW + q);
+                }
+            }
+            for (int e0 = pt; !inner && e0 < PH * PW; e0 += NP) {   // border tiles: clamped positions
+                {
+                    const int r = e0 / PW, q = e0 - r * PW;
+                    const int cy = clampi(y0 - 2 + r, 0, H - 1), cx = clampi(x0 - 2 + q, 0, W - 1);
+                    const int ly = cy - (y0 - HZ), lx = cx - (x0 - HZ);
+                    const int lxm = clampi(cx - 1, 0, W - 1) - (x0 - HZ), lxp = clampi(cx + 1, 0, W - 1) - (x0 - HZ);
+                    const int lym = clampi(cy - 1, 0, H - 1) - (y0 - HZ), lyp = clampi(cy + 1, 0, H - 1) - (y0 - HZ);
                     float gx[3], gy[3];
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
@@ -1137,52 +1197,71 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
                         gx[c] = __fmul_rn(__fsub_rn(zc[ly * ZW + lxp], zc[ly * ZW + lxm]), 0.5f);
                         gy[c] = __fmul_rn(__fsub_rn(zc[lyp * ZW + lx], zc[lym * ZW + lx]), 0.5f);
                     }
-                    float pxx = __fmul_rn(gx[0], gx[0]), pxy = __fmul_rn(gx[0], gy[0]), pyy = __fmul_rn(gy[0], gy[0]);
-#pragma unroll
-                    for (int c = 1; c < 3; ++c) {
-                        pxx = __fmaf_rn(gx[c], gx[c], pxx);
-                        pxy = __fmaf_rn(gx[c], gy[c], pxy);
-                        pyy = __fmaf_rn(gy[c], gy[c], pyy);
-                    }
-                    const int e = r * PW + q;
-                    ps[e] = pxx; ps[PH * PW + e] = pxy; ps[2 * PH * PW + e] = pyy;
+                    prod(gx, gy, e0);
                 }
             }
             bar_sync(BAR_PROD, NP);
-            // horizontal smoothing pass: one (field, row) per warp pass, lanes along x
-            for (int fr = pw; fr < 3 * PH; fr += NPW) {
-                const float* p = ps + fr * PW + lane;
-                float acc = __fmul_rn(wv[0], p[0]);
+            // horizontal smoothing pass: each thread makes 4 consecutive outputs
+            // of one (field, row) from two 16-byte loads of its 8 inputs
+            static_assert(PW % 4 == 0 && TW % 4 == 0, "16-byte rows");
+            for (int e = pt; e < 3 * PH * (TW / 4); e += NP) {
+                const int fr = e / (TW / 4), q = 4 * (e - fr * (TW / 4));
+                const float4 a4 = *reinterpret_cast<const float4*>(ps + fr * PW + q);
+                const float4 b4 = *reinterpret_cast<const float4*>(ps + fr * PW + q + 4);
+                const float p8[8] = {a4.x, a4.y, a4.z, a4.w, b4.x, b4.y, b4.z, b4.w};
+                float o4[4];
 #pragma unroll
-                for (int u = 1; u < 5; ++u) acc = __fmaf_rn(wv[u], p[u], acc);
-                hs[fr * TW + lane] = acc;
-            }
-            // RGB tile -> working colour space
-            for (int r = pw; r < ZH; r += NPW) {
+                for (int t = 0; t < 4; ++t) {
+                    float acc = __fmul_rn(wv[0], p8[t]);
 #pragma unroll
-                for (int qq = 0; qq < 2; ++qq) {
-                    const int q = lane + 32 * qq;
-                    if (q >= ZW) continue;
-                    const int e = r * ZW + q;
-                    float a, b, c;
-                    rgb_to_work(zs[e], zs[ZH * ZW + e], zs[2 * ZH * ZW + e], color, a, b, c);
-                    zs[e] = a; zs[ZH * ZW + e] = b; zs[2 * ZH * ZW + e] = c;
+                    for (int u = 1; u < 5; ++u) acc = __fmaf_rn(wv[u], p8[t + u], acc);
+                    o4[t] = acc;
                 }
+                *reinterpret_cast<float4*>(hs + fr * TW + q) = make_float4(o4[0], o4[1], o4[2], o4[3]);
+            }
+            // RGB tile -> working colour space, flat over the producer threads
+            // (the unused pad column is converted too)
+            for (int e = pt; e < ZH * ZW; e += NP) {
+                float a, b, c;
+                rgb_to_work(zs[e], zs[ZH * ZW + e], zs[2 * ZH * ZW + e], color, a, b, c);
+                zs[e] = a; zs[ZH * ZW + e] = b; zs[2 * ZH * ZW + e] = c;
             }
             bar_sync(BAR_PROD, NP);
-            // vertical pass, features, bucket: one row per warp pass, lanes along x
-            for (int r = pw; r < TH; r += NPW) {
+            // vertical pass, features, bucket: producer warp pw takes the 4
+            // consecutive rows 4 pw .. 4 pw + 3, lanes along x, with the five
+            // smoothing rows of each field held in a sliding register window
+            // (same products and sums, in the same order, as five loads)
+            static_assert(TH == 4 * NPW, "4 output rows per producer warp");
+            float win[3][4];
+#pragma unroll
+            for (int f = 0; f < 3; ++f)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) win[f][v] = hs[f * PH * TW + (4 * pw + v) * TW + lane];
+            float ta[4], tb[4], tc[4];
+#pragma unroll
+            for (int rr = 0; rr < 4; ++rr) {
+                const int r = 4 * pw + rr;
                 float t3[3];
 #pragma unroll
                 for (int f = 0; f < 3; ++f) {
-                    const float* p = hs + f * PH * TW + r * TW + lane;
-                    float acc = __fmul_rn(wv[0], p[0]);
+                    const float nxt = hs[f * PH * TW + (r + 4) * TW + lane];
+                    float acc = __fmul_rn(wv[0], win[f][0]);
 #pragma unroll
-                    for (int v = 1; v < 5; ++v) acc = __fmaf_rn(wv[v], p[v * TW], acc);
+                    for (int v = 1; v < 4; ++v) acc = __fmaf_rn(wv[v], win[f][v], acc);
+                    acc = __fmaf_rn(wv[4], nxt, acc);
                     t3[f] = acc;
+#pragma unroll
+                    for (int v = 0; v < 3; ++v) win[f][v] = win[f][v + 1];
+                    win[f][3] = nxt;
                 }
-                int k = bucket_of(t3[0], t3[1], t3[2], sp);
-                k = k < K ? k : K - 1;
+                ta[rr] = t3[0]; tb[rr] = t3[1]; tc[rr] = t3[2];
+            }
+            int kk[4];
+            buckets_of<4>(ta, tb, tc, sp, kk);   // the four rows' selectors overlap
+#pragma unroll
+            for (int rr = 0; rr < 4; ++rr) {
+                const int r = 4 * pw + rr;
+                const int k = kk[rr] < K ? kk[rr] : K - 1;
                 bk[r * TW + lane] = (uint8_t)k;
                 const int gy = y0 + r, gx = x0 + lane;
                 if (bmap && gy < H && gx < W) bmap[((int64_t)img * H + gy) * W + gx] = (uint8_t)k;

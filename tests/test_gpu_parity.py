@@ -323,7 +323,7 @@ def test_train_cascade_augment_multiscale_matches_oracle(mdn):
     ut = [O.dihedral(u, t) for u in us for t in range(8)]
     ref_banks, ref_counts = O.train_cascade(zt, ut, geom, 3, mirror32=True, storage="f32")
     Z, U = _tt(np.stack(zs), "f32"), _tt(np.stack(us), "f32")
-    banks, counts = mdn.train_cascade(Z, U, _geom(mdn, geom), 3, augment=True, chunk=3)
+    banks, counts = mdn.train_cascade(Z, U, _geom(mdn, geom), 3, augment=True, chunk=3, gram_precision=mdn.GRAM_FP32)
     torch.cuda.synchronize()
     for l in range(len(ref_banks)):
         c = counts[l].cpu().numpy()
@@ -395,7 +395,7 @@ def test_augment_dihedral_matches_oracle(mdn, geom):
     ga = _np(ga)
     assert np.linalg.norm(ga - g_ref) / np.linalg.norm(g_ref) < GRAM_TOL[0]
     # the cascade's augment option solves the same augmented system
-    banks, counts = mdn.train_cascade(Z, U, gm, 1, [bp], augment=True)
+    banks, counts = mdn.train_cascade(Z, U, gm, 1, [bp], augment=True, gram_precision=mdn.GRAM_FP32)
     assert np.array_equal(counts[0].cpu().numpy(), c_ref)
     ref_bank = O.solve_bank(g_ref, c_ref, geom, 1e-3)
     e = np.linalg.norm(_np(banks[0]) - ref_bank) / np.linalg.norm(ref_bank)
@@ -418,20 +418,22 @@ def test_solve_bank_matches_oracle(mdn):
 
 # ------------------------------------------------------------ A7 cascade
 
+@pytest.mark.parametrize("prec", ["fp32", "split_bf16"])
 @pytest.mark.parametrize("case", [("single", O.Geometry(2, -1), 1), ("three", O.Geometry(3, 3), 3)],
                          ids=lambda c: c[0])
-def test_train_cascade_matches_oracle(mdn, case):
+def test_train_cascade_matches_oracle(mdn, case, prec):
     """Section 4 cascade on the GPU (pyramids, per-level least squares, the
     trained level's output feeding the next finer level) vs the oracle's
-    cascade on the same pairs; FP32 storage, FP32 Gram.  Then the GPU banks
-    denoise a held-out image."""
+    cascade on the same pairs; FP32 storage, FP32 Gram and the default
+    split-BF16 Gram.  Then the GPU banks denoise a held-out image."""
     _, geom, levels = case
+    gp = {"fp32": mdn.GRAM_FP32, "split_bf16": mdn.GRAM_SPLIT_BF16}[prec]
     pairs = [synth.noisy_pair(128, 128, 1000 + i) for i in range(3)]
     zs = [O.round_storage(p[0], "f32") for p in pairs]
     us = [O.round_storage(p[1], "f32") for p in pairs]
     ref_banks, ref_counts = O.train_cascade(zs, us, geom, levels, mirror32=True, storage="f32")
     Z, U = _tt(np.stack(zs), "f32"), _tt(np.stack(us), "f32")
-    banks, counts = mdn.train_cascade(Z, U, _geom(mdn, geom), levels, chunk=2)
+    banks, counts = mdn.train_cascade(Z, U, _geom(mdn, geom), levels, chunk=2, gram_precision=gp)
     torch.cuda.synchronize()
     for l in range(len(ref_banks)):
         c = counts[l].cpu().numpy()

@@ -184,6 +184,38 @@ def test_coherence_range_and_fp32_path_agrees_outside_band():
     assert mism.sum() == 0
 
 
+def test_fp32_squared_domain_decisions_equal_feature_thresholds():
+    """The FP32 bucket decisions (no square roots or divisions: strength and
+    coherence thresholds compared in the squared domain on disc^2, lambda1 <
+    eps^2 for the zero tensor) equal thresholding the exact FP64 features at
+    every tensor whose features are not within 1e-6 of a threshold: random
+    PSD tensors spread over the strength and coherence ranges of the
+    thresholds (including 24 x 3 x 3, 16 x 5 x 3 and 16 x 16 x 16 grids), the
+    zero tensor, isotropic tensors and pure edges."""
+    rng = np.random.default_rng(21)
+    n = 200000
+    ang = rng.uniform(0, np.pi, n)
+    l1 = (rng.uniform(0, 0.35, n) * rng.choice([0.125, 0.25, 0.5, 1], n)) ** 2
+    l2 = l1 * rng.uniform(0, 1, n) ** rng.choice([1, 3, 8], n)
+    ca, sa = np.cos(ang), np.sin(ang)
+    a = l1 * ca ** 2 + l2 * sa ** 2
+    b = (l1 - l2) * ca * sa
+    c = l1 * sa ** 2 + l2 * ca ** 2
+    T = np.stack([a, b, c]).astype(np.float32).astype(np.float64)
+    T[:, :5] = 0.0                                   # zero tensors
+    T[:, 5:10] = np.array([[0.01], [0.0], [0.01]])   # isotropic
+    T[:, 10:15] = np.array([[0.02], [0.0], [0.0]])   # pure edges
+    T = T.reshape(3, 1, n)
+    for bp in [O.default_bparams(0), O.default_bparams(2), O.BucketParams(16, (0.02, 0.05, 0.1, 0.2), (0.2, 0.5)),
+               O.paper_grid_bparams(0)]:
+        ref, band = O.buckets(O.features(T, bp.coh_eps), bp, band_eps=1e-6)
+        got = O.buckets_fp32(T, bp)
+        # the angle bin is atan2 on the FP32 pair in both; compare outside the band
+        mism = (got != ref) & ~band
+        assert mism.sum() == 0, (bp.K, int(mism.sum()))
+        assert len(np.unique(ref)) > min(bp.K, 200) // 2
+
+
 # ------------------------------------------------------------ colour transform
 
 def test_ycbcr_golden_and_roundtrip():
