@@ -180,27 +180,32 @@ int mdn_denoise_multiscale(const void* noisy, int32_t dtype, int64_t n, int64_t 
 /* mdn_denoise_multiscale for a batch held in HOST memory, with copies and
  * kernels overlapped (a deployment layer: the paper describes per-image
  * inference only).  The batch is cut into chunks of `chunk` images; chunk c
- * is copied host_noisy -> dev_in on streams[0] (upload), denoised dev_in ->
- * dev_out on streams[1] (compute) with the same kernels and results as
- * mdn_denoise_multiscale, and copied dev_out -> host_out on streams[2]
- * (download); each stage of a chunk waits for the previous stage of that
- * chunk only, so consecutive chunks' uploads, kernels and downloads overlap.
+ * is copied host_noisy -> dev_in on the upload stream, denoised dev_in ->
+ * dev_out on a compute stream with the same kernels and results as
+ * mdn_denoise_multiscale, and copied dev_out -> host_out on the download
+ * stream; each stage of a chunk waits for the previous stage of that chunk
+ * only, so consecutive chunks' uploads, kernels and downloads overlap.
+ * streams: HOST array of nstreams distinct cudaStream_t, either 3 (upload,
+ * compute, download) or 4 (upload, compute A, compute B, download: chunks
+ * alternate between the two compute streams, so one chunk's kernel start-up
+ * and tail overlap the other's work).
  * host_noisy, host_out: HOST [n][3][h][w] buffers of dtype (page-locked
  * memory is needed for the copies to overlap); dev_in, dev_out: device
- * [n][3][h][w] buffers; ws: device workspace of at least
- * mdn_denoise_workspace_bytes(min(chunk, n), h, w, levels, dtype) (chunks run
- * one after the other on the compute stream and share it); streams: HOST
- * array of three distinct cudaStream_t.  The uploads and downloads start
- * after the work already queued on streams[1]; the call is asynchronous and
- * host_out is complete once streams[1] is synchronised.  Allocates no device
- * memory (it creates and releases three CUDA events per call).  Bucket maps
- * are not written.  MDN_EINVAL / MDN_ESHAPE / MDN_EWORKSPACE as for
- * mdn_denoise_multiscale, and MDN_EINVAL for chunk < 1 or equal streams. */
+ * [n][3][h][w] buffers; ws: device workspace of at least one chunk's
+ * mdn_denoise_workspace_bytes(min(chunk, n), h, w, levels, dtype) per compute
+ * stream (with two, each slice rounded up to 256 bytes; chunks on one compute
+ * stream share its slice).  The uploads, downloads and the second compute
+ * stream start after the work already queued on streams[1]; the call is
+ * asynchronous and host_out is complete once streams[1] is synchronised.
+ * Allocates no device memory (it creates and releases five CUDA events per
+ * call).  Bucket maps are not written.  MDN_EINVAL / MDN_ESHAPE /
+ * MDN_EWORKSPACE as for mdn_denoise_multiscale, and MDN_EINVAL for chunk < 1,
+ * nstreams other than 3 or 4, or equal streams. */
 int mdn_denoise_multiscale_pipelined(const void* host_noisy, int32_t dtype, int64_t n, int64_t h, int64_t w,
                                      int32_t levels, const void* const* banks, int32_t bank_dtype,
                                      const mdn_geometry* geom, const mdn_bucket_params* bparams, void* host_out,
                                      int64_t chunk, void* dev_in, void* dev_out, void* ws, size_t ws_bytes,
-                                     void* const* streams);
+                                     void* const* streams, int32_t nstreams);
 
 /* Same as mdn_denoise_multiscale, for callers that cannot allocate device
  * memory: a plug-in inside a host application that owns every device
@@ -255,6 +260,15 @@ int mdn_train_level_filters(const void* noisy_lvl, const void* coarse_out, const
                             int32_t gram_precision, int32_t accumulate, double* gram,
                             int64_t* counts, double lambda, float* bank_out, void* ws,
                             size_t ws_bytes, void* stream);
+
+/* Bounds-checked debug build (the library built with -DMDN_CHECK, a
+ * stand-in for a memory sanitizer): the kernels test their shared- and
+ * global-memory indices against the buffers they address; the first
+ * violation since the last call is reported here (synchronous) as the
+ * check site (a number > 0 naming the access in the source) and the index,
+ * and its access is skipped.  *site = 0: no violation; *site = -1: this
+ * library is not the checked build.  Reading clears the record. */
+int mdn_check_status(int32_t* site, int64_t* index);
 
 /* Bound, in nanoseconds, of every wait inside the tensor-core Gram kernel
  * (mbarrier hand-offs between its warp roles) for launches made after the

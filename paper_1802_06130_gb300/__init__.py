@@ -19,7 +19,8 @@ __all__ = ["build", "lib", "Geometry", "BucketParams", "default_bparams", "MdnEr
            "gram_state_shape", "train_status", "train_cascade", "Server", "F32", "F16", "YCBCR601", "RGB", "GRAM_FP32", "GRAM_TF32",
            "GRAM_BF16", "GRAM_SPLIT_BF16", "augment_dihedral", "dihedral", "estimate_noise", "nearest_level",
            "save_banks", "load_banks", "save_gram_state", "load_gram_state", "paper_grid_bparams",
-           "bucket_map_dtype", "MAX_K", "levels_for_sigma", "denoise_multiscale_pipelined", "pyramid_noise_factor", "set_gram_wait_limit",
+           "bucket_map_dtype", "MAX_K", "levels_for_sigma", "denoise_multiscale_pipelined", "use_checked_build",
+           "check_status", "pyramid_noise_factor", "set_gram_wait_limit",
            "gram_expire_next_wait"]
 
 F32, F16 = 0, 1
@@ -130,15 +131,37 @@ class ServerStats(C.Structure):
 
 
 _lib = None
+_lib_path = _LIB_PATH
+
+
+def use_checked_build(enable: bool = True) -> str:
+    """Switches this process's calls to the bounds-checked debug library
+    (built on first use; see mdn_check_status) or back to the normal one;
+    returns the library path now in use."""
+    global _lib, _lib_path
+    import importlib   # the module, not the function re-exported above under the same name
+    bmod = importlib.import_module(__name__ + ".build")
+    _lib_path = bmod.build(check=True) if enable else _LIB_PATH
+    _lib = None
+    return _lib_path
+
+
+def check_status():
+    """(site, index) of the first bounds violation recorded by the checked
+    library since the last call ((0, 0): none; site -1: not the checked
+    library)."""
+    site, idx = C.c_int32(0), C.c_int64(0)
+    _check(lib().mdn_check_status(C.byref(site), C.byref(idx)))
+    return site.value, idx.value
 
 
 def lib():
     """The loaded libmdn (raises if it has not been built)."""
     global _lib
     if _lib is None:
-        if not os.path.exists(_LIB_PATH):
-            raise RuntimeError(f"libmdn is not built ({_LIB_PATH}); call paper_1802_06130_gb300.build()")
-        L = C.CDLL(_LIB_PATH)
+        if not os.path.exists(_lib_path):
+            raise RuntimeError(f"libmdn is not built ({_lib_path}); call paper_1802_06130_gb300.build()")
+        L = C.CDLL(_lib_path)
         vp, i64, i32, sz = C.c_void_p, C.c_int64, C.c_int32, C.c_size_t
         G, B = C.POINTER(Geometry), C.POINTER(BucketParams)
         sig = {
@@ -154,7 +177,7 @@ def lib():
             "mdn_denoise_multiscale": (C.c_int, [vp, i32, i64, i64, i64, i32, C.POINTER(vp), i32, G, B, vp,
                                                  C.POINTER(vp), vp, sz, vp]),
             "mdn_denoise_multiscale_pipelined": (C.c_int, [vp, i32, i64, i64, i64, i32, C.POINTER(vp), i32, G, B,
-                                                           vp, i64, vp, vp, vp, sz, C.POINTER(vp)]),
+                                                           vp, i64, vp, vp, vp, sz, C.POINTER(vp), i32]),
             "mdn_gram_state_bytes": (sz, [G, i32]),
             "mdn_train_workspace_bytes": (sz, [i64, i64, i64, G, i32, i32]),
             "mdn_train_level_filters": (C.c_int, [vp, vp, vp, i32, i64, i64, i64, G, B, i32, i32, vp, vp,
@@ -162,6 +185,7 @@ def lib():
             "mdn_solve_workspace_bytes": (sz, [G, i32]),
             "mdn_train_status": (C.c_int, [C.POINTER(C.c_int32)]),
             "mdn_set_gram_wait_limit": (C.c_int, [C.c_uint64]),
+            "mdn_check_status": (C.c_int, [C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
             "mdn_gram_expire_next_wait": (C.c_int, [i32]),
             "mdn_pyramid_noise_factor": (C.c_double, [i32]),
             "mdn_levels_for_sigma": (i32, [C.c_double, C.c_double, i32, i32]),
@@ -334,16 +358,17 @@ def denoise_multiscale(noisy, banks, geom: Geometry, bparams, out=None, bucket_m
     return out if noisy.dim() == 4 else out[0]
 
 
-def denoise_multiscale_pipelined(host_noisy, banks, geom: Geometry, bparams, host_out, chunk: int = 2,
-                                 dev_in=None, dev_out=None, ws=None, streams=None):
+def denoise_multiscale_pipelined(host_noisy, banks, geom: Geometry, bparams, host_out, chunk: int = 1,
+                                 dev_in=None, dev_out=None, ws=None, streams=None, two_compute: bool = True):
     """Multiscale denoise of a batch in (pinned) host memory with the copies and
-    kernels of consecutive chunks overlapped on three streams
-    (mdn_denoise_multiscale_pipelined).  host_noisy, host_out: [n][3][h][w]
-    CPU tensors; dev_in, dev_out: matching CUDA tensors (allocated if None);
-    ws: workspace for `chunk` images; streams: (upload, compute, download)
-    torch streams (compute defaults to the current stream).  Asynchronous:
-    host_out is complete once the compute stream is synchronised.
-    Returns (dev_in, dev_out, ws, streams) for reuse."""
+    kernels of consecutive chunks overlapped (mdn_denoise_multiscale_pipelined).
+    host_noisy, host_out: [n][3][h][w] CPU tensors; dev_in, dev_out: matching
+    CUDA tensors (allocated if None); ws: workspace for `chunk` images per
+    compute stream; streams: (upload, compute, download) or (upload, compute
+    A, compute B, download) torch streams (the first compute stream defaults
+    to the current stream; two_compute picks the default layout).
+    Asynchronous: host_out is complete once the first compute stream is
+    synchronised.  Returns (dev_in, dev_out, ws, streams) for reuse."""
     torch = _torch()
     x = _img(host_noisy)
     n, _, h, w = x.shape
@@ -361,19 +386,22 @@ def denoise_multiscale_pipelined(host_noisy, banks, geom: Geometry, bparams, hos
     if dev_out is None:
         dev_out = torch.empty(x.shape, dtype=x.dtype, device=dev)
     c = max(1, min(chunk, n))
-    need = denoise_workspace_bytes(c, h, w, levels, _dtype_code(x))
+    if streams is None:
+        cur = torch.cuda.current_stream(dev)
+        streams = ((torch.cuda.Stream(device=dev), cur, torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev))
+                   if two_compute else (torch.cuda.Stream(device=dev), cur, torch.cuda.Stream(device=dev)))
+    per = denoise_workspace_bytes(c, h, w, levels, _dtype_code(x))
+    need = per if len(streams) == 3 else 2 * ((per + 255) // 256 * 256)
     if ws is None:
         ws = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
-    if streams is None:
-        streams = (torch.cuda.Stream(device=dev), torch.cuda.current_stream(dev), torch.cuda.Stream(device=dev))
-    sarr = (C.c_void_p * 3)(*[st.cuda_stream for st in streams])
+    sarr = (C.c_void_p * len(streams))(*[st.cuda_stream for st in streams])
     barr = (C.c_void_p * nb)(*[b.data_ptr() for b in banks])
     parr = (BucketParams * nb)(*bparams)
     _check(lib().mdn_denoise_multiscale_pipelined(C.c_void_p(x.data_ptr()), _dtype_code(x), n, h, w, levels, barr,
                                                   _dtype_code(banks[0]), C.byref(geom), parr,
                                                   C.c_void_p(host_out.data_ptr()), chunk, _dev(dev_in, "dev_in"),
                                                   _dev(dev_out, "dev_out"), _dev(ws, "ws"),
-                                                  ws.numel() * ws.element_size(), sarr))
+                                                  ws.numel() * ws.element_size(), sarr, len(streams)))
     return dev_in, dev_out, ws, streams
 
 

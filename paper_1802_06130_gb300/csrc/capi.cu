@@ -12,6 +12,10 @@
 
 namespace mdn {
 
+#ifdef MDN_CHECK
+__device__ unsigned long long g_mdn_check;   // first bounds violation (see common.cuh)
+#endif
+
 static thread_local std::string g_last_error;
 
 int fail(int code, const std::string& msg) {
@@ -378,6 +382,29 @@ int mdn_solve_bank(const double* gram, const int64_t* counts, const mdn_geometry
     int G = geom->cross_channel ? 1 : 3, T = geom->cross_channel ? 3 : 1;
     if (ws_bytes < solve_ws_bytes(K, G, D, T) || !ws) return fail(MDN_EWORKSPACE, "solve_bank: workspace too small");
     return launch_solve(gram, counts, K, G, D, T, lambda, bank_out, status_out, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int mdn_check_status(int32_t* site, int64_t* index) {
+    if (!site || !index) return fail(MDN_EINVAL, "check_status: null");
+#ifdef MDN_CHECK
+    unsigned long long v = 0, zero = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_mdn_check, sizeof(v));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_mdn_check, &zero, sizeof(zero));
+    if (e != cudaSuccess) return cuda_fail(e, "check_status");
+    if (v >> 63) {
+        *site = (int32_t)((v >> 48) & 0x7fff);
+        int64_t i = (int64_t)(v & 0xffffffffffffull);
+        if (i & (int64_t(1) << 47)) i -= int64_t(1) << 48;   // sign of the recorded 48-bit index
+        *index = i;
+    } else {
+        *site = 0;
+        *index = 0;
+    }
+#else
+    *site = -1;
+    *index = 0;
+#endif
+    return MDN_OK;
 }
 
 int mdn_set_gram_wait_limit(uint64_t ns) {

@@ -6,6 +6,23 @@
 
 namespace mdn {
 
+// Bounds checks of the debug build (-DMDN_CHECK, stand-in for a memory
+// sanitizer): mdn_in(i, n, site) is true when 0 <= i < n; otherwise the
+// first violation of the process (site, index) is recorded in g_mdn_check
+// (read and cleared by mdn_check_status) and the caller skips the access.
+// In normal builds it is the constant true and costs nothing.
+#ifdef MDN_CHECK
+extern __device__ unsigned long long g_mdn_check;
+__device__ __forceinline__ bool mdn_in(int64_t i, int64_t n, int site) {
+    if (i >= 0 && i < n) return true;
+    atomicCAS(&g_mdn_check, 0ull,
+              (1ull << 63) | ((unsigned long long)(site & 0x7fff) << 48) | ((unsigned long long)i & 0xffffffffffffull));
+    return false;
+}
+#else
+__device__ __forceinline__ constexpr bool mdn_in(int64_t, int64_t, int) { return true; }
+#endif
+
 template <typename T> __device__ __forceinline__ float ld_f(const T* p, int64_t i);
 template <> __device__ __forceinline__ float ld_f<float>(const float* p, int64_t i) { return __ldg(p + i); }
 template <> __device__ __forceinline__ float ld_f<__half>(const __half* p, int64_t i) {

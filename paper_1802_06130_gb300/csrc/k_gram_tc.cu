@@ -394,7 +394,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (int j = 0; j < PL; ++j) {
                 const int e = lane + 32 * j;
                 int bc = inv_c, bf = inv_f, bt = 0;
-                const int p = cur[j];
+                int p = cur[j];
+                if (p >= 0 && !mdn_in(p, (int64_t)ga.n * hw, 601)) p = -1;   // a pixel index past the images
                 if (p >= 0) {
                     const int img = p / hw, rem = p - img * hw;
                     const int y = rem / ga.w, x = rem - y * ga.w;

@@ -270,7 +270,8 @@ __global__ void __launch_bounds__(NT) k_level(const TS* __restrict__ z, const TS
         for (int i = tid; i < 3 * ZH * ZW; i += NT) {
             int c = i / (ZH * ZW), r = (i / ZW) % ZH, q = i % ZW;
             int gy = clampi(y0 - HZ + r, 0, H - 1), gx = clampi(x0 - HZ + q, 0, W - 1);
-            zs[i] = ld_f(zi, ((int64_t)c * H + gy) * W + gx);
+            const int64_t o = ((int64_t)c * H + gy) * W + gx;
+            zs[i] = mdn_in(o, 3 * (int64_t)H * W, 201) && mdn_in(img, nimg, 202) ? ld_f(zi, o) : 0.f;
         }
         if constexpr (FILTER && RC >= 0) {
             const TS* ci = coarse + (int64_t)img * 3 * Hc * Wc;
@@ -279,6 +280,7 @@ __global__ void __launch_bounds__(NT) k_level(const TS* __restrict__ z, const TS
                 int r = i / UW, q = i % UW;
                 int gy = clampi(cy0 + r, 0, Hc - 1), gx = clampi(cx0 + q, 0, Wc - 1);
                 int64_t o = (int64_t)gy * Wc + gx;
+                if (!mdn_in(o, (int64_t)Hc * Wc, 203)) o = 0;
                 float cr, cg, cb;
                 rgb_to_work(ld_f(ci, o), ld_f(ci, o + (int64_t)Hc * Wc), ld_f(ci, o + 2 * (int64_t)Hc * Wc), color,
                             cr, cg, cb);
@@ -343,7 +345,7 @@ __global__ void __launch_bounds__(NT) k_level(const TS* __restrict__ z, const TS
             k = k < K ? k : K - 1;
             bk[i] = (uint16_t)k;
             int gy = y0 + r, gx = x0 + q;
-            if (bmap && gy < H && gx < W) {
+            if (bmap && gy < H && gx < W && mdn_in(((int64_t)img * H + gy) * W + gx, (int64_t)nimg * H * W, 204)) {
                 const int64_t o = ((int64_t)img * H + gy) * W + gx;
                 if (wide) static_cast<uint16_t*>(bmap)[o] = (uint16_t)k;
                 else static_cast<uint8_t*>(bmap)[o] = (uint8_t)k;
@@ -357,7 +359,8 @@ __global__ void __launch_bounds__(NT) k_level(const TS* __restrict__ z, const TS
                 int r = i / TW, q = i % TW;
                 int gy = y0 + r, gx = x0 + q;
                 if (gy >= H || gx >= W) continue;
-                const int k = bk[i];
+                if (!mdn_in((int64_t)img * H * W + (int64_t)gy * W + gx, (int64_t)nimg * H * W, 205)) continue;
+                const int k = mdn_in(bk[i], K, 206) ? bk[i] : 0;
                 const float* zc = zs + (r + HZ) * ZW + (q + HZ);
                 const float* uc = us + (r / 2 + (RC > 0 ? RC : 0)) * UW + (q / 2 + (RC > 0 ? RC : 0));
                 float o[3];
@@ -591,7 +594,8 @@ __device__ __forceinline__ void tile_v2(unsigned char* smem, const unsigned char
     for (int i = tid; i < 3 * ZH * ZW; i += NT) {
         int c = i / (ZH * ZW), r = (i / ZW) % ZH, q = i % ZW;
         int gy = clampi(y0 - HZ + r, 0, H - 1), gx = clampi(x0 - HZ + q, 0, W - 1);
-        zs[i] = ld_f(zi, ((int64_t)c * H + gy) * W + gx);
+        const int64_t o = ((int64_t)c * H + gy) * W + gx;
+        zs[i] = mdn_in(o, 3 * (int64_t)H * W, 401) ? ld_f(zi, o) : 0.f;
     }
     if constexpr (RC >= 0) {
         constexpr int UWD = Coarse<SH, RC>::UWD;
@@ -600,6 +604,7 @@ __device__ __forceinline__ void tile_v2(unsigned char* smem, const unsigned char
             int r = i / UWD, q = i % UWD;
             int gy = clampi(cy0 + r, 0, Hc - 1), gx = clampi(cx0 + q, 0, Wc - 1);
             int64_t o = (int64_t)gy * Wc + gx;
+            if (!mdn_in(o, (int64_t)Hc * Wc, 402)) o = 0;
             float a, b, c;
             rgb_to_work(ld_f(ci, o), ld_f(ci, o + (int64_t)Hc * Wc), ld_f(ci, o + 2 * (int64_t)Hc * Wc), color, a, b,
                         c);
@@ -671,10 +676,20 @@ __device__ __forceinline__ void tile_v2(unsigned char* smem, const unsigned char
 #pragma unroll 1
         for (int pass = 0; pass < TH / NW; ++pass) {
             const int r = 2 * ((warp >> 1) + (NW / 2) * pass) + ro;
-            const uint2 kb = *reinterpret_cast<const uint2*>(bk + r * TW + c0);
+            uint2 kb = *reinterpret_cast<const uint2*>(bk + r * TW + c0);
+#ifdef MDN_CHECK
+            const bool ok = mdn_in(r + HZ + RF, ZH, 403) && mdn_in(c0 + HZ + RF + 7, ZW, 404) &&
+                            (RC < 0 || (mdn_in(r / 2 + 2 * (RC > 0 ? RC : 0), UH, 405) &&
+                                        mdn_in(c0 / 2 + 3 + 2 * (RC > 0 ? RC : 0), UW, 406)));
+            for (int p = 0; p < 8; ++p)
+                if (!mdn_in(((p < 4 ? kb.x : kb.y) >> (8 * (p & 3))) & 0xffu, K, 407)) kb = make_uint2(0u, 0u);
+            const int rr_ = ok ? r : 0, cc_ = ok ? c0 : 0;
+#else
+            const int rr_ = r, cc_ = c0;
+#endif
             float o[3];
-            v3::filter_group<RF, RC, CROSS, TB>(zs + (r + HZ - RF) * ZW + c0 + HZ - RF, ZH * ZW, ZW,
-                                                 us + (r / 2) * UW + c0 / 2, UH * UW, UW, bank_s, kb, j, o);
+            v3::filter_group<RF, RC, CROSS, TB>(zs + (rr_ + HZ - RF) * ZW + cc_ + HZ - RF, ZH * ZW, ZW,
+                                                 us + (rr_ / 2) * UW + cc_ / 2, UH * UW, UW, bank_s, kb, j, o);
             const int gy = y0 + r, gx = x0 + c0 + j;
             if (gy < H && gx < W) {
                 float R, Gc, B;
@@ -893,7 +908,8 @@ __device__ __forceinline__ void load_bank_rows(const TB* __restrict__ bank, int 
             const int cc = t / SL::NFR, dyi = t % SL::NFR;
             if (e < SL::NFR) src = SL::NCH * G::PC + cc * G::PF + dyi * SL::NFR + e;
         }
-        const TB v = src >= 0 ? bank[((int64_t)k * 3 + oc) * G::D + src] : TB(0.f);
+        const int64_t gi = ((int64_t)k * 3 + oc) * G::D + src;
+        const TB v = src >= 0 && mdn_in(gi, (int64_t)K * 3 * G::D, 127) ? bank[gi] : TB(0.f);
         reinterpret_cast<TB*>(bank_s + (size_t)k * BB + slot * SB)[e] = v;
     }
 }
@@ -1071,7 +1087,7 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
                     if (e < 3 * ZH * NCHUNK) {
                         const int c = e / (ZH * NCHUNK), r = (e / NCHUNK) % ZH, k = e % NCHUNK;
                         const TS* src = zi + ((int64_t)c * H + (y0 - HZ + r)) * W + (x0 - 4 + 4 * k);
-                        ld4(src, zreg + 4 * j);
+                        if (mdn_in(y0 - HZ + r, H, 101) && mdn_in(x0 - 4 + 4 * k, W - 3, 102)) ld4(src, zreg + 4 * j);
                     }
                 }
             } else {
@@ -1081,7 +1097,8 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
                     if (e < 3 * ZH * ZW) {
                         int c = e / (ZH * ZW), r = (e / ZW) % ZH, q = e % ZW;
                         int gy = clampi(y0 - HZ + r, 0, H - 1), gx = clampi(x0 - HZ + q, 0, W - 1);
-                        zreg[j] = ld_f(zi, ((int64_t)c * H + gy) * W + gx);
+                        const int64_t o = ((int64_t)c * H + gy) * W + gx;
+                        zreg[j] = mdn_in(o, 3 * (int64_t)H * W, 103) && mdn_in(img, nimg, 104) ? ld_f(zi, o) : 0.f;
                     }
                 }
             }
@@ -1095,6 +1112,7 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
                         int r = e / UWD, q = e % UWD;
                         int gy = clampi(cy0 + r, 0, Hc - 1), gx = clampi(cx0 + q, 0, Wc - 1);
                         int64_t o = (int64_t)gy * Wc + gx;
+                        if (!mdn_in(o, (int64_t)Hc * Wc, 105)) o = 0;
                         ureg[j][0] = ld_f(ci, o);
                         ureg[j][1] = ld_f(ci, o + (int64_t)Hc * Wc);
                         ureg[j][2] = ld_f(ci, o + 2 * (int64_t)Hc * Wc);
@@ -1125,7 +1143,7 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
 #pragma unroll
                         for (int t = 0; t < 4; ++t) {
                             const int q = 4 * k - 1 + t;
-                            if (q >= 0 && q < ZW) row[q] = zreg[4 * j + t];
+                            if (q >= 0 && q < ZW && mdn_in(cr * ZW + q, 3 * ZH * ZW, 106)) row[q] = zreg[4 * j + t];
                         }
                     }
                 }
@@ -1133,7 +1151,7 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
 #pragma unroll
                 for (int j = 0; j < NZS; ++j) {
                     const int e = pt + j * NP;
-                    if (e < 3 * ZH * ZW) zs[e] = zreg[j];
+                    if (e < 3 * ZH * ZW && mdn_in(e, 3 * ZH * ZW, 107)) zs[e] = zreg[j];
                 }
             }
             if constexpr (RC >= 0) {
@@ -1144,7 +1162,7 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
                         float a, b, c;
                         rgb_to_work(ureg[j][0], ureg[j][1], ureg[j][2], color, a, b, c);
                         const int o = (e / UWD) * UW + e % UWD;
-                        us[o] = a; us[UH * UW + o] = b; us[2 * UH * UW + o] = c;
+                        if (mdn_in(o, UH * UW, 108)) { us[o] = a; us[UH * UW + o] = b; us[2 * UH * UW + o] = c; }
                     }
                 }
             }
@@ -1162,13 +1180,14 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
                     pxy = __fmaf_rn(gx[c], gy[c], pxy);
                     pyy = __fmaf_rn(gy[c], gy[c], pyy);
                 }
-                ps[e] = pxx; ps[PH * PW + e] = pxy; ps[2 * PH * PW + e] = pyy;
+                if (mdn_in(e, PH * PW, 109)) { ps[e] = pxx; ps[PH * PW + e] = pxy; ps[2 * PH * PW + e] = pyy; }
             };
             if (inner) {
                 static_assert(PH % 2 == 0, "row pairs");
                 for (int e0 = pt; e0 < (PH / 2) * PW; e0 += NP) {
                     const int m = e0 / PW, q = e0 - m * PW;
-                    const int ly = 2 * m + 1, lx = q + 1;   // staged position of product (2m, q)
+                    int ly = 2 * m + 1, lx = q + 1;   // staged position of product (2m, q)
+                    if (!(mdn_in(ly - 1, ZH - 2, 110) && mdn_in(lx - 1, ZW - 2, 111))) ly = lx = 1;
                     float gx0[3], gy0[3], gx1[3], gy1[3];
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
@@ -1189,13 +1208,17 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
                     const int cy = clampi(y0 - 2 + r, 0, H - 1), cx = clampi(x0 - 2 + q, 0, W - 1);
                     const int ly = cy - (y0 - HZ), lx = cx - (x0 - HZ);
                     const int lxm = clampi(cx - 1, 0, W - 1) - (x0 - HZ), lxp = clampi(cx + 1, 0, W - 1) - (x0 - HZ);
-                    const int lym = clampi(cy - 1, 0, H - 1) - (y0 - HZ), lyp = clampi(cy + 1, 0, H - 1) - (y0 - HZ);
+                    int lym = clampi(cy - 1, 0, H - 1) - (y0 - HZ), lyp = clampi(cy + 1, 0, H - 1) - (y0 - HZ);
+                    int lyc = ly, lxc = lx, lxmc = lxm, lxpc = lxp;
+                    if (!(mdn_in(lym, ZH, 112) && mdn_in(lyp, ZH, 112) && mdn_in(lyc, ZH, 112) &&
+                          mdn_in(lxmc, ZW, 113) && mdn_in(lxpc, ZW, 113) && mdn_in(lxc, ZW, 113)))
+                        lym = lyp = lyc = lxc = lxmc = lxpc = 0;
                     float gx[3], gy[3];
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         const float* zc = zs + c * ZH * ZW;
-                        gx[c] = __fmul_rn(__fsub_rn(zc[ly * ZW + lxp], zc[ly * ZW + lxm]), 0.5f);
-                        gy[c] = __fmul_rn(__fsub_rn(zc[lyp * ZW + lx], zc[lym * ZW + lx]), 0.5f);
+                        gx[c] = __fmul_rn(__fsub_rn(zc[lyc * ZW + lxpc], zc[lyc * ZW + lxmc]), 0.5f);
+                        gy[c] = __fmul_rn(__fsub_rn(zc[lyp * ZW + lxc], zc[lym * ZW + lxc]), 0.5f);
                     }
                     prod(gx, gy, e0);
                 }
@@ -1205,7 +1228,8 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
             // of one (field, row) from two 16-byte loads of its 8 inputs
             static_assert(PW % 4 == 0 && TW % 4 == 0, "16-byte rows");
             for (int e = pt; e < 3 * PH * (TW / 4); e += NP) {
-                const int fr = e / (TW / 4), q = 4 * (e - fr * (TW / 4));
+                int fr = e / (TW / 4), q = 4 * (e - fr * (TW / 4));
+                if (!(mdn_in(fr * PW + q + 7, 3 * PH * PW, 114) && mdn_in(fr * TW + q + 3, 3 * PH * TW, 115))) fr = q = 0;
                 const float4 a4 = *reinterpret_cast<const float4*>(ps + fr * PW + q);
                 const float4 b4 = *reinterpret_cast<const float4*>(ps + fr * PW + q + 4);
                 const float p8[8] = {a4.x, a4.y, a4.z, a4.w, b4.x, b4.y, b4.z, b4.w};
@@ -1222,6 +1246,7 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
             // RGB tile -> working colour space, flat over the producer threads
             // (the unused pad column is converted too)
             for (int e = pt; e < ZH * ZW; e += NP) {
+                if (!mdn_in(e, ZH * ZW, 116)) continue;
                 float a, b, c;
                 rgb_to_work(zs[e], zs[ZH * ZW + e], zs[2 * ZH * ZW + e], color, a, b, c);
                 zs[e] = a; zs[ZH * ZW + e] = b; zs[2 * ZH * ZW + e] = c;
@@ -1236,7 +1261,8 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
 #pragma unroll
             for (int f = 0; f < 3; ++f)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) win[f][v] = hs[f * PH * TW + (4 * pw + v) * TW + lane];
+                for (int v = 0; v < 4; ++v)
+                    win[f][v] = mdn_in(4 * pw + v + 4, PH, 117) ? hs[f * PH * TW + (4 * pw + v) * TW + lane] : 0.f;
             float ta[4], tb[4], tc[4];
 #pragma unroll
             for (int rr = 0; rr < 4; ++rr) {
@@ -1244,7 +1270,7 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
                 float t3[3];
 #pragma unroll
                 for (int f = 0; f < 3; ++f) {
-                    const float nxt = hs[f * PH * TW + (r + 4) * TW + lane];
+                    const float nxt = mdn_in(r + 4, PH, 118) ? hs[f * PH * TW + (r + 4) * TW + lane] : 0.f;
                     float acc = __fmul_rn(wv[0], win[f][0]);
 #pragma unroll
                     for (int v = 1; v < 4; ++v) acc = __fmaf_rn(wv[v], win[f][v], acc);
@@ -1262,9 +1288,10 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
             for (int rr = 0; rr < 4; ++rr) {
                 const int r = 4 * pw + rr;
                 const int k = kk[rr] < K ? kk[rr] : K - 1;
-                bk[r * TW + lane] = (uint8_t)k;
+                if (mdn_in(r * TW + lane, TH * TW, 119)) bk[r * TW + lane] = (uint8_t)k;
                 const int gy = y0 + r, gx = x0 + lane;
-                if (bmap && gy < H && gx < W) bmap[((int64_t)img * H + gy) * W + gx] = (uint8_t)k;
+                const int64_t mo = ((int64_t)img * H + gy) * W + gx;
+                if (bmap && gy < H && gx < W && mdn_in(mo, (int64_t)nimg * H * W, 120)) bmap[mo] = (uint8_t)k;
             }
             bar_arrive(BAR_FULL0 + s, NT);
         }
@@ -1286,13 +1313,24 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
 #pragma unroll 1
             for (int pass = 0; pass < TH / 8; ++pass) {
                 const int r = 2 * ((warp >> 1) + 4 * pass) + ro;          // tile row of this group
-                const uint2 kb = *reinterpret_cast<const uint2*>(bk + r * TW + c0);
+                uint2 kb = *reinterpret_cast<const uint2*>(bk + r * TW + c0);
+#ifdef MDN_CHECK
+                // every patch row and column the group reads, and its buckets
+                const bool fine_ok = mdn_in(r + HZ + RF, ZH, 121) && mdn_in(c0 + HZ + RF + PX - 1, ZW, 122);
+                const bool coarse_ok = RC < 0 || (mdn_in(r / 2 + 2 * (RC > 0 ? RC : 0), UH, 123) &&
+                                                  mdn_in(c0 / 2 + PX / 2 + 2 * (RC > 0 ? RC : 0) - 1, UW, 124));
+                for (int p = 0; p < 8; ++p)
+                    if (!mdn_in(((p < 4 ? kb.x : kb.y) >> (8 * (p & 3))) & 0xffu, K, 125)) kb = make_uint2(0u, 0u);
+                const int rr_ = fine_ok && coarse_ok ? r : 0, cc_ = fine_ok && coarse_ok ? c0 : 0;
+#else
+                const int rr_ = r, cc_ = c0;
+#endif
                 float o[3];
-                filter_group<RF, RC, CROSS, TB>(zs + (r + HZ - RF) * ZW + c0 + HZ - RF, ZH * ZW, ZW,
-                                                 us + (r / 2) * UW + c0 / 2, UH * UW, UW, bank_s, kb, j, o);
+                filter_group<RF, RC, CROSS, TB>(zs + (rr_ + HZ - RF) * ZW + cc_ + HZ - RF, ZH * ZW, ZW,
+                                                 us + (rr_ / 2) * UW + cc_ / 2, UH * UW, UW, bank_s, kb, j, o);
                 if (pass == TH / 8 - 1 && i + 2 < T) bar_arrive(BAR_EMPTY0 + s, NT);   // stage s no longer read
                 const int gy = y0 + r, gx = x0 + c0 + j;
-                if (gy < H && gx < W) {
+                if (gy < H && gx < W && mdn_in((int64_t)img * H * W + (int64_t)gy * W + gx, (int64_t)nimg * H * W, 126)) {
                     float R, Gc, B;
                     work_to_rgb(o[0], o[1], o[2], color, R, Gc, B);
                     const int64_t po = (int64_t)gy * W + gx;

@@ -623,7 +623,7 @@ int launch_gram(const TrainArgs& a, cudaStream_t s) {
 
     GatherArgs ga{};
     ga.zw = zw; ga.tw = tw; ga.cw = a.coarse ? cw : nullptr;
-    ga.h = (int)a.h; ga.w = (int)a.w; ga.hc = (int)a.hc; ga.wc = (int)a.wc;
+    ga.h = (int)a.h; ga.w = (int)a.w; ga.hc = (int)a.hc; ga.wc = (int)a.wc; ga.n = (int)a.n;
     ga.P = P; ga.Hp = (int)Hp; ga.Wp = (int)Wp; ga.Hcp = (int)Hcp; ga.Wcp = (int)Wcp;
     ga.rf = a.geom.r_fine; ga.rc = a.geom.r_coarse; ga.cross = a.geom.cross_channel; ga.color = a.geom.color;
     ga.D = a.D; ga.T = a.T; ga.G = a.G; ga.Dp = a.Dp; ga.Dp4 = (a.Dp + 1 + 3) / 4 * 4;

@@ -28,7 +28,8 @@ __device__ __forceinline__ void tile_down(const TS* __restrict__ src, TS* __rest
         if (i < PIH * PIW) {
             int r = i / PIW, c = i % PIW;
             int gy = clampi(iy0 + r, 0, H - 1), gx = clampi(ix0 + c, 0, W - 1);
-            v[j] = ld_f(src, (int64_t)gy * W + gx);
+            const int64_t o = (int64_t)gy * W + gx;
+            v[j] = mdn_in(o, (int64_t)H * W, 301) ? ld_f(src, o) : 0.f;
         }
     }
 #pragma unroll
@@ -39,7 +40,7 @@ __device__ __forceinline__ void tile_down(const TS* __restrict__ src, TS* __rest
     __syncthreads();
     for (int i = tid; i < PIH * PTX; i += PNT) {
         int r = i / PTX, c = i % PTX;
-        const float* p = &tile[r][2 * c];
+        const float* p = &tile[r][mdn_in(2 * c + 4, PIW, 302) ? 2 * c : 0];
         float acc = __fmul_rn(b0, p[0]);
         acc = __fmaf_rn(b1, p[1], acc);
         acc = __fmaf_rn(b2, p[2], acc);
@@ -51,7 +52,7 @@ __device__ __forceinline__ void tile_down(const TS* __restrict__ src, TS* __rest
     for (int i = tid; i < PTY * PTX; i += PNT) {
         int ty = i / PTX, tx = i % PTX;
         int ox = ox0 + tx, oy = oy0 + ty;
-        if (ox < Wo && oy < Ho) {
+        if (ox < Wo && oy < Ho && mdn_in(2 * ty + 4, PIH, 303)) {
             float acc = __fmul_rn(b0, hs[2 * ty][tx]);
             acc = __fmaf_rn(b1, hs[2 * ty + 1][tx], acc);
             acc = __fmaf_rn(b2, hs[2 * ty + 2][tx], acc);

@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(pyr::PNT) k_serve_pyr(const WorkList* __restri
             int mid = (lo + hi + 1) / 2;
             if (wl->pyr[b + mid].tile_start <= t) lo = mid; else hi = mid - 1;
         }
-        const PyrItem& it = wl->pyr[b + lo];
+        const PyrItem& it = wl->pyr[mdn_in(b + lo, MAX_STAGE_ITEMS, 501) ? b + lo : 0];
         const int lt = t - it.tile_start;
         __syncthreads();   // shared buffers free
         pyr::tile_down(it.in + (int64_t)ch * it.H * it.W, it.out + (int64_t)ch * it.Ho * it.Wo, it.H, it.W, it.Ho,
@@ -111,8 +111,9 @@ __global__ void __launch_bounds__(SH::NT, 1) k_serve_level(const WorkList* __res
     int cur_bank = -1, item = 0;
     for (int t = begin; t < end; ++t) {
         while (item + 1 < n && items[item + 1].tile_start <= t) ++item;
-        const LvlItem& it = items[item];
+        const LvlItem& it = items[mdn_in(wl->lvl_begin[stage] + item, MAX_STAGE_ITEMS, 502) ? item : 0];
         __syncthreads();   // previous tile finished with the shared buffers
+        if (!mdn_in(it.bank, MAX_BANKS, 503)) continue;
         if (it.bank != cur_bank) {
             // items are sorted by bank: a CTA's contiguous tile range rarely switches
             lvl::v3::load_bank_rows<RF, RC, CROSS, __half>(tb->bank[it.bank], tb->K[it.bank], bank_s, threadIdx.x,

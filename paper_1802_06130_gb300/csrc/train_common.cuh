@@ -79,6 +79,7 @@ struct GatherArgs {
     const float* tw;   // [n][3][h][w] working space, clean level l (centre taps only, no border)
     const float* cw;   // [n][3][Hcp][Wcp] working space, coarse output, border P replicated, or nullptr
     int h, w, hc, wc;
+    int n;                     // images
     int P, Hp, Wp, Hcp, Wcp;   // Hp = h + 2P, Wp = w + 2P, Hcp = hc + 2P, Wcp = wc + 2P
     int rf, rc, cross, color;
     int D, T, G, Dp, Dp4;   // Dp4: SIMT row stride, >= Dp + 1, multiple of 4

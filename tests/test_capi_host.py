@@ -237,3 +237,26 @@ def test_depth_rule_behind_the_c_abi(L):
     assert mdn.levels_for_sigma(15 / 255) == 3 and mdn.levels_for_sigma(1 / 255, min_levels=2) == 2
     with pytest.raises(ValueError):
         mdn.pyramid_noise_factor(9)
+
+
+def test_pipelined_entry_checks_arguments(L):
+    """mdn_denoise_multiscale_pipelined rejects a stream count other than 3 or
+    4, a zero chunk and a missing stream array before any device work."""
+    bp = mdn.default_bparams(0)
+    barr = (C.c_void_p * 2)(16, 16)
+    parr = (mdn.BucketParams * 2)(bp, bp)
+    s3 = (C.c_void_p * 5)(8, 16, 24, 32, 40)
+    g = C.byref(mdn.Geometry(3, 3))
+    f = L.mdn_denoise_multiscale_pipelined
+    rc = f(C.c_void_p(16), 1, 2, 64, 64, 3, barr, 1, g, parr, C.c_void_p(32), 1, C.c_void_p(48), C.c_void_p(64),
+           C.c_void_p(80), 1 << 30, s3, 5)
+    assert rc == 1 and b"nstreams" in L.mdn_last_error()
+    rc = f(C.c_void_p(16), 1, 2, 64, 64, 3, barr, 1, g, parr, C.c_void_p(32), 0, C.c_void_p(48), C.c_void_p(64),
+           C.c_void_p(80), 1 << 30, s3, 3)
+    assert rc == 1 and b"chunk" in L.mdn_last_error()
+    rc = f(C.c_void_p(16), 1, 2, 64, 64, 3, barr, 1, g, parr, C.c_void_p(32), 1, C.c_void_p(48), C.c_void_p(64),
+           C.c_void_p(80), 1 << 30, None, 3)
+    assert rc == 1 and b"streams" in L.mdn_last_error()
+    rc = f(C.c_void_p(16), 1, 2, 64, 64, 3, barr, 1, g, parr, C.c_void_p(32), 1, C.c_void_p(48), C.c_void_p(64),
+           C.c_void_p(80), 10, s3, 4)
+    assert rc == 3 and b"workspace" in L.mdn_last_error()

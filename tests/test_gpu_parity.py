@@ -450,11 +450,12 @@ def test_train_cascade_matches_oracle(mdn, case, prec):
 
 # ------------------------------------------------------------ host-to-host pipeline
 
-@pytest.mark.parametrize("chunk", [1, 2, 5])
-def test_pipelined_host_path_equals_device_path(mdn, chunk):
+@pytest.mark.parametrize("two", [False, True], ids=["one_compute_stream", "two_compute_streams"])
+@pytest.mark.parametrize("chunk", [1, 3, 5])
+def test_pipelined_host_path_equals_device_path(mdn, chunk, two):
     """mdn_denoise_multiscale_pipelined (host buffers, chunks overlapped on
-    three streams) gives the device path's results exactly, for chunk sizes
-    that divide the batch, leave a ragged last chunk and exceed it."""
+    three or four streams) gives the device path's results exactly, for chunk
+    sizes that divide the batch, leave a ragged last chunk and exceed it."""
     frames = np.stack([synth.noisy_pair(97, 130, 800 + i)[0] for i in range(4)])
     geom = mdn.Geometry(3, 3)
     bps = [mdn.default_bparams(0), mdn.default_bparams(1)]
@@ -464,6 +465,6 @@ def test_pipelined_host_path_equals_device_path(mdn, chunk):
     ref = mdn.denoise_multiscale(x.cuda(), banks, geom, bps).cpu()
     host_in = x.pin_memory()
     host_out = torch.full_like(host_in, float("nan")).pin_memory()
-    mdn.denoise_multiscale_pipelined(host_in, banks, geom, bps, host_out, chunk=chunk)
+    mdn.denoise_multiscale_pipelined(host_in, banks, geom, bps, host_out, chunk=chunk, two_compute=two)
     torch.cuda.current_stream().synchronize()
     assert torch.equal(host_out, ref)
