@@ -341,19 +341,30 @@ def run_variants(mdn, x, geom, dev, stream, reps=10):
     """The rest of the 12 MP metric run, timing only (same frames, denoise via
     mdn_denoise_multiscale with preallocated output and workspace, L2 flushed
     before every timed call, median): FP16 and FP32 storage, batch 1 and 8,
-    the 4-level pipeline of the 12 MP batch, and the paper's own 16 x 16 x 16
-    grid with 7x7 + 5x5 taps (4096 buckets, bank read through L2)."""
+    the 4-level pipeline of the 12 MP batch, FP32 banks, and the paper's own
+    16 x 16 x 16 grid with 7x7 + 5x5 taps (4096 buckets).  Banks too large for
+    shared memory (the 4096-bucket grid, FP32 banks of 7x7 + 7x7 taps) run
+    plain (tile kernel, taps through L2) and prepared (mdn_prepare_bank_rows:
+    the fused kernel reading row slots through L2)."""
     import torch
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     res = {}
     paper_geom = mdn.Geometry(3, 2)
-    for name, xv, levels in [("f16_batch1_3level", x[:1], 3), ("f32_batch1_3level", x[:1].float(), 3),
-                             ("f32_batch8_3level", x.float(), 3), ("f16_batch8_4level", x, 4),
-                             ("f16_batch1_3level_grid16x16x16_7x7+5x5", x[:1], 3)]:
-        paper = "grid16" in name     # the paper's 4096-bucket grid: bank read through L2
+    f16, f32 = torch.float16, torch.float32
+    grid = "f16_batch1_3level_grid16x16x16_7x7+5x5"
+    for name, xv, levels, bank_dt, prepared in [
+            ("f16_batch1_3level", x[:1], 3, f16, False), ("f32_batch1_3level", x[:1].float(), 3, f16, False),
+            ("f32_batch8_3level", x.float(), 3, f16, False), ("f16_batch8_4level", x, 4, f16, False),
+            ("f32_batch1_3level_f32bank", x[:1].float(), 3, f32, False),
+            ("f32_batch1_3level_f32bank_prepared", x[:1].float(), 3, f32, True),
+            (grid, x[:1], 3, f16, False), (grid + "_prepared", x[:1], 3, f16, True),
+            (grid.replace("batch1", "batch8") + "_prepared", x, 3, f16, True)]:
+        paper = "grid16" in name
         g = paper_geom if paper else geom
-        banks = [torch.tensor(b, dtype=torch.float16, device=dev)
+        banks = [torch.tensor(b, dtype=bank_dt, device=dev)
                  for b in (random_banks(7, D=74, K=4096, nb=levels - 1) if paper else random_banks(7, nb=levels - 1))]
+        if prepared:
+            banks = [mdn.prepare_bank(b, g) for b in banks]
         bps = [(mdn.paper_grid_bparams if paper else mdn.default_bparams)(l) for l in range(levels - 1)]
         nv = xv.shape[0]
         dt = mdn.F16 if xv.dtype == torch.float16 else mdn.F32

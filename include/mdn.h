@@ -55,6 +55,9 @@ extern "C" {
 /* ---- element types ---- */
 #define MDN_F32 0
 #define MDN_F16 1
+/* bank types only: a bank prepared by mdn_prepare_bank_rows (row slots) */
+#define MDN_F16_ROWS 2
+#define MDN_F32_ROWS 3
 
 /* ---- colour spaces ---- */
 #define MDN_YCBCR601 0
@@ -154,6 +157,27 @@ int mdn_select_buckets(const void* z, int32_t dtype, int64_t n, int64_t h, int64
 int mdn_filter_level(const void* z, const void* coarse, int32_t dtype, int64_t n, int64_t h,
                      int64_t w, const void* bank, int32_t bank_dtype, const mdn_geometry* geom,
                      const mdn_bucket_params* bp, void* out, void* buckets_out, void* stream);
+
+/* Prepared banks.  mdn_prepare_bank_rows writes a bank [K][3][D] (bank_dtype
+ * MDN_F32 or MDN_F16, device) into `rows` (device, 16-byte aligned, at least
+ * mdn_bank_rows_bytes bytes) in the layout the fused level kernel reads: per
+ * bucket, output channel, block (coarse patch of each input channel, then
+ * fine patch of each) and filter row dy, one slot of 8 elements holding the
+ * 2r+1 taps dx = -r..r of that row, zero padded.  Pass `rows` as the bank
+ * with bank_dtype MDN_F16_ROWS / MDN_F32_ROWS to mdn_filter_level and the
+ * mdn_denoise_multiscale family: a bank that fits in shared memory is copied
+ * there whole; a larger one (the paper's 4096-bucket grid, FP32 banks of 216
+ * buckets of 7x7 + 7x7 taps) is read from this layout through L2 with 16-byte
+ * loads instead of tap by tap.  Results equal those of the plain bank where
+ * both run the same kernel; geometries: 5x5, 7x7 + 7x7, 7x7 + 5x5 per
+ * channel and 7x7x3 cross-channel.  mdn_bank_rows_bytes returns 0 for
+ * another geometry or bad arguments.  The layout carries no header: a
+ * prepared bank must be passed with the geometry and bucket count it was
+ * prepared for (the caller's contract, like the size of any buffer; the
+ * Python binding checks it).  Asynchronous on stream. */
+size_t mdn_bank_rows_bytes(const mdn_geometry* geom, int32_t K, int32_t bank_dtype);
+int mdn_prepare_bank_rows(const void* bank, int32_t bank_dtype, const mdn_geometry* geom, int32_t K, void* rows,
+                          size_t rows_bytes, void* stream);
 
 /* ------------------------------------------------------------------ */
 /* Multiscale denoising (Section 4)                                    */

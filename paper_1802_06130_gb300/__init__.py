@@ -20,10 +20,12 @@ __all__ = ["build", "lib", "Geometry", "BucketParams", "default_bparams", "MdnEr
            "GRAM_BF16", "GRAM_SPLIT_BF16", "augment_dihedral", "dihedral", "estimate_noise", "nearest_level",
            "save_banks", "load_banks", "save_gram_state", "load_gram_state", "paper_grid_bparams",
            "bucket_map_dtype", "MAX_K", "levels_for_sigma", "denoise_multiscale_pipelined", "use_checked_build",
+           "PreparedBank", "prepare_bank", "F16_ROWS", "F32_ROWS",
            "check_status", "pyramid_noise_factor", "set_gram_wait_limit",
            "gram_expire_next_wait"]
 
 F32, F16 = 0, 1
+F16_ROWS, F32_ROWS = 2, 3   # prepared banks (mdn_prepare_bank_rows)
 YCBCR601, RGB = 0, 1
 GRAM_FP32, GRAM_TF32, GRAM_BF16, GRAM_SPLIT_BF16 = 0, 1, 2, 3
 MAX_THR = 16
@@ -179,6 +181,8 @@ def lib():
             "mdn_denoise_multiscale_pipelined": (C.c_int, [vp, i32, i64, i64, i64, i32, C.POINTER(vp), i32, G, B,
                                                            vp, i64, vp, vp, vp, sz, C.POINTER(vp), i32]),
             "mdn_gram_state_bytes": (sz, [G, i32]),
+            "mdn_bank_rows_bytes": (sz, [G, i32, i32]),
+            "mdn_prepare_bank_rows": (C.c_int, [vp, i32, G, i32, vp, sz, vp]),
             "mdn_train_workspace_bytes": (sz, [i64, i64, i64, G, i32, i32]),
             "mdn_train_level_filters": (C.c_int, [vp, vp, vp, i32, i64, i64, i64, G, B, i32, i32, vp, vp,
                                                   C.c_double, vp, vp, sz, vp]),
@@ -228,6 +232,55 @@ def _dtype_code(t) -> int:
     if t.dtype == torch.float16:
         return F16
     raise TypeError(f"unsupported dtype {t.dtype} (float32 or float16)")
+
+
+class PreparedBank:
+    """A filter bank in the fused level kernel's row-slot layout
+    (mdn_prepare_bank_rows); accepted wherever a bank tensor is."""
+
+    def __init__(self, rows, code: int, K: int, geom: Geometry):
+        self.rows, self.code, self.K = rows, code, K
+        self.geom = (geom.r_fine, geom.r_coarse, int(geom.cross_channel != 0))
+
+    def data_ptr(self):
+        return self.rows.data_ptr()
+
+
+def prepare_bank(bank, geom: Geometry, stream=None) -> PreparedBank:
+    """Lays out a [K][3][D] FP16/FP32 CUDA bank once in the fused kernel's
+    row slots (mdn_prepare_bank_rows): banks too large for shared memory are
+    then read through L2 with 16-byte loads."""
+    torch = _torch()
+    K = bank.shape[0]
+    code = _dtype_code(bank)
+    nbytes = lib().mdn_bank_rows_bytes(C.byref(geom), K, code)
+    if nbytes == 0:
+        raise ValueError("prepare_bank: geometry not compiled or bad bank")
+    rows = torch.empty(nbytes, dtype=torch.uint8, device=bank.device)
+    _check(lib().mdn_prepare_bank_rows(_dev(bank, "bank"), code, C.byref(geom), K, _dev(rows, "rows"), nbytes,
+                                       _stream(stream)))
+    return PreparedBank(rows, F16_ROWS if code == F16 else F32_ROWS, K, geom)
+
+
+def _check_banks(banks, geom: Geometry, bparams):
+    """The C ABI takes one bank type for all levels, and a prepared bank's
+    layout is fixed by the geometry and bucket count it was prepared for."""
+    codes = {_bank_code(b) for b in banks}
+    if len(codes) != 1:
+        raise ValueError("all banks must have the same dtype / layout")
+    g = (geom.r_fine, geom.r_coarse, int(geom.cross_channel != 0))
+    for b, bp in zip(banks, bparams):
+        if isinstance(b, PreparedBank) and (b.geom != g or b.K != bp.K):
+            raise ValueError(f"prepared bank is for geometry {b.geom} with K={b.K}, "
+                             f"call has {g} with K={bp.K}")
+
+
+def _bank_code(b) -> int:
+    return b.code if isinstance(b, PreparedBank) else _dtype_code(b)
+
+
+def _bank_dev(b, name="bank"):
+    return _dev(b.rows if isinstance(b, PreparedBank) else b, name)
 
 
 def _dev(t, name="tensor"):
@@ -312,8 +365,9 @@ def filter_level(z, coarse, bank, geom: Geometry, bp: BucketParams, out=None, bu
     c4 = _img(coarse) if coarse is not None else None
     if out is None:
         out = torch.empty_like(z4)
-    _check(lib().mdn_filter_level(_dev(z4, "z"), _dev(c4, "coarse"), _dtype_code(z4), n, h, w, _dev(bank, "bank"),
-                                  _dtype_code(bank), C.byref(geom), C.byref(bp), _dev(out, "out"),
+    _check_banks([bank], geom, [bp])
+    _check(lib().mdn_filter_level(_dev(z4, "z"), _dev(c4, "coarse"), _dtype_code(z4), n, h, w, _bank_dev(bank),
+                                  _bank_code(bank), C.byref(geom), C.byref(bp), _dev(out, "out"),
                                   _map(buckets_out, bp.K, n, h, w, "buckets_out"), _stream(stream)))
     return out if z.dim() == 4 else out[0]
 
@@ -339,7 +393,8 @@ def denoise_multiscale(noisy, banks, geom: Geometry, bparams, out=None, bucket_m
     need = denoise_workspace_bytes(n, h, w, levels, _dtype_code(z4))
     if ws is None:
         ws = torch.empty(max(need, 1), dtype=torch.uint8, device=z4.device)
-    bank_dt = _dtype_code(banks[0])
+    _check_banks(banks, geom, bparams)
+    bank_dt = _bank_code(banks[0])
     barr = (C.c_void_p * nb)(*[b.data_ptr() for b in banks])
     parr = (BucketParams * nb)(*bparams)
     marr = None
@@ -395,10 +450,11 @@ def denoise_multiscale_pipelined(host_noisy, banks, geom: Geometry, bparams, hos
     if ws is None:
         ws = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
     sarr = (C.c_void_p * len(streams))(*[st.cuda_stream for st in streams])
+    _check_banks(banks, geom, bparams)
     barr = (C.c_void_p * nb)(*[b.data_ptr() for b in banks])
     parr = (BucketParams * nb)(*bparams)
     _check(lib().mdn_denoise_multiscale_pipelined(C.c_void_p(x.data_ptr()), _dtype_code(x), n, h, w, levels, barr,
-                                                  _dtype_code(banks[0]), C.byref(geom), parr,
+                                                  _bank_code(banks[0]), C.byref(geom), parr,
                                                   C.c_void_p(host_out.data_ptr()), chunk, _dev(dev_in, "dev_in"),
                                                   _dev(dev_out, "dev_out"), _dev(ws, "ws"),
                                                   ws.numel() * ws.element_size(), sarr, len(streams)))

@@ -112,6 +112,17 @@ int check_img(const void* p, int dtype, int64_t n, int64_t h, int64_t w, const c
 
 static size_t esize(int dtype) { return dtype == MDN_F16 ? 2 : 4; }
 
+// bank dtype code -> element type and layout (plain [K][3][D] or prepared row slots)
+static int bank_kind(int32_t bank_dtype, int* elem, bool* rows, const char* what) {
+    switch (bank_dtype) {
+        case MDN_F32: *elem = MDN_F32; *rows = false; return MDN_OK;
+        case MDN_F16: *elem = MDN_F16; *rows = false; return MDN_OK;
+        case MDN_F32_ROWS: *elem = MDN_F32; *rows = true; return MDN_OK;
+        case MDN_F16_ROWS: *elem = MDN_F16; *rows = true; return MDN_OK;
+        default: return fail(MDN_EINVAL, std::string(what) + ": bad bank dtype");
+    }
+}
+
 int launch_level_f32_f32(const LevelArgs& a, cudaStream_t s);
 int launch_level_f32_f16(const LevelArgs& a, cudaStream_t s);
 int launch_level_f16_f32(const LevelArgs& a, cudaStream_t s);
@@ -200,14 +211,17 @@ int mdn_filter_level(const void* z, const void* coarse, int32_t dtype, int64_t n
     if ((rc = check_geom(geom))) return rc;
     if (!out) return fail(MDN_EINVAL, "filter_level: null output");
     if (!bank) return fail(MDN_EINVAL, "filter_level: null bank");
-    if (bank_dtype != MDN_F32 && bank_dtype != MDN_F16) return fail(MDN_EINVAL, "filter_level: bad bank dtype");
+    int bank_elem = 0;
+    bool bank_rows = false;
+    if ((rc = bank_kind(bank_dtype, &bank_elem, &bank_rows, "filter_level"))) return rc;
     if (geom->r_coarse >= 0 && !coarse) return fail(MDN_EINVAL, "filter_level: coarse level required");
     if (out == z || (coarse && out == coarse)) return fail(MDN_EINVAL, "filter_level: out aliases an input");
     LevelArgs a{};
     if ((rc = make_sel_params(bp, &a.sel))) return rc;
     a.z = z; a.coarse = geom->r_coarse >= 0 ? coarse : nullptr; a.out = out; a.buckets = buckets_out;
     a.bank = bank; a.n = n; a.h = h; a.w = w; a.hc = (h + 1) / 2; a.wc = (w + 1) / 2;
-    a.dtype = dtype; a.bank_dtype = bank_dtype; a.K = bp->n_angle * bp->n_strength * bp->n_coherence;
+    a.dtype = dtype; a.bank_dtype = bank_elem; a.bank_rows = bank_rows;
+    a.K = bp->n_angle * bp->n_strength * bp->n_coherence;
     a.geom = *geom;
     return launch_level(a, (cudaStream_t)stream);
 }
@@ -239,6 +253,9 @@ int mdn_denoise_multiscale(const void* noisy, int32_t dtype, int64_t n, int64_t 
     if (!banks || !bparams || (!out && n * h * w > 0))
         return fail(MDN_EINVAL, "denoise_multiscale: null banks/bparams/out");
     if (out == noisy && n * h * w > 0) return fail(MDN_EINVAL, "denoise_multiscale: out aliases the input");
+    int bank_elem = 0;
+    bool bank_rows = false;
+    if ((rc = bank_kind(bank_dtype, &bank_elem, &bank_rows, "denoise_multiscale"))) return rc;
     const int nb = levels > 1 ? levels - 1 : 1;
     for (int l = 0; l < nb; ++l)
         if (!banks[l] && n * h * w > 0) return fail(MDN_EINVAL, "denoise_multiscale: null bank pointer");
@@ -277,7 +294,7 @@ int mdn_denoise_multiscale(const void* noisy, int32_t dtype, int64_t n, int64_t 
         a.z = zl[l]; a.coarse = coarse; a.out = ul[l];
         a.buckets = bucket_maps ? bucket_maps[l] : nullptr;
         a.bank = banks[l]; a.n = n; a.h = hl[l]; a.w = wl[l]; a.hc = (hl[l] + 1) / 2; a.wc = (wl[l] + 1) / 2;
-        a.dtype = dtype; a.bank_dtype = bank_dtype;
+        a.dtype = dtype; a.bank_dtype = bank_elem; a.bank_rows = bank_rows;
         a.K = bparams[l].n_angle * bparams[l].n_strength * bparams[l].n_coherence;
         a.geom = *geom;
         NvtxRange r(l == 0 ? "level 0" : l == 1 ? "level 1" : l == 2 ? "level 2" : "level 3+");

@@ -54,9 +54,10 @@ struct LevelArgs {
     const void* coarse;   // [n][3][hc][wc] or nullptr
     void* out;            // [n][3][h][w] or nullptr (select-only)
     void* buckets;        // [n][h][w] or nullptr, u8 (K <= 256) or u16
-    const void* bank;     // [K][3][D]
+    const void* bank;     // [K][3][D], or prepared row slots when bank_rows
     int64_t n, h, w, hc, wc;
-    int dtype, bank_dtype;
+    int dtype, bank_dtype;   // bank_dtype: element type (MDN_F32 / MDN_F16)
+    bool bank_rows;          // bank in the row-slot layout of mdn_prepare_bank_rows
     int K;
     mdn_geometry geom;
     SelParams sel;

@@ -560,10 +560,11 @@ __device__ __forceinline__ void build_bucket_placement(const SelParams& sp, int 
 
 }  // namespace v2
 namespace v3 {
-template <int RF, int RC, bool CROSS, typename TB>
+template <int RF, int RC, bool CROSS, typename TB, bool GLOBAL = false>
 __device__ __forceinline__ void filter_group(const float* __restrict__ zb, int zpl, int zst,
                                              const float* __restrict__ ub, int upl, int ust,
-                                             const unsigned char* __restrict__ bank_s, uint2 kb, int j, float o[3]);
+                                             const unsigned char* __restrict__ bank_s, const int (&kb)[8], int j,
+                                             float o[3]);
 }  // namespace v3
 namespace v2 {
 
@@ -676,13 +677,16 @@ __device__ __forceinline__ void tile_v2(unsigned char* smem, const unsigned char
 #pragma unroll 1
         for (int pass = 0; pass < TH / NW; ++pass) {
             const int r = 2 * ((warp >> 1) + (NW / 2) * pass) + ro;
-            uint2 kb = *reinterpret_cast<const uint2*>(bk + r * TW + c0);
+            const uint2 kbw = *reinterpret_cast<const uint2*>(bk + r * TW + c0);
+            int kb[8];
+#pragma unroll
+            for (int p = 0; p < 8; ++p) kb[p] = (int)(((p < 4 ? kbw.x : kbw.y) >> (8 * (p & 3))) & 0xffu);
 #ifdef MDN_CHECK
             const bool ok = mdn_in(r + HZ + RF, ZH, 403) && mdn_in(c0 + HZ + RF + 7, ZW, 404) &&
                             (RC < 0 || (mdn_in(r / 2 + 2 * (RC > 0 ? RC : 0), UH, 405) &&
                                         mdn_in(c0 / 2 + 3 + 2 * (RC > 0 ? RC : 0), UW, 406)));
             for (int p = 0; p < 8; ++p)
-                if (!mdn_in(((p < 4 ? kb.x : kb.y) >> (8 * (p & 3))) & 0xffu, K, 407)) kb = make_uint2(0u, 0u);
+                if (!mdn_in(kb[p], K, 407)) kb[p] = 0;
             const int rr_ = ok ? r : 0, cc_ = ok ? c0 : 0;
 #else
             const int rr_ = r, cc_ = c0;
@@ -926,21 +930,40 @@ __device__ __forceinline__ void load_bank_rows(const TB* __restrict__ bank, int 
 //   ub:  coarse plane of channel 0 at (row r/2, column c0/2) of the coarse
 //        stage (whose origin is RC rows and columns before the coarse pixel of
 //        the tile origin); upl, ust: plane and row strides
-//   kb:  the 8 pixels' buckets (one byte each, pixel p in byte p)
+//   kb:  the 8 pixels' buckets
+//   GLOBAL: the row-slot bank is in global memory (read through the
+//        read-only cache, 16-byte loads) instead of shared memory
 // The arithmetic (FMA order within a lane, reduction tree) is fixed, so any
 // kernel calling this gives bit-identical outputs for the same inputs.
-template <int RF, int RC, bool CROSS, typename TB>
+template <typename TB, bool GLOBAL> __device__ __forceinline__ void group_slot(const unsigned char* p, float h[8]) {
+    if constexpr (!GLOBAL) {
+        v2::load_slot<TB>(p, h);
+    } else if constexpr (sizeof(TB) == 2) {
+        const uint4 q = __ldg(reinterpret_cast<const uint4*>(p));
+        const __half2* hp = reinterpret_cast<const __half2*>(&q);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float2 f = __half22float2(hp[e]);
+            h[2 * e] = f.x; h[2 * e + 1] = f.y;
+        }
+    } else {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(p)), b = __ldg(reinterpret_cast<const float4*>(p + 16));
+        h[0] = a.x; h[1] = a.y; h[2] = a.z; h[3] = a.w; h[4] = b.x; h[5] = b.y; h[6] = b.z; h[7] = b.w;
+    }
+}
+
+template <int RF, int RC, bool CROSS, typename TB, bool GLOBAL>
 __device__ __forceinline__ void filter_group(const float* __restrict__ zb, int zpl, int zst,
                                              const float* __restrict__ ub, int upl, int ust,
-                                             const unsigned char* __restrict__ bank_s, uint2 kb, int j, float o[3]) {
+                                             const unsigned char* __restrict__ bank_s, const int (&kb)[8], int j,
+                                             float o[3]) {
     using SL = RowSlots<RF, RC, CROSS>;
     constexpr int SB = v2::SlotBytes<TB>::B;
     constexpr int BSTRIDE = bucket_bytes_rows<RF, RC, CROSS, TB>();
     const unsigned FULL = 0xffffffffu;
     const unsigned char* hb[PX];
 #pragma unroll
-    for (int p = 0; p < PX; ++p)
-        hb[p] = bank_s + (size_t)(((p < 4 ? kb.x : kb.y) >> (8 * (p & 3))) & 0xffu) * BSTRIDE;
+    for (int p = 0; p < PX; ++p) hb[p] = bank_s + (size_t)kb[p] * BSTRIDE;
     float acc[3][PX];
 #pragma unroll
     for (int oc = 0; oc < 3; ++oc)
@@ -963,7 +986,7 @@ __device__ __forceinline__ void filter_group(const float* __restrict__ zb, int z
 #pragma unroll
                     for (int p = 0; p < PX; ++p) {
                         float h[8];
-                        v2::load_slot<TB>(hb[p] + (slot + j) * SB, h);
+                        group_slot<TB, GLOBAL>(hb[p] + (slot + j) * SB, h);
 #pragma unroll
                         for (int d = 0; d < SL::NCR; ++d) acc[oc][p] = fmaf(h[d], col[p / 2 + d], acc[oc][p]);
                     }
@@ -983,7 +1006,7 @@ __device__ __forceinline__ void filter_group(const float* __restrict__ zb, int z
 #pragma unroll
                 for (int p = 0; p < PX; ++p) {
                     float h[8];
-                    v2::load_slot<TB>(hb[p] + (slot + j) * SB, h);
+                    group_slot<TB, GLOBAL>(hb[p] + (slot + j) * SB, h);
 #pragma unroll
                     for (int d = 0; d < SL::NFR; ++d) acc[oc][p] = fmaf(h[d], col[p + d], acc[oc][p]);
                 }
@@ -1017,35 +1040,49 @@ __device__ __forceinline__ void filter_group(const float* __restrict__ zb, int z
     }
 }
 
-template <int RC> constexpr size_t stage_bytes() {
-    return sizeof(float) * (3 * ZH * ZW + 3 * Coarse<RC>::UH * Coarse<RC>::UW) + TH * TW;
+// stage: zs [3][ZH][ZW], us [3][UH][UW], then the bucket tile [TH][TW] of
+// BTB-byte indices at a 16-byte aligned offset (8 indices = one vector load)
+template <int RC> constexpr size_t bk_offset() {
+    return (sizeof(float) * (3 * ZH * ZW + 3 * Coarse<RC>::UH * Coarse<RC>::UW) + 15) & ~size_t(15);
+}
+template <int RC, int BTB = 1> constexpr size_t stage_bytes() {
+    return (bk_offset<RC>() + (size_t)TH * TW * BTB + 15) & ~size_t(15);
 }
 constexpr size_t scratch_bytes() { return sizeof(float) * (3 * PH * PW + 3 * PH * TW); }
-template <int RC> constexpr size_t front_bytes() {
-    return ((2 * stage_bytes<RC>() + scratch_bytes()) + 15) & ~size_t(15);
+template <int RC, int BTB = 1> constexpr size_t front_bytes() {
+    return ((2 * stage_bytes<RC, BTB>() + scratch_bytes()) + 15) & ~size_t(15);
 }
-template <int RF, int RC, bool CROSS, typename TB> size_t smem_need(int K) {
-    return front_bytes<RC>() + (size_t)K * bucket_bytes_rows<RF, RC, CROSS, TB>();
+// GB: the bank stays in global memory (prepared row slots read through L2);
+// BTB: bytes per bucket index in the stage (1, or 2 above 256 buckets)
+template <int RF, int RC, bool CROSS, typename TB, bool GB = false, int BTB = 1> size_t smem_need(int K) {
+    return front_bytes<RC, BTB>() + (GB ? 0 : (size_t)K * bucket_bytes_rows<RF, RC, CROSS, TB>());
 }
 
-template <int RF, int RC, bool CROSS, typename TS, typename TB>
+template <int RF, int RC, bool CROSS, typename TS, typename TB, bool GB, typename BT>
 __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, const TS* __restrict__ coarse,
-                                                  TS* __restrict__ out, uint8_t* __restrict__ bmap,
+                                                  TS* __restrict__ out, void* __restrict__ bmap,
                                                   const TB* __restrict__ bank, int H, int W, int Hc, int Wc,
                                                   int nimg, int K, int color, SelParams sp, float w0, float w1,
-                                                  float w2) {
+                                                  float w2, int rows_in) {
     using SL = RowSlots<RF, RC, CROSS>;
     constexpr int UW = Coarse<RC>::UW, UH = Coarse<RC>::UH, UWD = Coarse<RC>::UWD;
     constexpr int SB = v2::SlotBytes<TB>::B;
     constexpr int BSTRIDE = bucket_bytes_rows<RF, RC, CROSS, TB>();
-    constexpr size_t SBY = stage_bytes<RC>();
+    constexpr size_t SBY = stage_bytes<RC, (int)sizeof(BT)>();
     extern __shared__ __align__(16) unsigned char smem[];
     float* ps = reinterpret_cast<float*>(smem + 2 * SBY);   // producer scratch [3][PH][PW]
     float* hs = ps + 3 * PH * PW;                             // [3][PH][TW]
-    unsigned char* bank_s = smem + front_bytes<RC>();
+    unsigned char* bank_s = GB ? (unsigned char*)bank : smem + front_bytes<RC, (int)sizeof(BT)>();
     const int tid = threadIdx.x;
 
-    load_bank_rows<RF, RC, CROSS, TB>(bank, K, bank_s, tid, NT);   // once per persistent CTA
+    if constexpr (!GB) {
+        if (rows_in) {   // prepared row slots: a straight 16-byte copy
+            for (int i = tid; i < K * BSTRIDE / 16; i += NT)
+                reinterpret_cast<uint4*>(bank_s)[i] = __ldg(reinterpret_cast<const uint4*>(bank) + i);
+        } else {
+            load_bank_rows<RF, RC, CROSS, TB>(bank, K, bank_s, tid, NT);
+        }
+    }   // once per persistent CTA
     __syncthreads();
 
     const int tiles_x = (W + TW - 1) / TW, tiles_y = (H + TH - 1) / TH;
@@ -1126,7 +1163,7 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
             if (i >= 2) bar_sync(BAR_EMPTY0 + s, NT);
             float* zs = reinterpret_cast<float*>(smem + s * SBY);
             float* us = zs + 3 * ZH * ZW;
-            uint8_t* bk = reinterpret_cast<uint8_t*>(us + 3 * UH * UW);
+            BT* bk = reinterpret_cast<BT*>(smem + s * SBY + bk_offset<RC>());
             const int64_t tile = blockIdx.x + i * gridDim.x;
             const int img = (int)(tile / ((int64_t)tiles_x * tiles_y));
             const int trem = (int)(tile % ((int64_t)tiles_x * tiles_y));
@@ -1288,10 +1325,10 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
             for (int rr = 0; rr < 4; ++rr) {
                 const int r = 4 * pw + rr;
                 const int k = kk[rr] < K ? kk[rr] : K - 1;
-                if (mdn_in(r * TW + lane, TH * TW, 119)) bk[r * TW + lane] = (uint8_t)k;
+                if (mdn_in(r * TW + lane, TH * TW, 119)) bk[r * TW + lane] = (BT)k;
                 const int gy = y0 + r, gx = x0 + lane;
                 const int64_t mo = ((int64_t)img * H + gy) * W + gx;
-                if (bmap && gy < H && gx < W && mdn_in(mo, (int64_t)nimg * H * W, 120)) bmap[mo] = (uint8_t)k;
+                if (bmap && gy < H && gx < W && mdn_in(mo, (int64_t)nimg * H * W, 120)) static_cast<BT*>(bmap)[mo] = (BT)k;
             }
             bar_arrive(BAR_FULL0 + s, NT);
         }
@@ -1304,7 +1341,7 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
             bar_sync(BAR_FULL0 + s, NT);
             const float* zs = reinterpret_cast<const float*>(smem + s * SBY);
             const float* us = zs + 3 * ZH * ZW;
-            const uint8_t* bk = reinterpret_cast<const uint8_t*>(us + 3 * UH * UW);
+            const BT* bk = reinterpret_cast<const BT*>(smem + s * SBY + bk_offset<RC>());
             const int64_t tile = blockIdx.x + i * gridDim.x;
             const int img = (int)(tile / ((int64_t)tiles_x * tiles_y));
             const int trem = (int)(tile % ((int64_t)tiles_x * tiles_y));
@@ -1313,20 +1350,30 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
 #pragma unroll 1
             for (int pass = 0; pass < TH / 8; ++pass) {
                 const int r = 2 * ((warp >> 1) + 4 * pass) + ro;          // tile row of this group
-                uint2 kb = *reinterpret_cast<const uint2*>(bk + r * TW + c0);
+                int kb[8];
+                if constexpr (sizeof(BT) == 1) {
+                    const uint2 w8 = *reinterpret_cast<const uint2*>(bk + r * TW + c0);
+#pragma unroll
+                    for (int p = 0; p < 8; ++p) kb[p] = (int)(((p < 4 ? w8.x : w8.y) >> (8 * (p & 3))) & 0xffu);
+                } else {
+                    const uint4 w16 = *reinterpret_cast<const uint4*>(bk + r * TW + c0);
+                    const uint32_t wv4[4] = {w16.x, w16.y, w16.z, w16.w};
+#pragma unroll
+                    for (int p = 0; p < 8; ++p) kb[p] = (int)((wv4[p >> 1] >> (16 * (p & 1))) & 0xffffu);
+                }
 #ifdef MDN_CHECK
                 // every patch row and column the group reads, and its buckets
                 const bool fine_ok = mdn_in(r + HZ + RF, ZH, 121) && mdn_in(c0 + HZ + RF + PX - 1, ZW, 122);
                 const bool coarse_ok = RC < 0 || (mdn_in(r / 2 + 2 * (RC > 0 ? RC : 0), UH, 123) &&
                                                   mdn_in(c0 / 2 + PX / 2 + 2 * (RC > 0 ? RC : 0) - 1, UW, 124));
                 for (int p = 0; p < 8; ++p)
-                    if (!mdn_in(((p < 4 ? kb.x : kb.y) >> (8 * (p & 3))) & 0xffu, K, 125)) kb = make_uint2(0u, 0u);
+                    if (!mdn_in(kb[p], K, 125)) kb[p] = 0;
                 const int rr_ = fine_ok && coarse_ok ? r : 0, cc_ = fine_ok && coarse_ok ? c0 : 0;
 #else
                 const int rr_ = r, cc_ = c0;
 #endif
                 float o[3];
-                filter_group<RF, RC, CROSS, TB>(zs + (rr_ + HZ - RF) * ZW + cc_ + HZ - RF, ZH * ZW, ZW,
+                filter_group<RF, RC, CROSS, TB, GB>(zs + (rr_ + HZ - RF) * ZW + cc_ + HZ - RF, ZH * ZW, ZW,
                                                  us + (rr_ / 2) * UW + cc_ / 2, UH * UW, UW, bank_s, kb, j, o);
                 if (pass == TH / 8 - 1 && i + 2 < T) bar_arrive(BAR_EMPTY0 + s, NT);   // stage s no longer read
                 const int gy = y0 + r, gx = x0 + c0 + j;
@@ -1343,10 +1390,10 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
     }
 }
 
-template <int RF, int RC, bool CROSS, typename TS, typename TB>
+template <int RF, int RC, bool CROSS, typename TS, typename TB, bool GB = false, typename BT = uint8_t>
 int run3(const LevelArgs& a, cudaStream_t s) {
-    auto kern = k_level3<RF, RC, CROSS, TS, TB>;
-    const size_t bytes = smem_need<RF, RC, CROSS, TB>(a.K);
+    auto kern = k_level3<RF, RC, CROSS, TS, TB, GB, BT>;
+    const size_t bytes = smem_need<RF, RC, CROSS, TB, GB, (int)sizeof(BT)>(a.K);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return cuda_fail(e, "k_level3: set smem attribute");
     int occ = 0;
@@ -1358,9 +1405,9 @@ int run3(const LevelArgs& a, cudaStream_t s) {
     if (grid > tiles) grid = tiles;
     float w[5];
     gauss5_weights(w);
-    kern<<<(unsigned)grid, NT, bytes, s>>>((const TS*)a.z, (const TS*)a.coarse, (TS*)a.out, (uint8_t*)a.buckets,
+    kern<<<(unsigned)grid, NT, bytes, s>>>((const TS*)a.z, (const TS*)a.coarse, (TS*)a.out, a.buckets,
                                            (const TB*)a.bank, (int)a.h, (int)a.w, (int)a.hc, (int)a.wc,
-                                           (int)a.n, a.K, a.geom.color, a.sel, w[0], w[1], w[2]);
+                                           (int)a.n, a.K, a.geom.color, a.sel, w[0], w[1], w[2], a.bank_rows ? 1 : 0);
     return check_launch("k_level3");
 }
 
@@ -1371,10 +1418,21 @@ int run3(const LevelArgs& a, cudaStream_t s) {
 #define MDN_USE_V3 1
 #endif
 
-// Geometry dispatch for one (storage, bank) type pair.
+// Geometry dispatch for one (storage, bank) type pair.  Plain banks
+// ([K][3][D]): the fused kernel with the bank in shared memory when it fits,
+// else the strip or tile kernels.  Prepared banks (row slots,
+// mdn_prepare_bank_rows): the fused kernel, with the bank copied to shared
+// memory when it fits and read through L2 otherwise.
 template <typename TS, typename TB> int dispatch(const LevelArgs& a, cudaStream_t s) {
     const mdn_geometry& g = a.geom;
+    const bool rows = a.bank_rows;
 #define MDN_GEO(RF_, RC_, CR_)                                                                  \
+    if (rows && g.r_fine == RF_ && g.r_coarse == RC_ && (g.cross_channel != 0) == CR_) {        \
+        if (a.K <= 256 && v3::smem_need<RF_, RC_, CR_, TB>(a.K) <= SMEM_LIMIT)                \
+            return v3::run3<RF_, RC_, CR_, TS, TB, false, uint8_t>(a, s);                     \
+        if (a.K <= 256) return v3::run3<RF_, RC_, CR_, TS, TB, true, uint8_t>(a, s);          \
+        return v3::run3<RF_, RC_, CR_, TS, TB, true, uint16_t>(a, s);                         \
+    }                                                                                           \
     if (g.r_fine == RF_ && g.r_coarse == RC_ && (g.cross_channel != 0) == CR_) {                \
         if (MDN_USE_V3 && a.K <= 256 && v3::smem_need<RF_, RC_, CR_, TB>(a.K) <= SMEM_LIMIT)  \
             return v3::run3<RF_, RC_, CR_, TS, TB>(a, s);                                      \

@@ -260,3 +260,30 @@ def test_pipelined_entry_checks_arguments(L):
     rc = f(C.c_void_p(16), 1, 2, 64, 64, 3, barr, 1, g, parr, C.c_void_p(32), 1, C.c_void_p(48), C.c_void_p(64),
            C.c_void_p(80), 10, s3, 4)
     assert rc == 3 and b"workspace" in L.mdn_last_error()
+
+
+def test_prepared_bank_layout_sizes_and_checks(L):
+    """mdn_bank_rows_bytes: one 16-byte (FP16) or 32-byte (FP32) slot per
+    bucket, output channel, tap block and filter row (2r+1 rows per block; a
+    7x7x3 cross-channel filter has three fine blocks per output channel);
+    mdn_prepare_bank_rows rejects bad arguments before any device work."""
+    cases = [((2, -1), 3 * 5), ((3, 3), 3 * (7 + 7)), ((3, 2), 3 * (7 + 5)), ((3, -1, 1), 3 * 3 * 7)]
+    for args, slots in cases:
+        g = C.byref(mdn.Geometry(*args))
+        assert L.mdn_bank_rows_bytes(g, 216, mdn.F16) == 216 * slots * 16
+        assert L.mdn_bank_rows_bytes(g, 4096, mdn.F32) == 4096 * slots * 32
+        assert L.mdn_bank_rows_bytes(g, 0, mdn.F16) == 0
+        assert L.mdn_bank_rows_bytes(g, 4097, mdn.F16) == 0
+        assert L.mdn_bank_rows_bytes(g, 216, mdn.F16_ROWS) == 0
+    assert L.mdn_bank_rows_bytes(C.byref(mdn.Geometry(1, -1)), 216, mdn.F16) == 0
+    assert L.mdn_bank_rows_bytes(None, 216, mdn.F16) == 0
+    g = C.byref(mdn.Geometry(3, 3))
+    f = L.mdn_prepare_bank_rows
+    need = L.mdn_bank_rows_bytes(g, 216, mdn.F16)
+    assert f(None, mdn.F16, g, 216, C.c_void_p(256), need, None) == 1
+    assert f(C.c_void_p(256), mdn.F16_ROWS, g, 216, C.c_void_p(256), need, None) == 1
+    assert f(C.c_void_p(256), mdn.F16, g, 0, C.c_void_p(256), need, None) == 1
+    assert f(C.c_void_p(256), mdn.F16, C.byref(mdn.Geometry(1, -1)), 216, C.c_void_p(256), need, None) == 2
+    assert f(C.c_void_p(256), mdn.F16, g, 216, C.c_void_p(256), need - 16, None) == 3
+    assert f(C.c_void_p(256), mdn.F16, g, 216, C.c_void_p(264), need, None) == 1
+    assert b"16-byte" in L.mdn_last_error()

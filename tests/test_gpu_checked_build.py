@@ -88,6 +88,8 @@ def test_checked_filter_level(mdn, geom_args, D, bank_dt):
             c = _img((h + 1) // 2, (w + 1) // 2, 960 + i, dt) if geom.r_coarse >= 0 else None
             ref, got = _both(mdn, lambda: mdn.filter_level(z, c, bank, geom, bp))
             _close(ref, got, dt)
+            ref, got = _both(mdn, lambda: mdn.filter_level(z, c, mdn.prepare_bank(bank, geom), geom, bp))
+            _close(ref, got, dt)
 
 
 def test_checked_denoise_multiscale_and_wide_grid(mdn):
@@ -99,6 +101,9 @@ def test_checked_denoise_multiscale_and_wide_grid(mdn):
         ref, got = _both(mdn, lambda: mdn.denoise_multiscale(x, banks, geom, [mdn.default_bparams(l) for l in range(3)]))
         _close(ref, got, torch.float16)
         ref, got = _both(mdn, lambda: mdn.denoise_multiscale(x, wide, geom_p, [mdn.paper_grid_bparams(l) for l in range(2)]))
+        _close(ref, got, torch.float16)
+        ref, got = _both(mdn, lambda: mdn.denoise_multiscale(x, [mdn.prepare_bank(b, geom_p) for b in wide], geom_p,
+                                                             [mdn.paper_grid_bparams(l) for l in range(2)]))
         _close(ref, got, torch.float16)
     host = _img(97, 131, 980, torch.float16).cpu().repeat(3, 1, 1, 1).contiguous().pin_memory()
 

@@ -468,3 +468,49 @@ def test_pipelined_host_path_equals_device_path(mdn, chunk, two):
     mdn.denoise_multiscale_pipelined(host_in, banks, geom, bps, host_out, chunk=chunk, two_compute=two)
     torch.cuda.current_stream().synchronize()
     assert torch.equal(host_out, ref)
+
+
+# ------------------------------------------------------------ prepared (row-slot) banks
+
+@pytest.mark.parametrize("geom", [O.Geometry(2, -1), O.Geometry(3, 3), O.Geometry(3, 2)],
+                         ids=["5x5", "7x7+7x7", "7x7+5x5"])
+def test_prepared_bank_in_shared_memory_equals_plain(mdn, geom):
+    """A 216-bucket FP16 bank prepared by mdn_prepare_bank_rows is copied to
+    shared memory whole and gives exactly the plain bank's results."""
+    bank = _tt(_bank(216, geom, 71, "f16"), "f16")
+    bp = mdn.default_bparams(0)
+    for i, (h, w) in enumerate([(33, 17), (200, 300)]):
+        z = _tt(O.round_storage(synth.noisy_pair(h, w, 7100 + i)[0], "f16"), "f16")[None]
+        c = _tt(O.round_storage(synth.clean_image((h + 1) // 2, (w + 1) // 2, 7200 + i), "f16"), "f16")[None] \
+            if geom.r_coarse >= 0 else None
+        m1 = torch.empty((1, h, w), dtype=torch.uint8, device="cuda")
+        m2 = torch.empty_like(m1)
+        a = mdn.filter_level(z, c, bank, _geom(mdn, geom), bp, buckets_out=m1)
+        b = mdn.filter_level(z, c, mdn.prepare_bank(bank, _geom(mdn, geom)), _geom(mdn, geom), bp, buckets_out=m2)
+        assert torch.equal(a, b) and torch.equal(m1, m2)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_prepared_fp32_bank_through_l2_matches_oracle(mdn, storage):
+    """An FP32 bank of 216 buckets of 7x7 + 7x7 taps (290 KB of row slots,
+    more than shared memory holds) is read by the fused kernel from its
+    prepared layout through L2: within the FP32 / FP16 bars of the FP64
+    oracle given the same FP32 bank, and close to the plain bank's tile kernel."""
+    geom = O.Geometry(3, 3)
+    bank = _bank(216, geom, 73, "f32")
+    bp_o = O.default_bparams(0)
+    for i, (h, w) in enumerate([(1, 1), (33, 17), (131, 97), (200, 300)]):
+        zs = O.round_storage(synth.noisy_pair(h, w, 7300 + i)[0], storage)
+        uc = O.round_storage(synth.clean_image((h + 1) // 2, (w + 1) // 2, 7400 + i), storage)
+        ref_b, band, _ = O.select(zs, bp_o, mirror32=True)
+        ref = O.round_storage(O.filter_level(zs, uc, ref_b, bank, geom), storage)
+        dbank = _tt(bank, "f32")
+        m = torch.empty((1, h, w), dtype=torch.uint8, device="cuda")
+        out = mdn.filter_level(_tt(zs, storage)[None], _tt(uc, storage)[None], mdn.prepare_bank(dbank, _geom(mdn, geom)),
+                               _geom(mdn, geom), mdn.default_bparams(0), buckets_out=m)
+        plain = mdn.filter_level(_tt(zs, storage)[None], _tt(uc, storage)[None], dbank, _geom(mdn, geom),
+                                 mdn.default_bparams(0))
+        mism = m[0].cpu().numpy() != ref_b
+        assert not (mism & ~band).any()
+        assert max_abs(_np(out[0]), ref, ~mism) <= TOL[storage]
+        assert (out.float() - plain.float()).abs().max().item() <= (1e-5 if storage == "f32" else 1e-3)

@@ -99,11 +99,14 @@ def test_wide_buckets_spread_over_the_grid(mdn):
 
 # ------------------------------------------------------------ A4
 
+@pytest.mark.parametrize("prepared", [False, True], ids=["plain_bank", "prepared_bank"])
 @pytest.mark.parametrize("storage", ["f32", "f16"])
 @pytest.mark.parametrize("bank_storage", ["f32", "f16"])
 @pytest.mark.parametrize("geom", [GEOM, O.Geometry(2, -1)], ids=["7x7+5x5", "5x5"])
-@pytest.mark.parametrize("hw", [(1, 1), (33, 17), (97, 130)])
-def test_wide_filter_level(mdn, storage, bank_storage, geom, hw):
+@pytest.mark.parametrize("hw", [(1, 1), (33, 17), (97, 130), (200, 300)])
+def test_wide_filter_level(mdn, storage, bank_storage, geom, hw, prepared):
+    """Plain banks run the tile kernel (taps through L2); prepared banks
+    (mdn_prepare_bank_rows) run the fused kernel reading row slots through L2."""
     h, w = hw
     z, _ = synth.noisy_pair(h, w, 5300 + h * w)
     zs = O.round_storage(z, storage)
@@ -114,9 +117,11 @@ def test_wide_filter_level(mdn, storage, bank_storage, geom, hw):
     ref_b, band, _ = O.select(zs, bp, mirror32=True)
     ref = O.round_storage(O.filter_level(zs, uc, ref_b, bank, geom), storage)
     bmap = torch.empty((1, h, w), dtype=torch.int16, device="cuda")
+    dbank = _tt(bank, bank_storage).contiguous()
+    if prepared:
+        dbank = mdn.prepare_bank(dbank, _geom(mdn, geom))
     out = mdn.filter_level(_tt(zs, storage)[None], _tt(uc, storage)[None] if uc is not None else None,
-                           _tt(bank, bank_storage).contiguous(), _geom(mdn, geom), _gbp(mdn, bp),
-                           buckets_out=bmap)
+                           dbank, _geom(mdn, geom), _gbp(mdn, bp), buckets_out=bmap)
     mism = _map(bmap[0]) != ref_b.astype(np.int64)
     assert not (mism & ~band).any()
     err = max_abs(_np(out[0]), ref, ~mism)
@@ -133,8 +138,9 @@ def test_wide_bucket_map_type_is_checked(mdn):
                          buckets_out=torch.empty((1, 16, 16), dtype=torch.uint8, device="cuda"))
 
 
+@pytest.mark.parametrize("prepared", [False, True], ids=["plain_bank", "prepared_bank"])
 @pytest.mark.parametrize("storage", ["f32", "f16"])
-def test_wide_denoise_multiscale(mdn, storage):
+def test_wide_denoise_multiscale(mdn, storage, prepared):
     h, w, levels = 101, 77, 3
     nb = levels - 1
     banks = [_bank(GEOM, 20 + l, storage) for l in range(nb)]
@@ -144,7 +150,10 @@ def test_wide_denoise_multiscale(mdn, storage):
     ref = O.denoise_multiscale(zs, banks, GEOM, bparams=bps, storage=storage, mirror32=True)
     shapes = [r.shape[1:] for r in ref.pyramid]
     maps = [torch.empty((1, *shapes[l]), dtype=torch.int16, device="cuda") for l in range(nb)]
-    out = mdn.denoise_multiscale(_tt(zs, storage)[None], [_tt(b, storage) for b in banks], _geom(mdn, GEOM),
+    dbanks = [_tt(b, storage) for b in banks]
+    if prepared:
+        dbanks = [mdn.prepare_bank(b, _geom(mdn, GEOM)) for b in dbanks]
+    out = mdn.denoise_multiscale(_tt(zs, storage)[None], dbanks, _geom(mdn, GEOM),
                                  [_gbp(mdn, b) for b in bps], bucket_maps=maps)
     mism = []
     for l in range(nb):
