@@ -403,10 +403,11 @@ int mdn_solve_bank(const double* gram, const int64_t* counts, const mdn_geometry
 /* ------------------------------------------------------------------ */
 
 /* A registered bank set: the filters of one noise level for a `levels`-level
- * pyramid.  Geometry must be 7x7 fine + 7x7 coarse per channel (r_fine = 3,
- * r_coarse = 3, cross_channel = 0); banks are FP16 [K][3][98] device
- * buffers (K <= 256: the server's kernels keep the bank in shared memory)
- * owned by the caller and read for the server's lifetime. */
+ * pyramid, in the server's geometry (mdn_server_cfg.geom: 7x7 fine + 7x7 or
+ * 5x5 coarse taps per channel); banks are FP16 [K][3][D] device buffers,
+ * K <= MDN_MAX_K (the paper's 4096-bucket grid included), owned by the
+ * caller and read for the server's lifetime (the server also keeps a copy
+ * of each in the prepared row-slot layout). */
 typedef struct {
     int32_t levels;                     /* 2..8 */
     const void* const* banks;           /* HOST array of levels-1 device pointers */
@@ -418,8 +419,11 @@ typedef struct {
     int32_t device;              /* CUDA device ordinal */
     size_t hbm_budget_bytes;     /* device memory for request buffers (one arena, allocated at create) */
     int32_t max_active;          /* requests on the device at once (1..256) */
-    int32_t autotune;            /* 1: time the compiled tile shapes at create and keep the fastest */
-    int32_t tile_variant;        /* used when autotune = 0: 0, 1 or 2 (see mdn_server_get_stats) */
+    int32_t autotune;            /* 1: time the level-kernel variants at create and keep the fastest */
+    int32_t tile_variant;        /* used when autotune = 0: 0, 1 or 2 (tile kernels, 7x7 + 7x7 banks of
+                                    at most 256 buckets) or 3 (fused kernel, any bank; the default) */
+    mdn_geometry geom;           /* bank geometry: r_fine 3, r_coarse 3 or 2, cross_channel 0 (color is
+                                    taken from each bank set); all zero = 7x7 + 7x7 */
 } mdn_server_cfg;
 
 typedef struct {
@@ -432,9 +436,10 @@ typedef struct {
     uint64_t submitted, completed, cancelled, ticks, tick_items;
     int32_t active, queued;
     size_t arena_bytes, arena_used, arena_peak;
-    int32_t tile_variant;        /* chosen level-kernel tile shape */
-    float variant_ms[3];         /* autotuner timings (ms, -1 = not measured) */
-    int32_t variant_threads[3], variant_rows[3];   /* threads per CTA, tile rows */
+    int32_t tile_variant;        /* chosen level-kernel variant */
+    float variant_ms[4];         /* autotuner timings (ms, -1 = not measured or not applicable) */
+    int32_t variant_threads[4], variant_rows[4];   /* threads per CTA, tile rows */
+    uint64_t ticks_large;        /* ticks of the large-request class */
 } mdn_server_stats;
 
 typedef struct mdn_server mdn_server;
@@ -448,11 +453,16 @@ int mdn_server_create(const mdn_server_cfg* cfg, const mdn_bankset* sets, int32_
 
 /* Queues one request: host_in and host_out are HOST buffers of [3][h][w]
  * FP16 RGB (pinned memory gives asynchronous copies) that must stay valid
- * until the request's result is polled.  Requests are admitted in FIFO order
- * as arena space and slots free up; each tick advances every admitted
- * request by one stage (upload, pyramid level, filter level, download), all
- * of a tick's stages running in the same two batched launches.  Returns
- * MDN_EBUDGET (nothing queued) if the request alone exceeds the budget. */
+ * until the request's result is polled.  Requests of at least 4 M pixels
+ * (large) run one per tick on two large-class tick contexts; smaller ones
+ * are batched, up to about 4 M pixels a tick, on four small-class contexts
+ * whose compute streams have the highest priority.  Each context has its
+ * own upload, compute and download streams, so small requests never wait in
+ * a stream behind a large one.  Within a class requests are admitted in
+ * FIFO order as arena space and slots free up; a tick runs its requests'
+ * whole chains (upload, pyramid, filter levels, download) in one replay of
+ * the context's graph.  Returns MDN_EBUDGET (nothing queued) if the request
+ * alone exceeds the budget. */
 int mdn_server_submit(mdn_server* srv, const void* host_in, void* host_out, int64_t h, int64_t w, int32_t set,
                       uint64_t* id);
 
@@ -467,7 +477,12 @@ int mdn_server_poll(mdn_server* srv, mdn_result* results, int32_t max, int32_t* 
 int mdn_server_get_stats(mdn_server* srv, mdn_server_stats* st);
 
 /* Stops the scheduler (queued requests are dropped, admitted ones finish
- * first), frees the arena and the graph. */
+ * first), frees the arena and the graph.  With the environment variable
+ * MDN_SERVER_TRACE set to a path when the server was created, writes there a
+ * CSV line per tick: requests, pixels, host launch and retire times (ms since
+ * creation), the device times of its upload, its wait for and run of the
+ * compute stream, its wait for and run of the download stream, and the ids of
+ * its requests. */
 int mdn_server_destroy(mdn_server* srv);
 
 #ifdef __cplusplus

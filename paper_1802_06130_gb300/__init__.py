@@ -111,7 +111,7 @@ def bucket_map_dtype(K: int):
 
 class ServerCfg(C.Structure):
     _fields_ = [("device", C.c_int32), ("hbm_budget_bytes", C.c_size_t), ("max_active", C.c_int32),
-                ("autotune", C.c_int32), ("tile_variant", C.c_int32)]
+                ("autotune", C.c_int32), ("tile_variant", C.c_int32), ("geom", Geometry)]
 
 
 class BankSet(C.Structure):
@@ -128,8 +128,8 @@ class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("cancelled", C.c_uint64),
                 ("ticks", C.c_uint64), ("tick_items", C.c_uint64), ("active", C.c_int32), ("queued", C.c_int32),
                 ("arena_bytes", C.c_size_t), ("arena_used", C.c_size_t), ("arena_peak", C.c_size_t),
-                ("tile_variant", C.c_int32), ("variant_ms", C.c_float * 3), ("variant_threads", C.c_int32 * 3),
-                ("variant_rows", C.c_int32 * 3)]
+                ("tile_variant", C.c_int32), ("variant_ms", C.c_float * 4), ("variant_threads", C.c_int32 * 4),
+                ("variant_rows", C.c_int32 * 4), ("ticks_large", C.c_uint64)]
 
 
 _lib = None
@@ -513,12 +513,14 @@ class Server:
     """Continuous-batching denoise server (mdn_server_*).
 
     bank_sets: list of (banks, bparams) with banks a list of levels-1 FP16
-    [K][3][98] CUDA tensors (7x7 + 7x7 per-channel geometry) and bparams the
-    matching BucketParams list.  Inputs/outputs are host FP16 [3][h][w]
-    tensors (pinned for asynchronous copies) kept alive until polled."""
+    [K][3][D] CUDA tensors in the server's geometry (default 7x7 + 7x7 per
+    channel, D = 98; Geometry(3, 2) for 7x7 + 5x5, D = 74), K up to 4096,
+    and bparams the matching BucketParams list.  Inputs/outputs are host
+    FP16 [3][h][w] tensors (pinned for asynchronous copies) kept alive until
+    polled.  tile_variant (autotune off): 0-2 tile kernels, 3 fused kernel."""
 
     def __init__(self, bank_sets, budget_bytes: int, max_active: int = 16, autotune: bool = True,
-                 tile_variant: int = 1, device: int = 0, color: int = YCBCR601):
+                 tile_variant: int = 3, device: int = 0, color: int = YCBCR601, geom: Geometry = None):
         self._keep = []
         n = len(bank_sets)
         arr = (BankSet * n)()
@@ -532,7 +534,8 @@ class Server:
             arr[i].banks = C.cast(ptrs, C.POINTER(C.c_void_p))
             arr[i].bparams = C.cast(bps, C.POINTER(BucketParams))
             arr[i].color = color
-        cfg = ServerCfg(device, budget_bytes, max_active, int(autotune), tile_variant)
+        cfg = ServerCfg(device, budget_bytes, max_active, int(autotune), tile_variant,
+                        geom if geom is not None else Geometry(3, 3))
         h = C.c_void_p()
         _check(lib().mdn_server_create(C.byref(cfg), arr, n, C.byref(h)))
         self._h = h

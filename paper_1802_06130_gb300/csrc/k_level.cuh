@@ -1058,12 +1058,52 @@ template <int RF, int RC, bool CROSS, typename TB, bool GB = false, int BTB = 1>
     return front_bytes<RC, BTB>() + (GB ? 0 : (size_t)K * bucket_bytes_rows<RF, RC, CROSS, TB>());
 }
 
-template <int RF, int RC, bool CROSS, typename TS, typename TB, bool GB, typename BT>
-__global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, const TS* __restrict__ coarse,
-                                                  TS* __restrict__ out, void* __restrict__ bmap,
-                                                  const TB* __restrict__ bank, int H, int W, int Hc, int Wc,
-                                                  int nimg, int K, int color, SelParams sp, float w0, float w1,
-                                                  float w2, int rows_in) {
+// One TW x TH tile as the kernel sees it: the image it lies in (bases of
+// the [3][H][W] input and output, the [3][Hc][Wc] coarse input, the [H][W]
+// bucket map or null), its origin, and the bank and colour space of its item.
+template <typename TS, typename BT> struct TileRef {
+    const TS* z;
+    const TS* coarse;
+    TS* out;
+    BT* bmap;
+    const unsigned char* bank;   // prepared row slots (bank read through L2), else unused
+    int H, W, Hc, Wc, x0, y0, K, color, item;
+};
+
+// Tile source of a batch of n equal-size images with one bank: tiles in
+// image-major, row-major order.
+template <typename TS, typename BT> struct BatchTiles {
+    const TS* z;
+    const TS* coarse;
+    TS* out;
+    BT* bmap;
+    const unsigned char* bank;
+    int H, W, Hc, Wc, nimg, K, color, tiles_x, tiles_y;
+    SelParams sp;
+    __device__ __forceinline__ int64_t count() const { return (int64_t)tiles_x * tiles_y * nimg; }
+    __device__ __forceinline__ TileRef<TS, BT> at(int64_t tile) const {
+        const int img = (int)(tile / ((int64_t)tiles_x * tiles_y));
+        const int trem = (int)(tile % ((int64_t)tiles_x * tiles_y));
+        TileRef<TS, BT> t;
+        t.z = z + (int64_t)img * 3 * H * W;
+        t.coarse = coarse ? coarse + (int64_t)img * 3 * Hc * Wc : nullptr;
+        t.out = out + (int64_t)img * 3 * H * W;
+        t.bmap = bmap ? bmap + (int64_t)img * H * W : nullptr;
+        t.bank = bank;
+        t.H = H; t.W = W; t.Hc = Hc; t.Wc = Wc;
+        t.x0 = (trem % tiles_x) * TW;
+        t.y0 = (trem / tiles_x) * TH;
+        t.K = mdn_in(img, nimg, 104) ? K : 0;
+        t.color = color;
+        t.item = 0;
+        return t;
+    }
+    __device__ __forceinline__ const SelParams& sel(int) const { return sp; }
+};
+
+template <int RF, int RC, bool CROSS, typename TS, typename TB, bool GB, typename BT, class SRC>
+__global__ void __launch_bounds__(NT, 1) k_level3(const __grid_constant__ SRC src, const TB* __restrict__ bank,
+                                                  float w0, float w1, float w2, int rows_in) {
     using SL = RowSlots<RF, RC, CROSS>;
     constexpr int UW = Coarse<RC>::UW, UH = Coarse<RC>::UH, UWD = Coarse<RC>::UWD;
     constexpr int SB = v2::SlotBytes<TB>::B;
@@ -1072,21 +1112,21 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
     extern __shared__ __align__(16) unsigned char smem[];
     float* ps = reinterpret_cast<float*>(smem + 2 * SBY);   // producer scratch [3][PH][PW]
     float* hs = ps + 3 * PH * PW;                             // [3][PH][TW]
-    unsigned char* bank_s = GB ? (unsigned char*)bank : smem + front_bytes<RC, (int)sizeof(BT)>();
+    unsigned char* bank_sm = smem + front_bytes<RC, (int)sizeof(BT)>();   // bank in shared memory (!GB)
     const int tid = threadIdx.x;
 
     if constexpr (!GB) {
+        const int K = src.K;   // shared-memory banks: batch sources only
         if (rows_in) {   // prepared row slots: a straight 16-byte copy
             for (int i = tid; i < K * BSTRIDE / 16; i += NT)
-                reinterpret_cast<uint4*>(bank_s)[i] = __ldg(reinterpret_cast<const uint4*>(bank) + i);
+                reinterpret_cast<uint4*>(bank_sm)[i] = __ldg(reinterpret_cast<const uint4*>(bank) + i);
         } else {
-            load_bank_rows<RF, RC, CROSS, TB>(bank, K, bank_s, tid, NT);
+            load_bank_rows<RF, RC, CROSS, TB>(bank, K, bank_sm, tid, NT);
         }
     }   // once per persistent CTA
     __syncthreads();
 
-    const int tiles_x = (W + TW - 1) / TW, tiles_y = (H + TH - 1) / TH;
-    const int64_t ntiles = (int64_t)tiles_x * tiles_y * nimg;
+    const int64_t ntiles = src.count();
     const int64_t T = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const int warp = tid >> 5, lane = tid & 31;
 
@@ -1108,16 +1148,15 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
         float zreg[NZ];
         float ureg[NU > 0 ? NU : 1][3];
         // vector loads need 4-element-aligned rows and an aligned image base
-        const bool rows_aligned = (W % 4) == 0 && (reinterpret_cast<uintptr_t>(z) & 15) == 0;
-        auto interior = [&](int x0, int y0) {
-            return rows_aligned && x0 - 4 >= 0 && x0 + TW + 4 <= W && y0 - HZ >= 0 && y0 + TH + HZ <= H;
+        auto interior = [&](const TileRef<TS, BT>& t) {
+            const bool rows_aligned = (t.W % 4) == 0 && (reinterpret_cast<uintptr_t>(t.z) & 15) == 0;
+            return rows_aligned && t.x0 - 4 >= 0 && t.x0 + TW + 4 <= t.W && t.y0 - HZ >= 0 && t.y0 + TH + HZ <= t.H;
         };
         auto fetch = [&](int64_t tile) {
-            const int img = (int)(tile / ((int64_t)tiles_x * tiles_y));
-            const int trem = (int)(tile % ((int64_t)tiles_x * tiles_y));
-            const int x0 = (trem % tiles_x) * TW, y0 = (trem / tiles_x) * TH;
-            const TS* zi = z + (int64_t)img * 3 * H * W;
-            if (interior(x0, y0)) {
+            const TileRef<TS, BT> t = src.at(tile);
+            const int x0 = t.x0, y0 = t.y0, H = t.H, W = t.W, Hc = t.Hc, Wc = t.Wc;
+            const TS* zi = t.z;
+            if (interior(t)) {
 #pragma unroll
                 for (int j = 0; j < NZV; ++j) {
                     const int e = pt + j * NP;
@@ -1135,12 +1174,12 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
                         int c = e / (ZH * ZW), r = (e / ZW) % ZH, q = e % ZW;
                         int gy = clampi(y0 - HZ + r, 0, H - 1), gx = clampi(x0 - HZ + q, 0, W - 1);
                         const int64_t o = ((int64_t)c * H + gy) * W + gx;
-                        zreg[j] = mdn_in(o, 3 * (int64_t)H * W, 103) && mdn_in(img, nimg, 104) ? ld_f(zi, o) : 0.f;
+                        zreg[j] = mdn_in(o, 3 * (int64_t)H * W, 103) && t.K > 0 ? ld_f(zi, o) : 0.f;
                     }
                 }
             }
             if constexpr (RC >= 0) {
-                const TS* ci = coarse + (int64_t)img * 3 * Hc * Wc;
+                const TS* ci = t.coarse;
                 const int cx0 = x0 / 2 - RC, cy0 = y0 / 2 - RC;
 #pragma unroll
                 for (int j = 0; j < NU; ++j) {
@@ -1165,10 +1204,10 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
             float* us = zs + 3 * ZH * ZW;
             BT* bk = reinterpret_cast<BT*>(smem + s * SBY + bk_offset<RC>());
             const int64_t tile = blockIdx.x + i * gridDim.x;
-            const int img = (int)(tile / ((int64_t)tiles_x * tiles_y));
-            const int trem = (int)(tile % ((int64_t)tiles_x * tiles_y));
-            const int x0 = (trem % tiles_x) * TW, y0 = (trem / tiles_x) * TH;
-            const bool inner = interior(x0, y0);
+            const TileRef<TS, BT> t = src.at(tile);
+            const int x0 = t.x0, y0 = t.y0, H = t.H, W = t.W, K = t.K, color = t.color;
+            const SelParams& sp = src.sel(t.item);
+            const bool inner = interior(t);
             if (inner) {
                 // chunk k covers staged columns 4k-1 .. 4k+2 (column -1 and >= ZW dropped)
 #pragma unroll
@@ -1324,11 +1363,11 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
 #pragma unroll
             for (int rr = 0; rr < 4; ++rr) {
                 const int r = 4 * pw + rr;
-                const int k = kk[rr] < K ? kk[rr] : K - 1;
+                const int k = kk[rr] < K ? kk[rr] : (K > 0 ? K - 1 : 0);
                 if (mdn_in(r * TW + lane, TH * TW, 119)) bk[r * TW + lane] = (BT)k;
                 const int gy = y0 + r, gx = x0 + lane;
-                const int64_t mo = ((int64_t)img * H + gy) * W + gx;
-                if (bmap && gy < H && gx < W && mdn_in(mo, (int64_t)nimg * H * W, 120)) static_cast<BT*>(bmap)[mo] = (BT)k;
+                const int64_t mo = (int64_t)gy * W + gx;
+                if (t.bmap && gy < H && gx < W && mdn_in(mo, (int64_t)H * W, 120)) t.bmap[mo] = (BT)k;
             }
             bar_arrive(BAR_FULL0 + s, NT);
         }
@@ -1343,10 +1382,11 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
             const float* us = zs + 3 * ZH * ZW;
             const BT* bk = reinterpret_cast<const BT*>(smem + s * SBY + bk_offset<RC>());
             const int64_t tile = blockIdx.x + i * gridDim.x;
-            const int img = (int)(tile / ((int64_t)tiles_x * tiles_y));
-            const int trem = (int)(tile % ((int64_t)tiles_x * tiles_y));
-            const int x0 = (trem % tiles_x) * TW, y0 = (trem / tiles_x) * TH;
-            TS* oi = out + (int64_t)img * 3 * H * W;
+            const TileRef<TS, BT> t = src.at(tile);
+            const int x0 = t.x0, y0 = t.y0, H = t.H, W = t.W;
+            TS* oi = t.out;
+            const unsigned char* bank_s = GB ? t.bank : bank_sm;
+            const int K = t.K;
 #pragma unroll 1
             for (int pass = 0; pass < TH / 8; ++pass) {
                 const int r = 2 * ((warp >> 1) + 4 * pass) + ro;          // tile row of this group
@@ -1377,9 +1417,9 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
                                                  us + (rr_ / 2) * UW + cc_ / 2, UH * UW, UW, bank_s, kb, j, o);
                 if (pass == TH / 8 - 1 && i + 2 < T) bar_arrive(BAR_EMPTY0 + s, NT);   // stage s no longer read
                 const int gy = y0 + r, gx = x0 + c0 + j;
-                if (gy < H && gx < W && mdn_in((int64_t)img * H * W + (int64_t)gy * W + gx, (int64_t)nimg * H * W, 126)) {
+                if (gy < H && gx < W && mdn_in((int64_t)gy * W + gx, (int64_t)H * W, 126)) {
                     float R, Gc, B;
-                    work_to_rgb(o[0], o[1], o[2], color, R, Gc, B);
+                    work_to_rgb(o[0], o[1], o[2], t.color, R, Gc, B);
                     const int64_t po = (int64_t)gy * W + gx;
                     st_f(oi, po, R);
                     st_f(oi, (int64_t)H * W + po, Gc);
@@ -1392,7 +1432,8 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const TS* __restrict__ z, cons
 
 template <int RF, int RC, bool CROSS, typename TS, typename TB, bool GB = false, typename BT = uint8_t>
 int run3(const LevelArgs& a, cudaStream_t s) {
-    auto kern = k_level3<RF, RC, CROSS, TS, TB, GB, BT>;
+    using SRC = BatchTiles<TS, BT>;
+    auto kern = k_level3<RF, RC, CROSS, TS, TB, GB, BT, SRC>;
     const size_t bytes = smem_need<RF, RC, CROSS, TB, GB, (int)sizeof(BT)>(a.K);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return cuda_fail(e, "k_level3: set smem attribute");
@@ -1405,9 +1446,18 @@ int run3(const LevelArgs& a, cudaStream_t s) {
     if (grid > tiles) grid = tiles;
     float w[5];
     gauss5_weights(w);
-    kern<<<(unsigned)grid, NT, bytes, s>>>((const TS*)a.z, (const TS*)a.coarse, (TS*)a.out, a.buckets,
-                                           (const TB*)a.bank, (int)a.h, (int)a.w, (int)a.hc, (int)a.wc,
-                                           (int)a.n, a.K, a.geom.color, a.sel, w[0], w[1], w[2], a.bank_rows ? 1 : 0);
+    SRC src;
+    src.z = (const TS*)a.z;
+    src.coarse = (const TS*)a.coarse;
+    src.out = (TS*)a.out;
+    src.bmap = (BT*)a.buckets;
+    src.bank = (const unsigned char*)a.bank;
+    src.H = (int)a.h; src.W = (int)a.w; src.Hc = (int)a.hc; src.Wc = (int)a.wc;
+    src.nimg = (int)a.n; src.K = a.K; src.color = a.geom.color;
+    src.tiles_x = (int)((a.w + TW - 1) / TW);
+    src.tiles_y = (int)((a.h + TH - 1) / TH);
+    src.sp = a.sel;
+    kern<<<(unsigned)grid, NT, bytes, s>>>(src, (const TB*)a.bank, w[0], w[1], w[2], a.bank_rows ? 1 : 0);
     return check_launch("k_level3");
 }
 

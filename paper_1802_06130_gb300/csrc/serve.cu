@@ -1,31 +1,40 @@
 // serve.cu -- continuous-batching denoise server (A8): native scheduler,
 // device arena, batched per-stage kernels replayed from CUDA graphs, and a
-// tile-shape autotuner.
+// level-kernel autotuner.
 //
 // A request is upload -> pyramid level 1 .. L-1 -> filter level L-2 .. 0 ->
-// download.  The scheduler thread forms a tick from the requests that are
-// queued when a tick context (stream + device work list + graph) is free and
-// the arena has room: all of the tick's requests run their whole chain in one
-// replay of the context's captured graph, whose nodes are one batched
-// pyramid launch per level and one batched filter launch per level (filter
-// items sorted by bank); every launch is persistent and reads its stage's
-// items from the device work list, so the graph never changes.  Ticks run in
-// FIFO order on one compute stream; an upload stream brings a tick's inputs
-// in while the previous tick computes and a download stream takes its outputs
-// out while the next one computes (events order the three).  Up to NCTX ticks are in flight, so
-// requests that arrive while others are on the GPU are admitted at once into
-// the next tick; a tick stops taking requests at ~4 MP (finest-level pixels)
-// because its requests finish together, so a 12 MP frame does not hold small
-// ones back.  The scheduler polls each in-flight tick's download event
-// and then releases the tick's arena space.  Per-pixel arithmetic is
-// that of the per-image path, so results do not depend on the batch.
+// download.  The scheduler thread forms a tick from queued requests when a
+// tick context (its own upload, compute and download streams, device work
+// list and captured graph) is free and the arena has room: all of the tick's
+// requests run their whole chain in one replay of the context's graph, whose
+// nodes are one batched pyramid launch per level and one batched filter
+// launch per level (filter items sorted by bank); every launch reads its
+// stage's items from the device work list, so the graph never changes.
+//
+// Requests come in two size classes.  Large ones (at least LARGE_PIXELS
+// finest-level pixels, e.g. 12 MP camera frames) run one per tick on the
+// large contexts, whose compute streams have the lowest priority; small
+// ones are batched (up to ~4 MP a tick) on the small contexts, whose compute
+// streams have the highest priority, so their kernels start as soon as SMs
+// free up between a large tick's launches.  Because every context has its own
+// streams, a small tick's upload, kernels and download never queue behind a
+// large tick's in a stream (on Grace hosts a 73 MB copy to or from a pinned
+// buffer the GPU has not used recently can take 10-30x its usual 0.4 ms;
+// with one download stream every later request waited for it).  Within a
+// class, requests are admitted in FIFO order.  The scheduler polls each
+// in-flight tick's download event and then releases the tick's arena space.
+// Per-pixel arithmetic is that of the per-image path, so results do not
+// depend on the batch or the class.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
+#include <string>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -43,10 +52,13 @@ constexpr int MAX_ITEMS = 256;      // requests per tick
 constexpr int MAX_LEVELS = 8;
 constexpr int MAX_STAGE_ITEMS = MAX_ITEMS * (MAX_LEVELS - 1);
 constexpr int MAX_BANKS = 64;
-constexpr int NCTX = 3;             // ticks in flight
-constexpr int64_t TICK_PIXELS = 4200000;   // a tick takes more requests only while under this (finest) size
-constexpr int RF = 3, RC = 3;
+constexpr int NCTX_LARGE = 2, NCTX_SMALL = 4;   // tick contexts per size class
+constexpr int NCTX = NCTX_LARGE + NCTX_SMALL;
+constexpr int64_t TICK_PIXELS = 4200000;    // a small tick takes more requests only while under this (finest) size
+constexpr int64_t LARGE_PIXELS = 4000000;   // requests of at least this many pixels are large
+constexpr int RF = 3, RC = 3;       // geometry of the tile kernels (variants 0-2)
 constexpr bool CROSS = false;
+constexpr int NVAR = 4;             // level-kernel variants: 0-2 tile kernels, 3 the fused kernel
 
 struct PyrItem {
     const __half* in;
@@ -70,6 +82,7 @@ struct WorkList {
 };
 struct Tables {
     const __half* bank[MAX_BANKS];
+    const unsigned char* rows[MAX_BANKS];   // the same banks as prepared row slots (fused kernel)
     int K[MAX_BANKS];
     int color[MAX_BANKS];
     SelParams sel[MAX_BANKS];
@@ -166,15 +179,82 @@ template <class SH> int launch_level(const WorkList* wl, const Tables* tb, int K
     return check_launch("k_serve_level");
 }
 
-int launch_variant(int v, const WorkList* wl, const Tables* tb, int Kmax, int stage, cudaStream_t s) {
+// Tile source of one filter stage of a tick for the fused kernel: the
+// stage's items (requests of any size and bank set, sorted by bank) in the
+// device work list, each item's 32 x 32 tiles row-major after those of the
+// items before it; every tile reads its own item's prepared bank and
+// selector parameters.
+template <typename BT> struct StageTiles {
+    const WorkList* wl;
+    const Tables* tb;
+    int stage;
+    __device__ __forceinline__ int64_t count() const { return wl->lvl_tiles[stage]; }
+    __device__ __forceinline__ lvl::v3::TileRef<__half, BT> at(int64_t tile) const {
+        const int n = wl->lvl_n[stage], b = wl->lvl_begin[stage];
+        int lo = 0, hi = n - 1;   // last item with tile_start <= tile
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (wl->lvl[b + mid].tile_start <= tile) lo = mid; else hi = mid - 1;
+        }
+        const LvlItem& it = wl->lvl[mdn_in(b + lo, MAX_STAGE_ITEMS, 504) ? b + lo : 0];
+        const int bk = mdn_in(it.bank, MAX_BANKS, 505) ? it.bank : 0;
+        const int lt = (int)tile - it.tile_start;
+        lvl::v3::TileRef<__half, BT> t;
+        t.z = it.z;
+        t.coarse = it.coarse;
+        t.out = it.out;
+        t.bmap = nullptr;
+        t.bank = tb->rows[bk];
+        t.H = it.H; t.W = it.W; t.Hc = it.Hc; t.Wc = it.Wc;
+        t.x0 = (lt % it.tiles_x) * lvl::v3::TW;
+        t.y0 = (lt / it.tiles_x) * lvl::v3::TH;
+        t.K = tb->K[bk];
+        t.color = tb->color[bk];
+        t.item = bk;
+        return t;
+    }
+    __device__ __forceinline__ const SelParams& sel(int bk) const { return tb->sel[bk]; }
+};
+
+// the fused warp-specialised level kernel over a stage's work list, banks read through L2
+template <int RF_, int RC_, bool CROSS_, typename BT>
+int launch_fused(const WorkList* wl, const Tables* tb, int stage, cudaStream_t s) {
+    using SRC = StageTiles<BT>;
+    auto kern = lvl::v3::k_level3<RF_, RC_, CROSS_, __half, __half, true, BT, SRC>;
+    const size_t bytes = lvl::v3::smem_need<RF_, RC_, CROSS_, __half, true, (int)sizeof(BT)>(0);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "server: fused level kernel smem attribute");
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, lvl::v3::NT, bytes);
+    if (e != cudaSuccess || occ < 1) return fail(MDN_ESHAPE, "server: fused level kernel does not fit");
+    SRC src{wl, tb, stage};
+    float w[5];
+    gauss5_weights(w);
+    kern<<<num_sms() * occ, lvl::v3::NT, bytes, s>>>(src, nullptr, w[0], w[1], w[2], 1);
+    return check_launch("k_level3 (server)");
+}
+
+// geometry of the server's banks (7x7 + 7x7 or 7x7 + 5x5 per channel) and bucket-index width
+int launch_fused_geom(const mdn_geometry& g, int Kmax, const WorkList* wl, const Tables* tb, int stage,
+                      cudaStream_t s) {
+    if (g.r_fine == 3 && g.r_coarse == 3)
+        return Kmax <= 256 ? launch_fused<3, 3, false, uint8_t>(wl, tb, stage, s)
+                           : launch_fused<3, 3, false, uint16_t>(wl, tb, stage, s);
+    return Kmax <= 256 ? launch_fused<3, 2, false, uint8_t>(wl, tb, stage, s)
+                       : launch_fused<3, 2, false, uint16_t>(wl, tb, stage, s);
+}
+
+int launch_variant(int v, const mdn_geometry& g, const WorkList* wl, const Tables* tb, int Kmax, int stage,
+                   cudaStream_t s) {
     switch (v) {
         case 0: return launch_level<S0>(wl, tb, Kmax, stage, s);
         case 1: return launch_level<S1>(wl, tb, Kmax, stage, s);
-        default: return launch_level<S2>(wl, tb, Kmax, stage, s);
+        case 2: return launch_level<S2>(wl, tb, Kmax, stage, s);
+        default: return launch_fused_geom(g, Kmax, wl, tb, stage, s);
     }
 }
-int variant_threads(int v) { return v == 0 ? S0::NT : v == 1 ? S1::NT : S2::NT; }
-int variant_rows(int v) { return v == 0 ? S0::TH : v == 1 ? S1::TH : S2::TH; }
+int variant_threads(int v) { return v == 0 ? S0::NT : v == 1 ? S1::NT : v == 2 ? S2::NT : lvl::v3::NT; }
+int variant_rows(int v) { return v == 0 ? S0::TH : v == 1 ? S1::TH : v == 2 ? S2::TH : lvl::v3::TH; }
 int variant_tile_rows(int v) { return variant_rows(v); }
 
 // ---------------------------------------------------------------- arena
@@ -265,7 +345,14 @@ using namespace mdn::srv;
 
 struct TickCtx {
     cudaStream_t stream = nullptr;   // capture stream of this context's graph
+    cudaStream_t s_up = nullptr, s_comp = nullptr, s_down = nullptr;
+    bool large = false;              // size class served by this context
     cudaEvent_t ev_up = nullptr, ev_comp = nullptr, ev_done = nullptr;
+    // tracing only (MDN_SERVER_TRACE): starts of the upload, compute and download phases
+    cudaEvent_t ev_t0 = nullptr, ev_cstart = nullptr, ev_dstart = nullptr;
+    double t_launch = 0;
+    int64_t pixels = 0;
+    uint64_t tick_id = 0;
     WorkList* d_wl = nullptr;
     WorkList* h_wl = nullptr;   // pinned staging
     cudaGraph_t graph = nullptr;
@@ -276,16 +363,18 @@ struct TickCtx {
 
 struct mdn_server {
     int device = 0;
-    cudaStream_t s_comp = nullptr, s_up = nullptr, s_down = nullptr;
     char* arena_mem = nullptr;
     Arena arena;
     Tables* d_tb = nullptr;
     TickCtx ctx[NCTX];
     int max_active = 16;
     int max_levels = 2;
-    int variant = 1;
-    float variant_ms[3] = {-1, -1, -1};
+    int variant = 3;
+    float variant_ms[NVAR] = {-1, -1, -1, -1};
     int Kmax = 0;
+    mdn_geometry geom{3, 3, 0, MDN_YCBCR601};   // bank geometry (7x7 + 7x7 or 7x7 + 5x5 per channel)
+    bool tile_ok = true;          // tile kernels (variants 0-2) apply: 7x7 + 7x7 and K <= 256
+    unsigned char* rows_mem = nullptr;   // prepared row slots of every bank
     struct Set {
         int levels;
         int bank_index[8];   // table index of level l's bank
@@ -295,13 +384,16 @@ struct mdn_server {
     std::mutex mu;
     std::condition_variable cv;       // scheduler wake-up: submissions, tick completions, stop
     std::condition_variable cv_done;  // pollers
-    std::deque<Request> queue;
+    std::deque<Request> queue[2];     // [0] small, [1] large requests
     int inflight = 0;
     std::deque<mdn_result> done;
     std::thread thread;
     std::atomic<bool> stop{false};
     std::atomic<int> thread_error{0};
     uint64_t next_id = 1;
+    // per-tick trace (environment variable MDN_SERVER_TRACE = output CSV path)
+    std::string trace_path;
+    std::vector<std::string> trace_rows;
     mdn_server_stats st{};
     std::chrono::steady_clock::time_point t0;
 
@@ -333,9 +425,7 @@ static int build_tables(mdn_server* s, const mdn_bankset* sets, int nsets, Table
             if (rc) return rc;
             tb->bank[nb] = (const __half*)bs.banks[l];
             tb->K[nb] = bs.bparams[l].n_angle * bs.bparams[l].n_strength * bs.bparams[l].n_coherence;
-            if (tb->K[nb] > 256)
-                return fail(MDN_ESHAPE, "server: a bank set level has more than 256 buckets (the serving "
-                                        "kernels hold the bank in shared memory)");
+            if (tb->K[nb] > MDN_MAX_K) return fail(MDN_ESHAPE, "server: a bank set level has more than 4096 buckets");
             tb->color[nb] = bs.color;
             s->Kmax = std::max(s->Kmax, tb->K[nb]);
             st.bank_index[l] = nb++;
@@ -396,22 +486,30 @@ int mdn_server::launch_tick(TickCtx& c) {
     NvtxRange nvtx_range("mdn_server tick");
     build_worklist(this, c.reqs, c.h_wl);
     cudaError_t e = cudaSuccess;
+    const bool tr = !trace_path.empty();
+    c.t_launch = now_ms();
+    c.tick_id = st.ticks;
+    c.pixels = 0;
+    for (auto& r : c.reqs) c.pixels += (int64_t)r.h * r.w;
+    if (tr) e = cudaEventRecord(c.ev_t0, c.s_up);
     // upload stream: inputs (overlapping the previous tick's kernels)
     for (auto& r : c.reqs)
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(r.z[0], r.host_in, (size_t)3 * r.h * r.w * 2, cudaMemcpyHostToDevice, s_up);
-    if (e == cudaSuccess) e = cudaEventRecord(c.ev_up, s_up);
+            e = cudaMemcpyAsync(r.z[0], r.host_in, (size_t)3 * r.h * r.w * 2, cudaMemcpyHostToDevice, c.s_up);
+    if (e == cudaSuccess) e = cudaEventRecord(c.ev_up, c.s_up);
     // compute stream: FIFO ticks
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s_comp, c.ev_up, 0);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(c.d_wl, c.h_wl, sizeof(WorkList), cudaMemcpyHostToDevice, s_comp);
-    if (e == cudaSuccess) e = cudaGraphLaunch(c.gexec, s_comp);
-    if (e == cudaSuccess) e = cudaEventRecord(c.ev_comp, s_comp);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c.s_comp, c.ev_up, 0);
+    if (tr && e == cudaSuccess) e = cudaEventRecord(c.ev_cstart, c.s_comp);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c.d_wl, c.h_wl, sizeof(WorkList), cudaMemcpyHostToDevice, c.s_comp);
+    if (e == cudaSuccess) e = cudaGraphLaunch(c.gexec, c.s_comp);
+    if (e == cudaSuccess) e = cudaEventRecord(c.ev_comp, c.s_comp);
     // download stream: outputs once this tick's kernels are done
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s_down, c.ev_comp, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c.s_down, c.ev_comp, 0);
+    if (tr && e == cudaSuccess) e = cudaEventRecord(c.ev_dstart, c.s_down);
     for (auto& r : c.reqs)
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(r.host_out, r.u[0], (size_t)3 * r.h * r.w * 2, cudaMemcpyDeviceToHost, s_down);
-    if (e == cudaSuccess) e = cudaEventRecord(c.ev_done, s_down);
+            e = cudaMemcpyAsync(r.host_out, r.u[0], (size_t)3 * r.h * r.w * 2, cudaMemcpyDeviceToHost, c.s_down);
+    if (e == cudaSuccess) e = cudaEventRecord(c.ev_done, c.s_down);
     if (e != cudaSuccess) return cuda_fail(e, "server tick");
     return MDN_OK;
 }
@@ -434,6 +532,26 @@ void mdn_server::run() {
                     break;
                 }
                 const double t = now_ms();
+                if (!trace_path.empty()) {
+                    // host ms: launch, retire; device ms: upload, wait for compute, compute,
+                    // wait for download, download; then the tick's request ids
+                    float up = 0, qw = 0, cp = 0, dw = 0, dn = 0;
+                    cudaEventElapsedTime(&up, c.ev_t0, c.ev_up);
+                    cudaEventElapsedTime(&qw, c.ev_up, c.ev_cstart);
+                    cudaEventElapsedTime(&cp, c.ev_cstart, c.ev_comp);
+                    cudaEventElapsedTime(&dw, c.ev_comp, c.ev_dstart);
+                    cudaEventElapsedTime(&dn, c.ev_dstart, c.ev_done);
+                    char line[256];
+                    snprintf(line, sizeof line, "%llu,%zu,%lld,%.3f,%.3f,%.3f,%.3f,%.3f,%.3f,%.3f,",
+                             (unsigned long long)c.tick_id, c.reqs.size(), (long long)c.pixels, c.t_launch, t, up,
+                             qw, cp, dw, dn);
+                    std::string row(line);
+                    for (size_t i = 0; i < c.reqs.size(); ++i) {
+                        snprintf(line, sizeof line, "%s%llu", i ? ";" : "", (unsigned long long)c.reqs[i].id);
+                        row += line;
+                    }
+                    trace_rows.push_back(row);
+                }
                 for (auto& r : c.reqs) {
                     arena.release(r.off, r.bytes);
                     done.push_back(mdn_result{r.id, MDN_OK, r.t_submit, r.t_admit, t});
@@ -447,17 +565,16 @@ void mdn_server::run() {
         }
         if (thread_error.load()) break;
         if (stop.load() && inflight == 0) break;
-        // start a tick on a free context with every queued request that fits
-        TickCtx* free_ctx = nullptr;
-        for (auto& c : ctx)
-            if (!c.busy) { free_ctx = &c; break; }
-        if (free_ctx && !queue.empty() && !stop.load()) {
-            TickCtx& c = *free_ctx;
+        // start a tick on a free context of each class with queued requests of that class
+        bool launched = false;
+        for (auto& c : ctx) {
+            std::deque<Request>& q = queue[c.large ? 1 : 0];
+            if (c.busy || q.empty() || stop.load()) continue;
             int64_t tick_pix = 0;
-            while (!queue.empty() && inflight < max_active && (int)c.reqs.size() < MAX_ITEMS) {
-                Request& r = queue.front();
-                // a batch finishes as one: keep big frames from holding small ones back
-                if (!c.reqs.empty() && tick_pix + (int64_t)r.h * r.w > TICK_PIXELS) break;
+            while (!q.empty() && inflight < max_active && (int)c.reqs.size() < MAX_ITEMS) {
+                Request& r = q.front();
+                // a batch finishes as one: one large request per tick, small ones up to TICK_PIXELS
+                if (!c.reqs.empty() && (c.large || tick_pix + (int64_t)r.h * r.w > TICK_PIXELS)) break;
                 tick_pix += (int64_t)r.h * r.w;
                 size_t off;
                 if (!arena.alloc(r.bytes, &off)) break;
@@ -472,13 +589,14 @@ void mdn_server::run() {
                 }
                 r.t_admit = now_ms();
                 c.reqs.push_back(r);
-                queue.pop_front();
+                q.pop_front();
                 inflight++;
             }
             if (!c.reqs.empty()) {
                 c.busy = true;
                 st.ticks++;
                 st.tick_items += c.reqs.size();
+                if (c.large) st.ticks_large++;
                 lk.unlock();
                 const int rc = launch_tick(c);
                 lk.lock();
@@ -486,9 +604,11 @@ void mdn_server::run() {
                     thread_error = 1;
                     break;
                 }
-                continue;   // look for more work at once
+                launched = true;
             }
         }
+        if (thread_error.load()) break;
+        if (launched) continue;   // look for more work at once
         // ticks in flight: poll their completion events every 20 us; idle:
         // sleep until a submission (or stop) arrives
         if (busy_any)
@@ -516,7 +636,8 @@ static int autotune(mdn_server* s) {
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     float best = 1e30f;
-    for (int v = 0; v < 3 && rc == MDN_OK; ++v) {
+    for (int v = 0; v < NVAR && rc == MDN_OK; ++v) {
+        if (v < 3 && !s->tile_ok) continue;   // tile kernels: 7x7 + 7x7 banks of at most 256 buckets
         s->variant = v;
         WorkList* wl = c.h_wl;
         std::memset(wl, 0, offsetof(WorkList, pyr));
@@ -528,9 +649,10 @@ static int autotune(mdn_server* s) {
         it.tile_start = 0;
         wl->lvl_tiles[0] = it.tiles_x * ((H + variant_rows(v) - 1) / variant_rows(v));
         cudaMemcpyAsync(c.d_wl, wl, sizeof(WorkList), cudaMemcpyHostToDevice, c.stream);
-        rc = launch_variant(v, c.d_wl, s->d_tb, s->Kmax, 0, c.stream);   // warm-up
+        rc = launch_variant(v, s->geom, c.d_wl, s->d_tb, s->Kmax, 0, c.stream);   // warm-up
         cudaEventRecord(a, c.stream);
-        for (int rep = 0; rep < 3 && rc == MDN_OK; ++rep) rc = launch_variant(v, c.d_wl, s->d_tb, s->Kmax, 0, c.stream);
+        for (int rep = 0; rep < 3 && rc == MDN_OK; ++rep)
+            rc = launch_variant(v, s->geom, c.d_wl, s->d_tb, s->Kmax, 0, c.stream);
         cudaEventRecord(b, c.stream);
         cudaEventSynchronize(b);
         float ms = 0.f;
@@ -558,7 +680,7 @@ static int capture_graph(mdn_server* s, TickCtx& c) {
     int rc = MDN_OK;
     for (int l = 1; l < s->max_levels; ++l) k_serve_pyr<<<num_sms() * 4, pyr::PNT, 0, c.stream>>>(c.d_wl, l);
     for (int l = s->max_levels - 2; l >= 0 && rc == MDN_OK; --l)
-        rc = launch_variant(s->variant, c.d_wl, s->d_tb, s->Kmax, l, c.stream);
+        rc = launch_variant(s->variant, s->geom, c.d_wl, s->d_tb, s->Kmax, l, c.stream);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(c.stream, &g);
     if (rc) return rc;
@@ -574,16 +696,17 @@ static void release_server(mdn_server* s) {
         if (c.ev_up) cudaEventDestroy(c.ev_up);
         if (c.ev_comp) cudaEventDestroy(c.ev_comp);
         if (c.ev_done) cudaEventDestroy(c.ev_done);
+        for (cudaEvent_t ev : {c.ev_t0, c.ev_cstart, c.ev_dstart})
+            if (ev) cudaEventDestroy(ev);
         if (c.gexec) cudaGraphExecDestroy(c.gexec);
         if (c.graph) cudaGraphDestroy(c.graph);
         if (c.d_wl) cudaFree(c.d_wl);
         if (c.h_wl) cudaFreeHost(c.h_wl);
-        if (c.stream) cudaStreamDestroy(c.stream);
+        for (cudaStream_t st : {c.stream, c.s_up, c.s_comp, c.s_down})
+            if (st) cudaStreamDestroy(st);
     }
-    if (s->s_comp) cudaStreamDestroy(s->s_comp);
-    if (s->s_up) cudaStreamDestroy(s->s_up);
-    if (s->s_down) cudaStreamDestroy(s->s_down);
     if (s->arena_mem) cudaFree(s->arena_mem);
+    if (s->rows_mem) cudaFree(s->rows_mem);
     if (s->d_tb) cudaFree(s->d_tb);
     delete s;
 }
@@ -594,23 +717,39 @@ int mdn_server_create(const mdn_server_cfg* cfg, const mdn_bankset* sets, int32_
     if (!cfg || !sets || nsets < 1 || !out) return fail(MDN_EINVAL, "server_create: null argument");
     if (cfg->max_active < 1 || cfg->max_active > MAX_ITEMS) return fail(MDN_EINVAL, "server_create: max_active 1..256");
     if (cfg->hbm_budget_bytes < (size_t(1) << 20)) return fail(MDN_EBUDGET, "server_create: budget below 1 MiB");
+    mdn_geometry geom = cfg->geom;
+    if (geom.r_fine == 0) geom = mdn_geometry{3, 3, 0, MDN_YCBCR601};   // default: 7x7 + 7x7 per channel
+    if (geom.r_fine != 3 || (geom.r_coarse != 3 && geom.r_coarse != 2) || geom.cross_channel != 0)
+        return fail(MDN_ESHAPE, "server_create: geometry must be 7x7 + 7x7 or 7x7 + 5x5 per channel");
     mdn_server* s = new (std::nothrow) mdn_server();
     if (!s) return fail(MDN_ENOMEM, "server_create: host allocation");
+    s->geom = geom;
     s->device = cfg->device;
     s->max_active = cfg->max_active;
+    if (const char* tp = getenv("MDN_SERVER_TRACE")) s->trace_path = tp;
+    const unsigned evf = s->trace_path.empty() ? cudaEventDisableTiming : cudaEventDefault;
     s->t0 = std::chrono::steady_clock::now();
     cudaError_t e = cudaSetDevice(cfg->device);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_comp, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_up, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_down, cudaStreamNonBlocking);
+    int prio_low = 0, prio_high = 0;   // numerically: least >= greatest
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
     if (e == cudaSuccess) e = cudaMalloc(&s->arena_mem, cfg->hbm_budget_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_tb, sizeof(Tables));
     for (int i = 0; i < NCTX && e == cudaSuccess; ++i) {
         TickCtx& c = s->ctx[i];
+        c.large = i < NCTX_LARGE;
         e = cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ev_up, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ev_comp, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ev_done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c.s_up, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c.s_down, cudaStreamNonBlocking);
+        if (e == cudaSuccess)
+            e = cudaStreamCreateWithPriority(&c.s_comp, cudaStreamNonBlocking, c.large ? prio_low : prio_high);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ev_up, evf);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ev_comp, evf);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ev_done, evf);
+        if (e == cudaSuccess && !s->trace_path.empty()) {
+            e = cudaEventCreate(&c.ev_t0);
+            if (e == cudaSuccess) e = cudaEventCreate(&c.ev_cstart);
+            if (e == cudaSuccess) e = cudaEventCreate(&c.ev_dstart);
+        }
         if (e == cudaSuccess) e = cudaMalloc(&c.d_wl, sizeof(WorkList));
         if (e == cudaSuccess) e = cudaMallocHost(&c.h_wl, sizeof(WorkList));
         if (e == cudaSuccess) {
@@ -627,11 +766,29 @@ int mdn_server_create(const mdn_server_cfg* cfg, const mdn_bankset* sets, int32_
     s->arena.init(s->arena_mem, cfg->hbm_budget_bytes);
     Tables tb;
     int rc = build_tables(s, sets, nsets, &tb);
+    int nbanks = 0;
+    for (auto& st : s->sets) nbanks += st.levels - 1;
+    // every bank once more as prepared row slots, which the fused kernel reads through L2
+    size_t rows_total = 0;
+    for (int b = 0; b < nbanks && rc == MDN_OK; ++b)
+        rows_total += align256(mdn_bank_rows_bytes(&s->geom, tb.K[b], MDN_F16));
+    if (rc == MDN_OK) {
+        e = cudaMalloc(&s->rows_mem, rows_total);
+        if (e != cudaSuccess) rc = cuda_fail(e, "server_create: prepared banks");
+    }
+    for (size_t b = 0, off = 0; (int)b < nbanks && rc == MDN_OK; ++b) {
+        const size_t nbytes = mdn_bank_rows_bytes(&s->geom, tb.K[b], MDN_F16);
+        rc = mdn_prepare_bank_rows(tb.bank[b], MDN_F16, &s->geom, tb.K[b], s->rows_mem + off, nbytes, nullptr);
+        tb.rows[b] = s->rows_mem + off;
+        off += align256(nbytes);
+    }
     if (rc == MDN_OK) {
         e = cudaMemcpy(s->d_tb, &tb, sizeof(Tables), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) rc = cuda_fail(e, "server_create: tables");
     }
-    s->st.tile_variant = cfg->tile_variant >= 0 && cfg->tile_variant < 3 ? cfg->tile_variant : 1;
+    s->tile_ok = s->geom.r_coarse == RC && s->Kmax <= 256;
+    s->st.tile_variant = cfg->tile_variant >= 0 && cfg->tile_variant < NVAR ? cfg->tile_variant : 3;
+    if (!s->tile_ok) s->st.tile_variant = 3;
     s->variant = s->st.tile_variant;
     if (rc == MDN_OK && cfg->autotune) rc = autotune(s);
     for (int i = 0; i < NCTX && rc == MDN_OK; ++i) rc = capture_graph(s, s->ctx[i]);
@@ -674,7 +831,7 @@ int mdn_server_submit(mdn_server* s, const void* host_in, void* host_out, int64_
         if (s->stop.load()) return fail(MDN_EINVAL, "server_submit: server is stopping");
         r.id = s->next_id++;
         r.t_submit = s->now_ms();
-        s->queue.push_back(r);
+        s->queue[(int64_t)r.h * r.w >= LARGE_PIXELS ? 1 : 0].push_back(r);
         s->st.submitted++;
         *id = r.id;
     }
@@ -685,13 +842,15 @@ int mdn_server_submit(mdn_server* s, const void* host_in, void* host_out, int64_
 int mdn_server_cancel(mdn_server* s, uint64_t id) {
     if (!s) return fail(MDN_EINVAL, "server_cancel: null");
     std::lock_guard<std::mutex> lk(s->mu);
-    for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
-        if (it->id == id) {
-            s->done.push_back(mdn_result{id, MDN_ETIMEOUT, it->t_submit, -1.0, s->now_ms()});
-            s->queue.erase(it);
-            s->st.cancelled++;
-            s->cv_done.notify_all();
-            return MDN_OK;
+    for (auto& q : s->queue) {
+        for (auto it = q.begin(); it != q.end(); ++it) {
+            if (it->id == id) {
+                s->done.push_back(mdn_result{id, MDN_ETIMEOUT, it->t_submit, -1.0, s->now_ms()});
+                q.erase(it);
+                s->st.cancelled++;
+                s->cv_done.notify_all();
+                return MDN_OK;
+            }
         }
     }
     return fail(MDN_EINVAL, "server_cancel: request is not queued");
@@ -718,11 +877,11 @@ int mdn_server_get_stats(mdn_server* s, mdn_server_stats* st) {
     std::lock_guard<std::mutex> lk(s->mu);
     *st = s->st;
     st->active = s->inflight;
-    st->queued = (int)s->queue.size();
+    st->queued = (int)(s->queue[0].size() + s->queue[1].size());
     st->arena_bytes = s->arena.size();
     st->arena_used = s->arena.used();
     st->arena_peak = s->arena.peak();
-    for (int v = 0; v < 3; ++v) {
+    for (int v = 0; v < NVAR; ++v) {
         st->variant_ms[v] = s->variant_ms[v];
         st->variant_threads[v] = variant_threads(v);
         st->variant_rows[v] = variant_rows(v);
@@ -734,12 +893,21 @@ int mdn_server_destroy(mdn_server* s) {
     if (!s) return fail(MDN_EINVAL, "server_destroy: null");
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        s->queue.clear();   // queued requests are dropped; admitted ticks finish
+        s->queue[0].clear();   // queued requests are dropped; admitted ticks finish
+        s->queue[1].clear();
         s->stop = true;
     }
     s->cv.notify_all();
     if (s->thread.joinable()) s->thread.join();
     cudaDeviceSynchronize();
+    if (!s->trace_path.empty()) {
+        if (FILE* f = fopen(s->trace_path.c_str(), "w")) {
+            fprintf(f, "tick,requests,pixels,launch_ms,retire_ms,upload_ms,compute_wait_ms,compute_ms,"
+                       "download_wait_ms,download_ms,ids\n");
+            for (auto& l : s->trace_rows) fprintf(f, "%s\n", l.c_str());
+            fclose(f);
+        }
+    }
     release_server(s);
     return MDN_OK;
 }

@@ -66,7 +66,7 @@ def test_mixed_stream_equals_single_image_path(mdn):
         st = srv.stats()
         assert st["completed"] == len(reqs)
         assert st["tick_items"] > st["ticks"]          # stages of several requests shared ticks
-        assert st["tile_variant"] in (0, 1, 2) and min(st["variant_ms"]) > 0
+        assert st["tile_variant"] in (0, 1, 2, 3) and min(st["variant_ms"]) > 0
     finally:
         srv.close()
 
@@ -123,3 +123,93 @@ def test_cancel_queued_request_and_poll_timeout(mdn):
             srv.cancel(ids[0])                              # already finished
     finally:
         srv.close()
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_every_level_kernel_variant_equals_single_image_path(mdn, variant):
+    """Tile kernels (0-2) and the fused warp-specialised kernel reading
+    prepared banks through L2 (3) give the per-image path's results bit for
+    bit, on sizes with ragged tiles."""
+    sets = [_bank_set(mdn, 3, 11), _bank_set(mdn, 4, 12)]
+    sizes = [(1, 1), (33, 17), (131, 97), (240, 320), (517, 389)]
+    srv = mdn.Server(sets, budget_bytes=256 << 20, max_active=8, autotune=False, tile_variant=variant)
+    try:
+        assert srv.stats()["tile_variant"] == variant
+        io = []
+        for i, (h, w) in enumerate(sizes * 2):
+            x = _frame(h, w, 63000 + i)
+            io.append((x, torch.empty_like(x).pin_memory(), i % 2))
+        reqs = [(srv.submit(x, y, s), x, y, s) for x, y, s in io]
+        got = _drain(srv, len(reqs))
+        assert all(r["status"] == 0 for r in got.values())
+        for rid, x, y, s in reqs:
+            banks, bps = sets[s]
+            ref = mdn.denoise_multiscale(x.cuda()[None], banks, mdn.Geometry(3, 3), bps)[0].cpu()
+            assert torch.equal(y, ref), (variant, rid, tuple(x.shape))
+    finally:
+        srv.close()
+
+
+def test_large_and_small_classes(mdn):
+    """Requests of at least 4 M pixels run one per tick in the large class,
+    smaller ones batched in the small class; all results equal the per-image
+    path's, whatever class or tick they ran in."""
+    sets = [_bank_set(mdn, 3, 13)]
+    sizes = [(2048, 2048), (240, 320), (97, 131), (2001, 2100), (480, 640), (64, 80)]
+    srv = mdn.Server(sets, budget_bytes=1 << 30, max_active=16, autotune=True)
+    try:
+        io = []
+        for i, (h, w) in enumerate(sizes):
+            x = _frame(h, w, 64000 + i)
+            io.append((x, torch.empty_like(x).pin_memory()))
+        reqs = [(srv.submit(x, y, 0), x, y) for x, y in io]
+        got = _drain(srv, len(reqs))
+        assert all(r["status"] == 0 for r in got.values())
+        banks, bps = sets[0]
+        for rid, x, y in reqs:
+            ref = mdn.denoise_multiscale(x.cuda()[None], banks, mdn.Geometry(3, 3), bps)[0].cpu()
+            assert torch.equal(y, ref), tuple(x.shape)
+        st = srv.stats()
+        assert st["ticks_large"] == 2                      # the two frames of >= 4 M pixels, one tick each
+        assert st["ticks"] > st["ticks_large"]
+    finally:
+        srv.close()
+
+
+def test_paper_grid_served_with_prepared_banks(mdn):
+    """The paper's 16 x 16 x 16 grid (4096 buckets) with 7x7 + 5x5 taps:
+    only the fused kernel applies (the tile kernels hold banks of at most
+    256 buckets in shared memory); results equal the per-image path run with
+    the same banks prepared (the same kernel over a batch)."""
+    geom = mdn.Geometry(3, 2)
+    rng = np.random.default_rng(14)
+    banks = []
+    for _ in range(2):
+        b = rng.standard_normal((4096, 3, 74)).astype(np.float32) * 0.03
+        b += (1.0 - b.sum(axis=2, keepdims=True)) / 74
+        banks.append(torch.tensor(b, dtype=torch.float16, device="cuda"))
+    bps = [mdn.paper_grid_bparams(l) for l in range(2)]
+    srv = mdn.Server([(banks, bps)], budget_bytes=512 << 20, max_active=8, autotune=True, geom=geom)
+    try:
+        st = srv.stats()
+        assert st["tile_variant"] == 3 and st["variant_ms"][0] < 0 and st["variant_ms"][3] > 0
+        io = []
+        for i, (h, w) in enumerate([(1, 1), (33, 17), (131, 97), (480, 640), (517, 389)]):
+            x = _frame(h, w, 65000 + i)
+            io.append((x, torch.empty_like(x).pin_memory()))
+        reqs = [(srv.submit(x, y, 0), x, y) for x, y in io]
+        got = _drain(srv, len(reqs))
+        assert all(r["status"] == 0 for r in got.values())
+        prepared = [mdn.prepare_bank(b, geom) for b in banks]
+        for rid, x, y in reqs:
+            ref = mdn.denoise_multiscale(x.cuda()[None], prepared, geom, bps)[0].cpu()
+            assert torch.equal(y, ref), tuple(x.shape)
+    finally:
+        srv.close()
+
+
+def test_server_rejects_uncompiled_geometry(mdn):
+    sets = [_bank_set(mdn, 3, 15)]
+    with pytest.raises(mdn.MdnError) as ei:
+        mdn.Server(sets, budget_bytes=64 << 20, geom=mdn.Geometry(2, -1))
+    assert ei.value.code == 2

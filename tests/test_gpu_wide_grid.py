@@ -212,14 +212,29 @@ def test_wide_train_level_gram_and_bank(mdn, prec):
 
 # ------------------------------------------------------------ A8
 
-def test_server_rejects_wide_bank_sets(mdn):
-    """The serving kernels keep the bank in shared memory: a 4096-bucket set
-    is refused at create with MDN_ESHAPE."""
-    banks = [torch.zeros((K, 3, 98), dtype=torch.float16, device="cuda") for _ in range(2)]
-    with pytest.raises(mdn.MdnError) as ei:
-        mdn.Server([(banks, [mdn.paper_grid_bparams(0), mdn.paper_grid_bparams(1)])], budget_bytes=64 << 20,
-                   autotune=False)
-    assert ei.value.code == 2 and "256 buckets" in str(ei.value)
+def test_server_serves_wide_bank_sets(mdn):
+    """A 4096-bucket set of 7x7 + 7x7 banks is served by the fused kernel
+    reading the server's prepared copy through L2 (the tile kernels, which
+    hold banks of at most 256 buckets in shared memory, are skipped), with
+    the per-image path's results for the same prepared banks."""
+    geom = mdn.Geometry(3, 3)
+    banks = [_tt(_bank(O.Geometry(3, 3), 80 + l, "f16"), "f16") for l in range(2)]
+    bps = [mdn.paper_grid_bparams(0), mdn.paper_grid_bparams(1)]
+    srv = mdn.Server([(banks, bps)], budget_bytes=64 << 20, autotune=False, tile_variant=0)
+    try:
+        assert srv.stats()["tile_variant"] == 3
+        xs = [torch.tensor(synth.noisy_pair(h, w, 8100 + h)[0], dtype=torch.float16).pin_memory()
+              for h, w in [(33, 17), (131, 97)]]
+        ys = [torch.empty_like(x).pin_memory() for x in xs]
+        ids = [srv.submit(x, y, 0) for x, y in zip(xs, ys)]
+        got = set()
+        while len(got) < len(ids):
+            got |= {r["id"] for r in srv.poll(8, 200)}
+        prepared = [mdn.prepare_bank(b, geom) for b in banks]
+        for x, y in zip(xs, ys):
+            assert torch.equal(y, mdn.denoise_multiscale(x.cuda()[None], prepared, geom, bps)[0].cpu())
+    finally:
+        srv.close()
 
 
 # ------------------------------------------------------------ the u8 / u16 boundary
