@@ -461,8 +461,13 @@ int mdn_server_create(const mdn_server_cfg* cfg, const mdn_bankset* sets, int32_
  * a stream behind a large one.  Within a class requests are admitted in
  * FIFO order as arena space and slots free up; a tick runs its requests'
  * whole chains (upload, pyramid, filter levels, download) in one replay of
- * the context's graph.  Returns MDN_EBUDGET (nothing queued) if the request
- * alone exceeds the budget. */
+ * the context's graph.  Pinned (page-locked, mapped) host buffers at 16-byte
+ * aligned addresses are read and written by an SM copy kernel on a few SMs
+ * that the server's compute kernels leave free; other buffers go through the
+ * copy engines.  On Grace hosts the copy engines slow down 10-30x on pinned
+ * buffers the GPU has not used for a second or more, SM copies 2-4x.
+ * Returns MDN_EBUDGET (nothing queued) if the request alone exceeds the
+ * budget. */
 int mdn_server_submit(mdn_server* srv, const void* host_in, void* host_out, int64_t h, int64_t w, int32_t set,
                       uint64_t* id);
 
@@ -482,7 +487,8 @@ int mdn_server_get_stats(mdn_server* srv, mdn_server_stats* st);
  * CSV line per tick: requests, pixels, host launch and retire times (ms since
  * creation), the device times of its upload, its wait for and run of the
  * compute stream, its wait for and run of the download stream, and the ids of
- * its requests. */
+ * its requests.  With MDN_SERVER_COPY_ENGINES=1 at creation, all host
+ * transfers use the copy engines (see mdn_server_submit). */
 int mdn_server_destroy(mdn_server* srv);
 
 #ifdef __cplusplus

@@ -25,6 +25,16 @@
 // in-flight tick's download event and then releases the tick's arena space.
 // Per-pixel arithmetic is that of the per-image path, so results do not
 // depend on the batch or the class.
+//
+// Host transfers are SM copy kernels, not copy-engine copies.  On the Grace
+// host a copy-engine transfer to or from a pinned buffer that the GPU has not
+// used for a second or more runs at ~7-10 GB/s instead of ~190 (7-10 ms for
+// a 12 MP FP16 frame), and serving rotates through many user buffers; SM
+// loads and stores of the same memory overlap their address translations
+// across many warps (1.3-3 ms when cold, the copy engines' speed when hot).
+// The level and pyramid kernels leave COPY_SMS SMs free, which is enough for
+// a copy kernel to run the host link at full speed while they compute.
+// Buffers that are not pinned or not 16-byte aligned use the copy engines.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -59,6 +69,8 @@ constexpr int64_t LARGE_PIXELS = 4000000;   // requests of at least this many pi
 constexpr int RF = 3, RC = 3;       // geometry of the tile kernels (variants 0-2)
 constexpr bool CROSS = false;
 constexpr int NVAR = 4;             // level-kernel variants: 0-2 tile kernels, 3 the fused kernel
+constexpr int COPY_SMS = 8;         // SMs the level and pyramid kernels leave to the host copies
+constexpr int COPY_NT = 256, COPY_BLOCKS = 4 * COPY_SMS;
 
 struct PyrItem {
     const __half* in;
@@ -74,11 +86,19 @@ struct LvlItem {
 // Items of stage l: pyr[pyr_begin[l] .. pyr_begin[l] + pyr_n[l]) builds
 // pyramid level l (1..7); lvl[lvl_begin[l] .. + lvl_n[l]) filters level l
 // (0..6).  tile_start is relative to the stage.
+// one host <-> device transfer of whole 16-byte units (the tail goes by copy engine)
+struct CopyItem {
+    const uint4* src;
+    uint4* dst;
+    int64_t n16;
+};
 struct WorkList {
     int pyr_begin[MAX_LEVELS], pyr_n[MAX_LEVELS], pyr_tiles[MAX_LEVELS];
     int lvl_begin[MAX_LEVELS], lvl_n[MAX_LEVELS], lvl_tiles[MAX_LEVELS];
+    int n_up, n_down;
     PyrItem pyr[MAX_STAGE_ITEMS];
     LvlItem lvl[MAX_STAGE_ITEMS];
+    CopyItem up[MAX_ITEMS], down[MAX_ITEMS];
 };
 struct Tables {
     const __half* bank[MAX_BANKS];
@@ -143,6 +163,28 @@ __global__ void __launch_bounds__(SH::NT, 1) k_serve_level(const WorkList* __res
     }
 }
 
+// A tick's uploads (down = 0) or downloads (down = 1): every item copied by
+// the whole grid, four independent 16-byte loads in flight per thread.
+__global__ void __launch_bounds__(COPY_NT) k_host_copy(const WorkList* __restrict__ wl, int down) {
+    const int n = down ? wl->n_down : wl->n_up;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (int k = 0; k < n; ++k) {
+        const CopyItem it = (down ? wl->down : wl->up)[mdn_in(k, MAX_ITEMS, 506) ? k : 0];
+        const uint4* __restrict__ src = it.src;
+        uint4* __restrict__ dst = it.dst;
+        const size_t m = (size_t)it.n16;
+        size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+        for (; i + 3 * stride < m; i += 4 * stride) {
+            const uint4 a = src[i], b = src[i + stride], c = src[i + 2 * stride], d = src[i + 3 * stride];
+            dst[i] = a;
+            dst[i + stride] = b;
+            dst[i + 2 * stride] = c;
+            dst[i + 3 * stride] = d;
+        }
+        for (; i < m; i += stride) dst[i] = src[i];
+    }
+}
+
 // deterministic structured test pattern for the autotuner (no host data)
 __global__ void k_fill_pattern(__half* p, int H, int W) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -175,7 +217,7 @@ template <class SH> int launch_level(const WorkList* wl, const Tables* tb, int K
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, SH::NT, bytes);
     if (e != cudaSuccess || occ < 1) return fail(MDN_ESHAPE, "server: level kernel does not fit");
-    kern<<<num_sms() * occ, SH::NT, bytes, s>>>(wl, tb, stage);
+    kern<<<(num_sms() - COPY_SMS) * occ, SH::NT, bytes, s>>>(wl, tb, stage);
     return check_launch("k_serve_level");
 }
 
@@ -230,7 +272,7 @@ int launch_fused(const WorkList* wl, const Tables* tb, int stage, cudaStream_t s
     SRC src{wl, tb, stage};
     float w[5];
     gauss5_weights(w);
-    kern<<<num_sms() * occ, lvl::v3::NT, bytes, s>>>(src, nullptr, w[0], w[1], w[2], 1);
+    kern<<<(num_sms() - COPY_SMS) * occ, lvl::v3::NT, bytes, s>>>(src, nullptr, w[0], w[1], w[2], 1);
     return check_launch("k_level3 (server)");
 }
 
@@ -322,6 +364,8 @@ struct Request {
     __half* u[9] = {};   // u[l] = level-l output (u[0] = output)
     int hl[9], wl[9];
     double t_submit = 0, t_admit = 0, t_done = 0;
+    const void* dev_in = nullptr;   // device addresses of pinned, 16-byte aligned host buffers (SM copies),
+    void* dev_out = nullptr;        // else null (copy engines)
 };
 
 size_t request_bytes(int h, int w, int levels) {
@@ -375,6 +419,7 @@ struct mdn_server {
     mdn_geometry geom{3, 3, 0, MDN_YCBCR601};   // bank geometry (7x7 + 7x7 or 7x7 + 5x5 per channel)
     bool tile_ok = true;          // tile kernels (variants 0-2) apply: 7x7 + 7x7 and K <= 256
     unsigned char* rows_mem = nullptr;   // prepared row slots of every bank
+    bool copy_engines = false;           // MDN_SERVER_COPY_ENGINES=1: host transfers by copy engine only
     struct Set {
         int levels;
         int bank_index[8];   // table index of level l's bank
@@ -456,6 +501,12 @@ static void build_worklist(const mdn_server* s, std::vector<Request>& reqs, Work
         wl->pyr_tiles[l] = tiles;
     }
     wl->pyr_begin[0] = wl->pyr_n[0] = wl->pyr_tiles[0] = 0;
+    wl->n_up = wl->n_down = 0;
+    for (auto& r : reqs) {
+        const int64_t n16 = (int64_t)3 * r.h * r.w * 2 / 16;
+        if (r.dev_in) wl->up[wl->n_up++] = CopyItem{(const uint4*)r.dev_in, (uint4*)r.z[0], n16};
+        if (r.dev_out) wl->down[wl->n_down++] = CopyItem{(const uint4*)r.u[0], (uint4*)r.dev_out, n16};
+    }
     for (int l = 0; l < MAX_LEVELS; ++l) {   // filter stages, items sorted by bank
         std::vector<LvlItem> items;
         for (auto& r : reqs) {
@@ -492,23 +543,37 @@ int mdn_server::launch_tick(TickCtx& c) {
     c.pixels = 0;
     for (auto& r : c.reqs) c.pixels += (int64_t)r.h * r.w;
     if (tr) e = cudaEventRecord(c.ev_t0, c.s_up);
-    // upload stream: inputs (overlapping the previous tick's kernels)
-    for (auto& r : c.reqs)
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(r.z[0], r.host_in, (size_t)3 * r.h * r.w * 2, cudaMemcpyHostToDevice, c.s_up);
+    // upload stream: the work list, then the inputs (overlapping other ticks' kernels)
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c.d_wl, c.h_wl, sizeof(WorkList), cudaMemcpyHostToDevice, c.s_up);
+    if (e == cudaSuccess && c.h_wl->n_up) {
+        k_host_copy<<<COPY_BLOCKS, COPY_NT, 0, c.s_up>>>(c.d_wl, 0);
+        e = cudaGetLastError();
+    }
+    for (auto& r : c.reqs) {   // copy-engine transfers: whole buffers, or the tails of the SM copies
+        const size_t bytes = (size_t)3 * r.h * r.w * 2, done16 = r.dev_in ? bytes / 16 * 16 : 0;
+        if (e == cudaSuccess && done16 < bytes)
+            e = cudaMemcpyAsync((char*)r.z[0] + done16, (const char*)r.host_in + done16, bytes - done16,
+                                cudaMemcpyHostToDevice, c.s_up);
+    }
     if (e == cudaSuccess) e = cudaEventRecord(c.ev_up, c.s_up);
-    // compute stream: FIFO ticks
+    // compute stream
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c.s_comp, c.ev_up, 0);
     if (tr && e == cudaSuccess) e = cudaEventRecord(c.ev_cstart, c.s_comp);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(c.d_wl, c.h_wl, sizeof(WorkList), cudaMemcpyHostToDevice, c.s_comp);
     if (e == cudaSuccess) e = cudaGraphLaunch(c.gexec, c.s_comp);
     if (e == cudaSuccess) e = cudaEventRecord(c.ev_comp, c.s_comp);
     // download stream: outputs once this tick's kernels are done
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c.s_down, c.ev_comp, 0);
     if (tr && e == cudaSuccess) e = cudaEventRecord(c.ev_dstart, c.s_down);
-    for (auto& r : c.reqs)
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(r.host_out, r.u[0], (size_t)3 * r.h * r.w * 2, cudaMemcpyDeviceToHost, c.s_down);
+    if (e == cudaSuccess && c.h_wl->n_down) {
+        k_host_copy<<<COPY_BLOCKS, COPY_NT, 0, c.s_down>>>(c.d_wl, 1);
+        e = cudaGetLastError();
+    }
+    for (auto& r : c.reqs) {
+        const size_t bytes = (size_t)3 * r.h * r.w * 2, done16 = r.dev_out ? bytes / 16 * 16 : 0;
+        if (e == cudaSuccess && done16 < bytes)
+            e = cudaMemcpyAsync((char*)r.host_out + done16, (const char*)r.u[0] + done16, bytes - done16,
+                                cudaMemcpyDeviceToHost, c.s_down);
+    }
     if (e == cudaSuccess) e = cudaEventRecord(c.ev_done, c.s_down);
     if (e != cudaSuccess) return cuda_fail(e, "server tick");
     return MDN_OK;
@@ -678,7 +743,7 @@ static int capture_graph(mdn_server* s, TickCtx& c) {
     cudaError_t e = cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "server: begin capture");
     int rc = MDN_OK;
-    for (int l = 1; l < s->max_levels; ++l) k_serve_pyr<<<num_sms() * 4, pyr::PNT, 0, c.stream>>>(c.d_wl, l);
+    for (int l = 1; l < s->max_levels; ++l) k_serve_pyr<<<(num_sms() - COPY_SMS) * 4, pyr::PNT, 0, c.stream>>>(c.d_wl, l);
     for (int l = s->max_levels - 2; l >= 0 && rc == MDN_OK; --l)
         rc = launch_variant(s->variant, s->geom, c.d_wl, s->d_tb, s->Kmax, l, c.stream);
     cudaGraph_t g = nullptr;
@@ -727,6 +792,7 @@ int mdn_server_create(const mdn_server_cfg* cfg, const mdn_bankset* sets, int32_
     s->device = cfg->device;
     s->max_active = cfg->max_active;
     if (const char* tp = getenv("MDN_SERVER_TRACE")) s->trace_path = tp;
+    if (const char* ce = getenv("MDN_SERVER_COPY_ENGINES")) s->copy_engines = ce[0] == '1';
     const unsigned evf = s->trace_path.empty() ? cudaEventDisableTiming : cudaEventDefault;
     s->t0 = std::chrono::steady_clock::now();
     cudaError_t e = cudaSetDevice(cfg->device);
@@ -805,6 +871,18 @@ int mdn_server_create(const mdn_server_cfg* cfg, const mdn_bankset* sets, int32_
     return MDN_OK;
 }
 
+// The device address of a pinned (page-locked, mapped) host buffer if it is
+// 16-byte aligned, else null: such buffers are copied by the SM copy kernel.
+static const void* host_view(const void* p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();   // clear the error: the copy engines take this buffer
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer || (uintptr_t)a.devicePointer % 16) return nullptr;
+    return a.devicePointer;
+}
+
 int mdn_server_submit(mdn_server* s, const void* host_in, void* host_out, int64_t h, int64_t w, int32_t set,
                       uint64_t* id) {
     if (!s || !host_in || !host_out || !id) return fail(MDN_EINVAL, "server_submit: null argument");
@@ -825,6 +903,10 @@ int mdn_server_submit(mdn_server* s, const void* host_in, void* host_out, int64_
         r.wl[l] = (r.wl[l - 1] + 1) / 2;
     }
     r.bytes = request_bytes(r.h, r.w, r.levels);
+    if (!s->copy_engines) {
+        r.dev_in = host_view(host_in);
+        r.dev_out = const_cast<void*>(host_view(host_out));
+    }
     if (r.bytes > s->arena.size()) return fail(MDN_EBUDGET, "server_submit: request exceeds the HBM budget");
     {
         std::lock_guard<std::mutex> lk(s->mu);

@@ -213,3 +213,50 @@ def test_server_rejects_uncompiled_geometry(mdn):
     with pytest.raises(mdn.MdnError) as ei:
         mdn.Server(sets, budget_bytes=64 << 20, geom=mdn.Geometry(2, -1))
     assert ei.value.code == 2
+
+
+@pytest.mark.parametrize("copy_engines", [False, True], ids=["sm_copies", "copy_engines"])
+def test_host_buffer_kinds(mdn, copy_engines, monkeypatch):
+    """Pinned 16-byte aligned host buffers are moved by the SM copy kernel
+    (byte counts that are not a multiple of 16 leave a tail for the copy
+    engines); pageable buffers and pinned ones at an odd offset by the copy
+    engines; MDN_SERVER_COPY_ENGINES=1 sends everything through the copy
+    engines.  Every combination gives the per-image path's results."""
+    if copy_engines:
+        monkeypatch.setenv("MDN_SERVER_COPY_ENGINES", "1")
+    sets = [_bank_set(mdn, 3, 16)]
+    srv = mdn.Server(sets, budget_bytes=256 << 20, max_active=8, autotune=False)
+    monkeypatch.delenv("MDN_SERVER_COPY_ENGINES", raising=False)
+
+    def odd_offset(h, w, seed):
+        base = torch.empty(3 * h * w + 8, dtype=torch.float16).pin_memory()
+        v = base[1:1 + 3 * h * w].view(3, h, w)
+        v.copy_(_frame(h, w, seed))
+        assert v.data_ptr() % 16 != 0
+        return v, base
+
+    try:
+        keep, io = [], []
+        for i, (h, w) in enumerate([(97, 131), (64, 80), (1, 1), (240, 320)]):
+            pinned = _frame(h, w, 66000 + i)
+            pageable = pinned.clone()
+            odd, base = odd_offset(h, w, 66000 + i)
+            keep.append(base)
+            outs = [torch.empty_like(pinned).pin_memory(), torch.empty_like(pinned)]
+            ob = torch.empty(3 * h * w + 8, dtype=torch.float16).pin_memory()
+            keep.append(ob)
+            outs.append(ob[1:1 + 3 * h * w].view(3, h, w))
+            for x in (pinned, pageable, odd):
+                for y in outs:
+                    io.append((x, y))
+        reqs = []
+        for x, y in io:
+            y.zero_()
+            reqs.append((srv.submit(x, y, 0), x, y))
+            got = _drain(srv, 1)                           # one at a time: outputs share buffers
+            assert all(r["status"] == 0 for r in got.values())
+            banks, bps = sets[0]
+            ref = mdn.denoise_multiscale(x.contiguous().cuda()[None], banks, mdn.Geometry(3, 3), bps)[0].cpu()
+            assert torch.equal(y, ref), (tuple(x.shape), x.is_pinned(), x.data_ptr() % 16, y.data_ptr() % 16)
+    finally:
+        srv.close()
