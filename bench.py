@@ -580,13 +580,93 @@ SERVE_SIZES = [(480, 640), (720, 1280), (1080, 1920), (3024, 4032)]
 SERVE_SIGMAS = [15, 25, 50]
 
 
+def _serve_stream(mdn, srv, sets, geom, frames, out_pool, pick, arr, dev):
+    """One Poisson request stream through the server, then through the plain
+    per-image path (one mdn_denoise_multiscale per request, in arrival order,
+    torch copies in and out); latency percentiles and Mpix/s of both."""
+    import threading
+    import torch
+    nreq = len(pick)
+    sizes = list(out_pool)
+    pix = sum(hw[0] * hw[1] for hw, _, _ in pick)
+    # server: submissions at the arrival times, a poller thread (blocking
+    # poll, GIL released in the C call) timestamps completions.  Output
+    # buffers: a LIFO pool of 8 per size (the most recently released host
+    # buffer is reused first; past 8 in flight of one size buffers are shared
+    # round-robin, the bench does not read outputs).
+    lat, inflight, spill = [], {}, {hw: 0 for hw in sizes}
+    free = {hw: list(range(len(out_pool[hw]) - 1, -1, -1)) for hw in sizes}
+    internal, by_size = [], {hw: [] for hw in sizes}
+    lock = threading.Lock()
+    stop = [False]
+
+    def poller():
+        got = 0
+        while got < nreq and not stop[0]:
+            for r in srv.poll(64, 50):
+                t = time.perf_counter() - t0
+                with lock:
+                    a, hw_, bi = inflight.pop(r["id"])
+                    if bi not in free[hw_]:
+                        free[hw_].append(bi)
+                    lat.append((t - a) * 1e3)
+                    by_size[hw_].append((t - a) * 1e3)
+                    internal.append(r["done_ms"] - r["submit_ms"])
+                got += 1
+
+    t0 = time.perf_counter()
+    th = threading.Thread(target=poller)
+    th.start()
+    for i in range(nreq):
+        wait = arr[i] - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        hw, si, f = pick[i]
+        with lock:
+            if free[hw]:
+                bi = free[hw].pop()
+            else:
+                bi = spill[hw] % len(out_pool[hw])
+                spill[hw] += 1
+            rid = srv.submit(frames[hw][f], out_pool[hw][bi], si)
+            inflight[rid] = (arr[i], hw, bi)
+    th.join(timeout=120)
+    stop[0] = True
+    span = time.perf_counter() - t0
+    pct = lambda v, q: round(float(np.percentile(v, q)), 3)
+    srv_line = {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "mpix_s": round(pix / span / 1e6, 1),
+                "internal_p50_ms": pct(internal, 50), "internal_p99_ms": pct(internal, 99),
+                "by_size_p50_p99_ms": {f"{w}x{h}": [pct(v, 50), pct(v, 99)] for (h, w), v in by_size.items() if v}}
+    # plain per-image path, same stream of requests
+    lat_b = []
+    stream = torch.cuda.current_stream()
+    xin = {hw: torch.empty((1, 3, *hw), dtype=torch.float16, device=dev) for hw in sizes}
+    t0 = time.perf_counter()
+    for k in range(nreq):
+        wait = arr[k] - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        hw, si, f = pick[k]
+        banks, bps = sets[si]
+        xin[hw][0].copy_(frames[hw][f], non_blocking=True)
+        y = mdn.denoise_multiscale(xin[hw], banks, geom, bps)
+        out_pool[hw][0].copy_(y[0], non_blocking=True)
+        stream.synchronize()
+        lat_b.append((time.perf_counter() - t0 - arr[k]) * 1e3)
+    span_b = time.perf_counter() - t0
+    return srv_line, {"p50_ms": pct(lat_b, 50), "p99_ms": pct(lat_b, 99), "mpix_s": round(pix / span_b / 1e6, 1)}
+
+
 def run_serving(args, dev):
-    """Poisson request stream (mixed sizes, sigma and level count) through the
-    continuous-batching server and through the plain per-image path (one
-    mdn_denoise_multiscale per request, in arrival order); p50/p99 latency and
-    Mpix/s for both at every rate."""
+    """Poisson request streams (mixed sizes, sigma and level count) through
+    the continuous-batching server and through the plain per-image path;
+    p50/p99 latency and Mpix/s for both at every rate.  Then the paper's
+    16 x 16 x 16 grid (4096 buckets, 7x7 + 5x5 taps) served the same way at
+    one rate (the server reads its prepared banks through L2; the per-image
+    path is given the banks prepared too)."""
     import torch
     import paper_1802_06130_gb300 as mdn
+    import synth
     rng = np.random.default_rng(50000)
     # bank sets: one per (sigma, levels in {3, 4}); random FP16 banks
     sets, set_of = [], {}
@@ -596,11 +676,8 @@ def run_serving(args, dev):
             set_of[(sg, L)] = len(sets)
             sets.append((banks, [mdn.default_bparams(l) for l in range(L - 1)]))
     # two distinct pinned input frames per size
-    import synth
-    frames = {}
-    for (h, w) in SERVE_SIZES:
-        frames[(h, w)] = [torch.tensor(synth.noisy_pair(h, w, 50100 + i + h)[0], dtype=torch.float16).pin_memory()
-                          for i in range(2)]
+    frames = {(h, w): [torch.tensor(synth.noisy_pair(h, w, 50100 + i + h)[0], dtype=torch.float16).pin_memory()
+                       for i in range(2)] for (h, w) in SERVE_SIZES}
     nreq = args.serve_requests
     out_pool = {hw: [torch.empty((3, *hw), dtype=torch.float16).pin_memory() for _ in range(8)] for hw in SERVE_SIZES}
     geom = mdn.Geometry(3, 3)
@@ -610,95 +687,40 @@ def run_serving(args, dev):
     try:
         for rate in args.serve_rates:
             arr = np.cumsum(rng.exponential(1.0 / rate, nreq))
-            pick = [(SERVE_SIZES[rng.integers(4)], SERVE_SIGMAS[rng.integers(3)], int(rng.integers(3, 5)), int(rng.integers(2)))
-                    for _ in range(nreq)]
-            pix = sum(hw[0] * hw[1] for hw, _, _, _ in pick)
-            # ---- server: submissions at the arrival times, a poller thread
-            # (blocking poll, GIL released in the C call) timestamps completions
-            # output buffers: a LIFO pool of 8 per size (the most recently
-            # released host buffer is reused first; past 8 in flight of one size
-            # buffers are shared round-robin, the bench does not read outputs).
-            # Device writes into many distinct pinned buffers in turn (64 per
-            # size) grew the device-to-host copy time up to ~10x over a run on
-            # the Grace host; the per-image path reuses one buffer per size.
-            lat, inflight, spill = [], {}, {hw: 0 for hw in SERVE_SIZES}
-            free = {hw: list(range(len(out_pool[hw]) - 1, -1, -1)) for hw in SERVE_SIZES}
-            internal, by_size = [], {hw: [] for hw in SERVE_SIZES}
-            lock = threading.Lock()
-            stop = [False]
-
-            def poller():
-                got = 0
-                while got < nreq and not stop[0]:
-                    for r in srv.poll(64, 50):
-                        t = time.perf_counter() - t0
-                        with lock:
-                            a, hw_, bi = inflight.pop(r["id"])
-                            if bi not in free[hw_]:
-                                free[hw_].append(bi)
-                            lat.append((t - a) * 1e3)
-                            by_size[hw_].append((t - a) * 1e3)
-                            internal.append(r["done_ms"] - r["submit_ms"])
-                        got += 1
-
-            t0 = time.perf_counter()
-            th = threading.Thread(target=poller)
-            th.start()
-            for i in range(nreq):
-                wait = arr[i] - (time.perf_counter() - t0)
-                if wait > 0:
-                    time.sleep(wait)
-                hw, sg, L, f = pick[i]
-                with lock:
-                    if free[hw]:
-                        bi = free[hw].pop()
-                    else:
-                        bi = spill[hw] % len(out_pool[hw])
-                        spill[hw] += 1
-                    rid = srv.submit(frames[hw][f], out_pool[hw][bi], set_of[(sg, L)])
-                    inflight[rid] = (arr[i], hw, bi)
-            th.join(timeout=120)
-            stop[0] = True
-            span = time.perf_counter() - t0
-            srv_line = {"p50_ms": round(float(np.percentile(lat, 50)), 3),
-                        "p99_ms": round(float(np.percentile(lat, 99)), 3),
-                        "mpix_s": round(pix / span / 1e6, 1),
-                        "internal_p50_ms": round(float(np.percentile(internal, 50)), 3),
-                        "internal_p99_ms": round(float(np.percentile(internal, 99)), 3),
-                        "by_size_p50_p99_ms": {f"{w}x{h}": [round(float(np.percentile(v, 50)), 3),
-                                                            round(float(np.percentile(v, 99)), 3)]
-                                               for (h, w), v in by_size.items() if v}}
-            # ---- plain per-image path, same stream ----
-            lat_b = []
-            stream = torch.cuda.current_stream()
-            xin = {hw: torch.empty((1, 3, *hw), dtype=torch.float16, device=dev) for hw in SERVE_SIZES}
-            t0 = time.perf_counter()
-            for k in range(nreq):
-                wait = arr[k] - (time.perf_counter() - t0)
-                if wait > 0:
-                    time.sleep(wait)
-                hw, sg, L, f = pick[k]
-                banks, bps = sets[set_of[(sg, L)]]
-                xin[hw][0].copy_(frames[hw][f], non_blocking=True)
-                y = mdn.denoise_multiscale(xin[hw], banks, geom, bps)
-                out_pool[hw][0].copy_(y[0], non_blocking=True)
-                stream.synchronize()
-                lat_b.append((time.perf_counter() - t0 - arr[k]) * 1e3)
-            span_b = time.perf_counter() - t0
+            pick = []
+            for _ in range(nreq):
+                hw, sg, L = SERVE_SIZES[rng.integers(4)], SERVE_SIGMAS[rng.integers(3)], int(rng.integers(3, 5))
+                pick.append((hw, set_of[(sg, L)], int(rng.integers(2))))
+            srv_line, img_line = _serve_stream(mdn, srv, sets, geom, frames, out_pool, pick, arr, dev)
             results.append({"rate_rps": rate, "requests": nreq,
                             "label": "saturation sweep (offered load above capacity)" if rate >= 1000 else "offered load",
-                            "server": srv_line,
-                            "per_image": {"p50_ms": round(float(np.percentile(lat_b, 50)), 3),
-                                          "p99_ms": round(float(np.percentile(lat_b, 99)), 3),
-                                          "mpix_s": round(pix / span_b / 1e6, 1)}})
+                            "server": srv_line, "per_image": img_line})
         st = srv.stats()
     finally:
         srv.close()
+    # the paper's grid: 4096 buckets, 7x7 + 5x5 per channel, 3 levels
+    pg = mdn.Geometry(3, 2)
+    pbanks = [torch.tensor(b, dtype=torch.float16, device=dev) for b in random_banks(900, D=74, K=4096, nb=2)]
+    pbps = [mdn.paper_grid_bparams(l) for l in range(2)]
+    psrv = mdn.Server([(pbanks, pbps)], budget_bytes=40 << 30, max_active=64, autotune=True, geom=pg)
+    try:
+        rate, n = args.paper_grid_rate, max(nreq // 2, 1)
+        arr = np.cumsum(rng.exponential(1.0 / rate, n))
+        pick = [(SERVE_SIZES[rng.integers(4)], 0, int(rng.integers(2))) for _ in range(n)]
+        srv_line, img_line = _serve_stream(mdn, psrv, [([mdn.prepare_bank(b, pg) for b in pbanks], pbps)], pg,
+                                           frames, out_pool, pick, arr, dev)
+        paper = {"workload": "the paper's 16x16x16 grid (4096 buckets), 7x7 + 5x5 taps, 3 levels; sizes as above",
+                 "rate_rps": rate, "requests": n, "server": srv_line, "per_image": img_line,
+                 "tile_variant": psrv.stats()["tile_variant"]}
+    finally:
+        psrv.close()
     return {"workload": "Poisson arrivals; sizes uniform over 640x480, 1280x720, 1920x1080, 4032x3024 FP16; "
                         "sigma in {15,25,50}/255 and 3 or 4 levels per request (one bank set each); 80 GB budget; "
-                        "64 slots", "rates": results, "tile_variant": tune["tile_variant"],
+                        "64 slots; host transfers by SM copy kernels (pinned, aligned buffers)",
+            "rates": results, "tile_variant": tune["tile_variant"],
             "autotune_ms": [round(v, 3) for v in tune["variant_ms"]],
-            "mean_stages_per_tick": round(st["tick_items"] / max(st["ticks"], 1), 2)}
+            "mean_stages_per_tick": round(st["tick_items"] / max(st["ticks"], 1), 2),
+            "large_ticks": st["ticks_large"], "paper_grid": paper}
 
 
 # ---------------------------------------------------------------- training
@@ -888,7 +910,7 @@ def serving_subprocess(args):
     host memory) so that the throughput benchmark's allocations do not colour
     its latencies."""
     cmd = [sys.executable, os.path.abspath(__file__), "--serve-only", "--serve-requests", str(args.serve_requests),
-           "--serve-rates", *[str(r) for r in args.serve_rates]]
+           "--serve-rates", *[str(r) for r in args.serve_rates], "--paper-grid-rate", str(args.paper_grid_rate)]
     r = subprocess.run(cmd, capture_output=True, text=True, timeout=1800)
     for ln in r.stdout.splitlines()[::-1]:
         if ln.startswith("{"):
@@ -908,6 +930,7 @@ def main():
     ap.add_argument("--no-serve", dest="serve", action="store_false")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[50, 100, 200, 400, 1600])
+    ap.add_argument("--paper-grid-rate", type=float, default=200, help="request rate of the 4096-bucket serving run")
     ap.add_argument("--serve-only", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-train", dest="train", action="store_false")
     ap.add_argument("--no-variants", dest="variants", action="store_false")
