@@ -738,14 +738,27 @@ def _read(path):
         return header, f.read()
 
 
+def _check_payload(path, raw, nbytes):
+    if len(raw) != nbytes:
+        raise ValueError(f"{path}: payload is {len(raw)} bytes, the header describes {nbytes}")
+
+
 def save_banks(path, banks, geom: Geometry, bparams, sigma=None):
-    """Writes a bank set (one [K][3][D] bank per level) with its geometry,
-    per-level bucket parameters and the noise level it was trained for."""
+    """Writes a bank set (one [K][3][D] FP32 or FP16 bank per level) with its
+    geometry, per-level bucket parameters and the noise level it was trained
+    for; the payload keeps each bank's own precision."""
     import numpy as np
-    arr = [b.detach().float().cpu().numpy().astype("<f4") for b in banks]
+    torch = _torch()
+    arr, dts = [], []
+    for b in banks:
+        if b.dtype not in (torch.float32, torch.float16):
+            raise ValueError(f"save_banks: banks must be float32 or float16, got {b.dtype}")
+        dt = "<f2" if b.dtype == torch.float16 else "<f4"
+        arr.append(b.detach().cpu().numpy().astype(dt))
+        dts.append(dt)
     header = {"format": _CKPT_FORMAT, "kind": "banks", "geometry": _geom_dict(geom),
               "bparams": [_bp_dict(b) for b in bparams], "sigma": sigma,
-              "shapes": [list(a.shape) for a in arr], "dtype": "<f4"}
+              "shapes": [list(a.shape) for a in arr], "dtypes": dts}
     _write(path, header, arr)
 
 
@@ -756,12 +769,16 @@ def load_banks(path, device="cuda"):
     h, raw = _read(path)
     if h["kind"] != "banks":
         raise ValueError(f"{path}: not a bank checkpoint")
+    dts = h.get("dtypes", [h.get("dtype", "<f4")] * len(h["shapes"]))   # older files: one FP32 dtype
+    if len(dts) != len(h["shapes"]) or any(d not in ("<f4", "<f2") for d in dts):
+        raise ValueError(f"{path}: bad bank dtypes {dts}")
+    sizes = [int(np.prod(shp)) * (2 if d == "<f2" else 4) for shp, d in zip(h["shapes"], dts)]
+    _check_payload(path, raw, sum(sizes))
     banks, off = [], 0
-    for shp in h["shapes"]:
-        n = int(np.prod(shp))
-        a = np.frombuffer(raw, dtype="<f4", count=n, offset=off).reshape(shp)
-        off += 4 * n
-        banks.append(torch.tensor(a, dtype=torch.float32, device=device))
+    for shp, d, nb in zip(h["shapes"], dts, sizes):
+        a = np.frombuffer(raw, dtype=d, count=nb // (2 if d == "<f2" else 4), offset=off).reshape(shp)
+        off += nb
+        banks.append(torch.tensor(a, dtype=torch.float16 if d == "<f2" else torch.float32, device=device))
     g = h["geometry"]
     geom = Geometry(g["r_fine"], g["r_coarse"], g["cross_channel"], g["color"])
     return banks, geom, [_bp_from(d) for d in h["bparams"]], h["sigma"]
@@ -785,6 +802,7 @@ def load_gram_state(path, device="cuda"):
     if h["kind"] != "gram":
         raise ValueError(f"{path}: not a Gram checkpoint")
     n = int(np.prod(h["gram_shape"]))
+    _check_payload(path, raw, 8 * n + 8 * int(np.prod(h["counts_shape"])))
     g = np.frombuffer(raw, dtype="<f8", count=n).reshape(h["gram_shape"])
     c = np.frombuffer(raw, dtype="<i8", count=int(np.prod(h["counts_shape"])), offset=8 * n)
     gm = h["geometry"]

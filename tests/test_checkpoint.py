@@ -18,7 +18,7 @@ def test_bank_round_trip(tmp_path):
     mdn.save_banks(p, banks, geom, bps, sigma=25 / 255)
     with open(p, "rb") as f:
         head = json.loads(f.readline())
-    assert head["kind"] == "banks" and head["shapes"] == [[216, 3, 98]] * 2 and head["dtype"] == "<f4"
+    assert head["kind"] == "banks" and head["shapes"] == [[216, 3, 98]] * 2 and head["dtypes"] == ["<f4"] * 2
     b2, g2, bp2, sig = mdn.load_banks(p, device="cpu")
     assert all(torch.equal(a, b) for a, b in zip(banks, b2))
     assert (g2.r_fine, g2.r_coarse, g2.cross_channel, g2.color) == (3, 3, 0, 0)
@@ -61,3 +61,40 @@ def test_paper_grid_bank_round_trip(tmp_path):
         assert b.K == 4096 and (b.n_strength, b.n_coherence) == (16, 16)
         assert list(a.strength_thr) == list(b.strength_thr)
         assert list(a.coherence_thr) == list(b.coherence_thr)
+
+
+def test_fp16_banks_keep_their_precision(tmp_path):
+    geom = mdn.Geometry(3, 3)
+    bps = [mdn.default_bparams(0), mdn.default_bparams(1)]
+    rng = np.random.default_rng(2)
+    banks = [torch.tensor(rng.standard_normal((216, 3, 98)), dtype=torch.float16),
+             torch.tensor(rng.standard_normal((216, 3, 98)), dtype=torch.float32)]
+    p = tmp_path / "mixed.bank"
+    mdn.save_banks(p, banks, geom, bps)
+    b2, _, _, _ = mdn.load_banks(p, device="cpu")
+    assert [b.dtype for b in b2] == [torch.float16, torch.float32]
+    assert all(torch.equal(a, b) for a, b in zip(banks, b2))
+    with pytest.raises(ValueError):
+        mdn.save_banks(tmp_path / "x.bank", [banks[0].double()], geom, bps[:1])
+
+
+def test_payload_length_is_checked(tmp_path):
+    """A truncated file or one with trailing bytes is refused with ValueError,
+    not read short or past its header's shapes."""
+    geom = mdn.Geometry(2, -1)
+    bank = torch.zeros((216, 3, 25), dtype=torch.float32)
+    p = tmp_path / "one.bank"
+    mdn.save_banks(p, [bank], geom, [mdn.default_bparams(0)])
+    data = p.read_bytes()
+    (tmp_path / "short.bank").write_bytes(data[:-4])
+    (tmp_path / "long.bank").write_bytes(data + b"\0" * 8)
+    for name in ("short.bank", "long.bank"):
+        with pytest.raises(ValueError, match="payload"):
+            mdn.load_banks(tmp_path / name, device="cpu")
+    g = torch.zeros((216, 1, 26, 26), dtype=torch.float64)
+    c = torch.zeros(216, dtype=torch.int64)
+    q = tmp_path / "l.gram"
+    mdn.save_gram_state(q, g, c, geom, mdn.default_bparams(0))
+    (tmp_path / "short.gram").write_bytes(q.read_bytes()[:-8])
+    with pytest.raises(ValueError, match="payload"):
+        mdn.load_gram_state(tmp_path / "short.gram", device="cpu")
