@@ -569,9 +569,33 @@ def run_gpu(args, rank, world, frames):
         line["accuracy"] = {"headline": accuracy_headline(mdn, frames[0], random_banks(7), dev)}
         if args.train:
             line["accuracy"]["training_vs_oracle"] = accuracy_training(mdn, dev)
+    if args.autotune and world == 1:
+        line["autotune"] = run_autotune(mdn)
     if args.cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline_block(12, 1)
     print(json.dumps(line), flush=True)
+
+
+def run_autotune(mdn):
+    """The level-kernel autotuner on the metric's configurations (after every
+    timed section; the table is emptied again so that nothing above depends
+    on it): ms per call of each applicable variant and the chosen one, per
+    (geometry, storage, bank type, buckets, size)."""
+    out = []
+    g33, g32 = mdn.Geometry(3, 3), mdn.Geometry(3, 2)
+    for name, geom, bp, dt, bdt, n, h, w in [
+            ("7x7+7x7 216 f16/f16 12MP", g33, mdn.default_bparams(0), mdn.F16, mdn.F16, 1, H, W),
+            ("7x7+7x7 216 f16/f16 1080p", g33, mdn.default_bparams(0), mdn.F16, mdn.F16, 1, 1080, 1920),
+            ("7x7+7x7 216 f16/f16 2016x1512 (level 1)", g33, mdn.default_bparams(1), mdn.F16, mdn.F16, 1,
+             (H + 1) // 2, (W + 1) // 2),
+            ("7x7+7x7 216 f32/f32 12MP", g33, mdn.default_bparams(0), mdn.F32, mdn.F32, 1, H, W),
+            ("7x7+7x7 216 f32/f32-prepared 12MP", g33, mdn.default_bparams(0), mdn.F32, mdn.F32_ROWS, 1, H, W),
+            ("7x7+5x5 4096 f16/f16 12MP", g32, mdn.paper_grid_bparams(0), mdn.F16, mdn.F16, 1, H, W),
+            ("7x7+5x5 4096 f16/f16-prepared 12MP", g32, mdn.paper_grid_bparams(0), mdn.F16, mdn.F16_ROWS, 1, H, W)]:
+        best, ms = mdn.autotune_level(geom, bp, dt, bdt, n, h, w)
+        out.append({"config": name, "chosen": mdn.LEVEL_VARIANTS[best], "ms": ms})
+    mdn.autotune_clear()
+    return out
 
 
 # ---------------------------------------------------------------- serving
@@ -935,6 +959,7 @@ def main():
     ap.add_argument("--no-train", dest="train", action="store_false")
     ap.add_argument("--no-variants", dest="variants", action="store_false")
     ap.add_argument("--no-accuracy", dest="accuracy", action="store_false")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--train-images", type=int, default=256)
     ap.add_argument("--train-only", action="store_true", help="only the training section (profiling driver)")
     ap.add_argument("--quality", action="store_true", help="whole-pipeline PSNR sanity check (configs 1 and 2), then exit")

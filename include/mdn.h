@@ -179,6 +179,42 @@ size_t mdn_bank_rows_bytes(const mdn_geometry* geom, int32_t K, int32_t bank_dty
 int mdn_prepare_bank_rows(const void* bank, int32_t bank_dtype, const mdn_geometry* geom, int32_t K, void* rows,
                           size_t rows_bytes, void* stream);
 
+/* Level-kernel autotuner.  The paper fixes what a level computes, not how;
+ * the library holds several kernels for it (variants, MDN_LV_*), and which
+ * is fastest depends on the geometry, the storage and bank types, the bucket
+ * count and the image size.  mdn_autotune_level times every variant that
+ * applies to such a call on synthetic frames of that size (reps timed calls
+ * each, after one warm-up; it allocates and frees its own device scratch,
+ * so call it at set-up, not inside stream capture), writes the mean ms per
+ * call of each variant to ms[MDN_LEVEL_VARIANTS] (-1 where one does not
+ * apply) and the fastest to *best, and records it in a process-wide table.
+ * mdn_filter_level and the mdn_denoise_multiscale family then use the
+ * table's variant for calls with the same configuration (the entry of the
+ * nearest image-size class when the size differs), and their static rule
+ * otherwise.  Results differ between variants only by FP32 summation order.
+ * mdn_autotune_save / _load write and merge the table as text (lines
+ * "level r_fine r_coarse cross dtype bank_elem prepared K size_class variant
+ * ms" and "server r_fine r_coarse wide variant ms"); the environment
+ * variable MDN_AUTOTUNE_TABLE names a file loaded on first use.  The server
+ * (mdn_server_create) stores its own tuning there and, created without
+ * tuning and with tile_variant -1, uses the table's entry for its geometry
+ * and bank width.  mdn_autotune_lookup / _server_lookup return the recorded
+ * variant (-1: none); mdn_autotune_clear empties the table.  Thread-safe. */
+#define MDN_LV_FUSED_SMEM 0     /* warp-specialised fused kernel, bank in shared memory */
+#define MDN_LV_FUSED_L2 1       /* fused kernel, prepared bank read through L2 */
+#define MDN_LV_STRIP 2          /* strip kernel, bank in shared memory */
+#define MDN_LV_TILE_SMEM 3      /* one pixel per thread, bank in shared memory */
+#define MDN_LV_TILE_L2 4        /* one pixel per thread, taps read through L2 */
+#define MDN_LEVEL_VARIANTS 5
+int mdn_autotune_level(const mdn_geometry* geom, const mdn_bucket_params* bp, int32_t dtype, int32_t bank_dtype,
+                       int64_t n, int64_t h, int64_t w, int32_t reps, int32_t* best, float* ms, void* stream);
+int mdn_autotune_lookup(const mdn_geometry* geom, int32_t K, int32_t dtype, int32_t bank_dtype, int64_t n,
+                        int64_t h, int64_t w);
+int mdn_autotune_server_lookup(const mdn_geometry* geom, int32_t wide);
+int mdn_autotune_save(const char* path);
+int mdn_autotune_load(const char* path);
+void mdn_autotune_clear(void);
+
 /* ------------------------------------------------------------------ */
 /* Multiscale denoising (Section 4)                                    */
 /* ------------------------------------------------------------------ */
@@ -421,7 +457,8 @@ typedef struct {
     int32_t max_active;          /* requests on the device at once (1..256) */
     int32_t autotune;            /* 1: time the level-kernel variants at create and keep the fastest */
     int32_t tile_variant;        /* used when autotune = 0: 0, 1 or 2 (tile kernels, 7x7 + 7x7 banks of
-                                    at most 256 buckets) or 3 (fused kernel, any bank; the default) */
+                                    at most 256 buckets) or 3 (fused kernel, any bank); -1: the
+                                    autotune table's entry, else 3 */
     mdn_geometry geom;           /* bank geometry: r_fine 3, r_coarse 3 or 2, cross_channel 0 (color is
                                     taken from each bank set); all zero = 7x7 + 7x7 */
 } mdn_server_cfg;

@@ -20,7 +20,8 @@ __all__ = ["build", "lib", "Geometry", "BucketParams", "default_bparams", "MdnEr
            "GRAM_BF16", "GRAM_SPLIT_BF16", "augment_dihedral", "dihedral", "estimate_noise", "nearest_level",
            "save_banks", "load_banks", "save_gram_state", "load_gram_state", "paper_grid_bparams",
            "bucket_map_dtype", "MAX_K", "levels_for_sigma", "denoise_multiscale_pipelined", "use_checked_build",
-           "PreparedBank", "prepare_bank", "F16_ROWS", "F32_ROWS",
+           "PreparedBank", "prepare_bank", "F16_ROWS", "F32_ROWS", "LEVEL_VARIANTS", "autotune_level",
+           "autotune_lookup", "autotune_save", "autotune_load", "autotune_clear",
            "check_status", "pyramid_noise_factor", "set_gram_wait_limit",
            "gram_expire_next_wait"]
 
@@ -182,6 +183,13 @@ def lib():
                                                            vp, i64, vp, vp, vp, sz, C.POINTER(vp), i32]),
             "mdn_gram_state_bytes": (sz, [G, i32]),
             "mdn_bank_rows_bytes": (sz, [G, i32, i32]),
+            "mdn_autotune_level": (C.c_int, [G, B, i32, i32, i64, i64, i64, i32, C.POINTER(i32),
+                                             C.POINTER(C.c_float), vp]),
+            "mdn_autotune_lookup": (C.c_int, [G, i32, i32, i32, i64, i64, i64]),
+            "mdn_autotune_server_lookup": (C.c_int, [G, i32]),
+            "mdn_autotune_save": (C.c_int, [C.c_char_p]),
+            "mdn_autotune_load": (C.c_int, [C.c_char_p]),
+            "mdn_autotune_clear": (None, []),
             "mdn_prepare_bank_rows": (C.c_int, [vp, i32, G, i32, vp, sz, vp]),
             "mdn_train_workspace_bytes": (sz, [i64, i64, i64, G, i32, i32]),
             "mdn_train_level_filters": (C.c_int, [vp, vp, vp, i32, i64, i64, i64, G, B, i32, i32, vp, vp,
@@ -273,6 +281,37 @@ def _check_banks(banks, geom: Geometry, bparams):
         if isinstance(b, PreparedBank) and (b.geom != g or b.K != bp.K):
             raise ValueError(f"prepared bank is for geometry {b.geom} with K={b.K}, "
                              f"call has {g} with K={bp.K}")
+
+
+LEVEL_VARIANTS = ("fused_smem", "fused_l2", "strip", "tile_smem", "tile_l2")
+
+
+def autotune_level(geom: Geometry, bp: BucketParams, dtype: int, bank_dtype: int, n: int, h: int, w: int,
+                   reps: int = 3, stream=None):
+    """Times every level-kernel variant that applies to this configuration
+    (mdn_autotune_level) and records the fastest in the autotune table, which
+    the level calls then follow.  -> (best variant index, {name: ms or None})."""
+    best = C.c_int32(-1)
+    ms = (C.c_float * len(LEVEL_VARIANTS))()
+    _check(lib().mdn_autotune_level(C.byref(geom), C.byref(bp), dtype, bank_dtype, n, h, w, reps, C.byref(best), ms,
+                                    _stream(stream)))
+    return best.value, {name: (round(ms[i], 5) if ms[i] >= 0 else None) for i, name in enumerate(LEVEL_VARIANTS)}
+
+
+def autotune_lookup(geom: Geometry, K: int, dtype: int, bank_dtype: int, n: int, h: int, w: int) -> int:
+    return lib().mdn_autotune_lookup(C.byref(geom), K, dtype, bank_dtype, n, h, w)
+
+
+def autotune_save(path):
+    _check(lib().mdn_autotune_save(str(path).encode()))
+
+
+def autotune_load(path):
+    _check(lib().mdn_autotune_load(str(path).encode()))
+
+
+def autotune_clear():
+    lib().mdn_autotune_clear()
 
 
 def _bank_code(b) -> int:
@@ -517,10 +556,11 @@ class Server:
     channel, D = 98; Geometry(3, 2) for 7x7 + 5x5, D = 74), K up to 4096,
     and bparams the matching BucketParams list.  Inputs/outputs are host
     FP16 [3][h][w] tensors (pinned for asynchronous copies) kept alive until
-    polled.  tile_variant (autotune off): 0-2 tile kernels, 3 fused kernel."""
+    polled.  tile_variant (autotune off): 0-2 tile kernels, 3 fused kernel,
+    -1 the autotune table's entry (else 3)."""
 
     def __init__(self, bank_sets, budget_bytes: int, max_active: int = 16, autotune: bool = True,
-                 tile_variant: int = 3, device: int = 0, color: int = YCBCR601, geom: Geometry = None):
+                 tile_variant: int = -1, device: int = 0, color: int = YCBCR601, geom: Geometry = None):
         self._keep = []
         n = len(bank_sets)
         arr = (BankSet * n)()

@@ -220,7 +220,7 @@ int mdn_filter_level(const void* z, const void* coarse, int32_t dtype, int64_t n
     if ((rc = make_sel_params(bp, &a.sel))) return rc;
     a.z = z; a.coarse = geom->r_coarse >= 0 ? coarse : nullptr; a.out = out; a.buckets = buckets_out;
     a.bank = bank; a.n = n; a.h = h; a.w = w; a.hc = (h + 1) / 2; a.wc = (w + 1) / 2;
-    a.dtype = dtype; a.bank_dtype = bank_elem; a.bank_rows = bank_rows;
+    a.dtype = dtype; a.bank_dtype = bank_elem; a.bank_rows = bank_rows; a.variant = g_force_variant;
     a.K = bp->n_angle * bp->n_strength * bp->n_coherence;
     a.geom = *geom;
     return launch_level(a, (cudaStream_t)stream);
@@ -294,7 +294,7 @@ int mdn_denoise_multiscale(const void* noisy, int32_t dtype, int64_t n, int64_t 
         a.z = zl[l]; a.coarse = coarse; a.out = ul[l];
         a.buckets = bucket_maps ? bucket_maps[l] : nullptr;
         a.bank = banks[l]; a.n = n; a.h = hl[l]; a.w = wl[l]; a.hc = (hl[l] + 1) / 2; a.wc = (wl[l] + 1) / 2;
-        a.dtype = dtype; a.bank_dtype = bank_elem; a.bank_rows = bank_rows;
+        a.dtype = dtype; a.bank_dtype = bank_elem; a.bank_rows = bank_rows; a.variant = g_force_variant; a.variant = g_force_variant;
         a.K = bparams[l].n_angle * bparams[l].n_strength * bparams[l].n_coherence;
         a.geom = *geom;
         NvtxRange r(l == 0 ? "level 0" : l == 1 ? "level 1" : l == 2 ? "level 2" : "level 3+");

@@ -61,8 +61,27 @@ struct LevelArgs {
     int K;
     mdn_geometry geom;
     SelParams sel;
+    int variant = -1;        // level-kernel variant (LV_*), -1: autotune table, else the static rule
 };
 int launch_level(const LevelArgs& a, cudaStream_t s);
+
+// Level-kernel variants of the per-image path (mdn_autotune_level times them).
+enum LevelVariant {
+    LV_FUSED_SMEM = 0,   // warp-specialised fused kernel, bank in shared memory (K <= 256, if it fits)
+    LV_FUSED_L2 = 1,     // fused kernel reading a prepared bank through L2
+    LV_STRIP = 2,        // strip kernel, bank in shared memory (K <= 256, if it fits)
+    LV_TILE_SMEM = 3,    // one pixel per thread, bank in shared memory (if it fits)
+    LV_TILE_L2 = 4,      // one pixel per thread, taps read through L2
+    LV_COUNT = 5
+};
+// Autotune table (tune.cu): the variant recorded for this call's geometry,
+// storage / bank types, K and image-size class, or -1.  Thread-safe.
+int tune_lookup(const LevelArgs& a);
+// Server entries: the level-kernel variant for a server geometry and bank width, or -1.
+int tune_server_lookup(const mdn_geometry& g, bool wide);
+void tune_server_store(const mdn_geometry& g, bool wide, int variant, float ms);
+// variant forced on the calling thread's level calls (the tuner), -1 = none
+extern thread_local int g_force_variant;
 int launch_pyramid_down(const void* in, void* out, int dtype, int64_t n, int64_t h, int64_t w,
                         cudaStream_t s);
 

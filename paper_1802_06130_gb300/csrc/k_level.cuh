@@ -1468,30 +1468,62 @@ int run3(const LevelArgs& a, cudaStream_t s) {
 #define MDN_USE_V3 1
 #endif
 
-// Geometry dispatch for one (storage, bank) type pair.  Plain banks
-// ([K][3][D]): the fused kernel with the bank in shared memory when it fits,
-// else the strip or tile kernels.  Prepared banks (row slots,
-// mdn_prepare_bank_rows): the fused kernel, with the bank copied to shared
-// memory when it fits and read through L2 otherwise.
+// Whether level-kernel variant v applies to this call.
+template <int RF, int RC, bool CROSS, typename TB> bool variant_ok(const LevelArgs& a, int v) {
+    const bool small = a.K <= 256;
+    switch (v) {
+        case LV_FUSED_SMEM: return small && v3::smem_need<RF, RC, CROSS, TB>(a.K) <= SMEM_LIMIT;
+        case LV_FUSED_L2: return a.bank_rows;
+        case LV_STRIP: return !a.bank_rows && small && v2::smem_need<RF, RC, CROSS, TB>(a.K) <= SMEM_LIMIT;
+        case LV_TILE_SMEM: return !a.bank_rows && smem_need<RF, RC, CROSS, TB>(a.K) <= SMEM_LIMIT;
+        case LV_TILE_L2: return !a.bank_rows;
+        default: return false;
+    }
+}
+
+template <int RF, int RC, bool CROSS, typename TS, typename TB>
+int run_variant(const LevelArgs& a, int v, cudaStream_t s) {
+    switch (v) {
+        case LV_FUSED_SMEM: return v3::run3<RF, RC, CROSS, TS, TB, false, uint8_t>(a, s);   // plain or prepared bank
+        case LV_FUSED_L2:
+            return a.K <= 256 ? v3::run3<RF, RC, CROSS, TS, TB, true, uint8_t>(a, s)
+                              : v3::run3<RF, RC, CROSS, TS, TB, true, uint16_t>(a, s);
+        case LV_STRIP: return v2::run2<RF, RC, CROSS, TS, TB>(a, s);
+        case LV_TILE_SMEM: return run<RF, RC, CROSS, TS, TB, true, true>(a, s);
+        default: return run<RF, RC, CROSS, TS, TB, false, true>(a, s);
+    }
+}
+
+// One compiled geometry: the forced variant (the tuner), else the autotune
+// table's entry, else the static rule.  Plain banks ([K][3][D]): the fused
+// kernel with the bank in shared memory when it fits, else the strip or tile
+// kernels.  Prepared banks (row slots, mdn_prepare_bank_rows): the fused
+// kernel, with the bank copied to shared memory when it fits and read
+// through L2 otherwise.
+template <int RF, int RC, bool CROSS, typename TS, typename TB>
+int dispatch_geo(const LevelArgs& a, cudaStream_t s) {
+    if (a.variant >= 0) {
+        if (!variant_ok<RF, RC, CROSS, TB>(a, a.variant))
+            return fail(MDN_ESHAPE, "filter_level: this level-kernel variant does not apply to the call");
+        return run_variant<RF, RC, CROSS, TS, TB>(a, a.variant, s);
+    }
+    const int t = tune_lookup(a);
+    if (t >= 0 && variant_ok<RF, RC, CROSS, TB>(a, t)) return run_variant<RF, RC, CROSS, TS, TB>(a, t, s);
+    if (a.bank_rows)
+        return run_variant<RF, RC, CROSS, TS, TB>(
+            a, variant_ok<RF, RC, CROSS, TB>(a, LV_FUSED_SMEM) ? LV_FUSED_SMEM : LV_FUSED_L2, s);
+    for (int v : {LV_FUSED_SMEM, LV_STRIP, LV_TILE_SMEM})
+        if ((v != LV_FUSED_SMEM || MDN_USE_V3) && variant_ok<RF, RC, CROSS, TB>(a, v))
+            return run_variant<RF, RC, CROSS, TS, TB>(a, v, s);
+    return run_variant<RF, RC, CROSS, TS, TB>(a, LV_TILE_L2, s);
+}
+
+// Geometry dispatch for one (storage, bank) type pair.
 template <typename TS, typename TB> int dispatch(const LevelArgs& a, cudaStream_t s) {
     const mdn_geometry& g = a.geom;
-    const bool rows = a.bank_rows;
-#define MDN_GEO(RF_, RC_, CR_)                                                                  \
-    if (rows && g.r_fine == RF_ && g.r_coarse == RC_ && (g.cross_channel != 0) == CR_) {        \
-        if (a.K <= 256 && v3::smem_need<RF_, RC_, CR_, TB>(a.K) <= SMEM_LIMIT)                \
-            return v3::run3<RF_, RC_, CR_, TS, TB, false, uint8_t>(a, s);                     \
-        if (a.K <= 256) return v3::run3<RF_, RC_, CR_, TS, TB, true, uint8_t>(a, s);          \
-        return v3::run3<RF_, RC_, CR_, TS, TB, true, uint16_t>(a, s);                         \
-    }                                                                                           \
-    if (g.r_fine == RF_ && g.r_coarse == RC_ && (g.cross_channel != 0) == CR_) {                \
-        if (MDN_USE_V3 && a.K <= 256 && v3::smem_need<RF_, RC_, CR_, TB>(a.K) <= SMEM_LIMIT)  \
-            return v3::run3<RF_, RC_, CR_, TS, TB>(a, s);                                      \
-        if (a.K <= 256 && v2::smem_need<RF_, RC_, CR_, TB>(a.K) <= SMEM_LIMIT)                \
-            return v2::run2<RF_, RC_, CR_, TS, TB>(a, s);                                      \
-        if (smem_need<RF_, RC_, CR_, TB>(a.K) <= SMEM_LIMIT)                                  \
-            return run<RF_, RC_, CR_, TS, TB, true, true>(a, s);                              \
-        return run<RF_, RC_, CR_, TS, TB, false, true>(a, s);                                 \
-    }
+#define MDN_GEO(RF_, RC_, CR_)                                                   \
+    if (g.r_fine == RF_ && g.r_coarse == RC_ && (g.cross_channel != 0) == CR_) \
+        return dispatch_geo<RF_, RC_, CR_, TS, TB>(a, s);
     MDN_GEO(2, -1, false)
     MDN_GEO(3, 3, false)
     MDN_GEO(3, 2, false)

@@ -853,10 +853,17 @@ int mdn_server_create(const mdn_server_cfg* cfg, const mdn_bankset* sets, int32_
         if (e != cudaSuccess) rc = cuda_fail(e, "server_create: tables");
     }
     s->tile_ok = s->geom.r_coarse == RC && s->Kmax <= 256;
-    s->st.tile_variant = cfg->tile_variant >= 0 && cfg->tile_variant < NVAR ? cfg->tile_variant : 3;
-    if (!s->tile_ok) s->st.tile_variant = 3;
+    int tv = cfg->tile_variant;
+    if (tv < 0 || tv >= NVAR) {   // the autotune table's entry for this geometry and bank width, else the fused kernel
+        tv = tune_server_lookup(s->geom, s->Kmax > 256);
+        if (tv < 0) tv = 3;
+    }
+    s->st.tile_variant = s->tile_ok ? tv : 3;
     s->variant = s->st.tile_variant;
-    if (rc == MDN_OK && cfg->autotune) rc = autotune(s);
+    if (rc == MDN_OK && cfg->autotune) {
+        rc = autotune(s);
+        if (rc == MDN_OK) tune_server_store(s->geom, s->Kmax > 256, s->variant, s->variant_ms[s->variant]);
+    }
     for (int i = 0; i < NCTX && rc == MDN_OK; ++i) rc = capture_graph(s, s->ctx[i]);
     if (rc == MDN_OK) {
         e = cudaDeviceSynchronize();

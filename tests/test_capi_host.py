@@ -287,3 +287,51 @@ def test_prepared_bank_layout_sizes_and_checks(L):
     assert f(C.c_void_p(256), mdn.F16, g, 216, C.c_void_p(256), need - 16, None) == 3
     assert f(C.c_void_p(256), mdn.F16, g, 216, C.c_void_p(264), need, None) == 1
     assert b"16-byte" in L.mdn_last_error()
+
+
+def test_autotune_table_host(L, tmp_path):
+    """The autotune table without a device: load, exact and nearest-size
+    lookups, server entries, save / reload, malformed files, clear; the tuner
+    rejects bad arguments before touching the device."""
+    try:
+        L.mdn_autotune_clear()
+        g = mdn.Geometry(3, 3)
+        # level r_fine r_coarse cross dtype bank_elem prepared K size_class variant ms
+        p = tmp_path / "t.txt"
+        p.write_text("# a comment\n"
+                     "level 3 3 0 1 1 0 216 20 2 0.5\n"
+                     "level 3 3 0 1 1 0 216 24 3 1.5\n"
+                     "level 3 2 0 1 1 1 4096 23 1 0.9\n"
+                     "server 3 3 0 1 0.2\n")
+        assert L.mdn_autotune_load(str(p).encode()) == 0
+        f = L.mdn_autotune_lookup
+        assert f(C.byref(g), 216, mdn.F16, mdn.F16, 1, 1024, 1024) == 2      # 2^20 pixels: exact class
+        assert f(C.byref(g), 216, mdn.F16, mdn.F16, 8, 3024, 4032) == 3      # 2^26.5: nearest class 24
+        assert f(C.byref(g), 216, mdn.F16, mdn.F32, 1, 1024, 1024) == -1     # other bank type: no entry
+        assert f(C.byref(mdn.Geometry(3, 2)), 4096, mdn.F16, mdn.F16_ROWS, 1, 3024, 4032) == 1
+        assert L.mdn_autotune_server_lookup(C.byref(g), 0) == 1
+        assert L.mdn_autotune_server_lookup(C.byref(g), 1) == -1
+        q = tmp_path / "saved.txt"
+        assert L.mdn_autotune_save(str(q).encode()) == 0
+        L.mdn_autotune_clear()
+        assert f(C.byref(g), 216, mdn.F16, mdn.F16, 1, 1024, 1024) == -1
+        assert L.mdn_autotune_load(str(q).encode()) == 0
+        assert f(C.byref(g), 216, mdn.F16, mdn.F16, 1, 1024, 1024) == 2
+        assert L.mdn_autotune_server_lookup(C.byref(g), 0) == 1
+        bad = tmp_path / "bad.txt"
+        bad.write_text("level 3 3 0 1 1 0 216 20 9 0.5\nnonsense\n")     # variant 9 does not exist
+        assert L.mdn_autotune_load(str(bad).encode()) == 1
+        assert L.mdn_autotune_load(str(tmp_path / "missing.txt").encode()) == 1
+        best = C.c_int32()
+        ms = (C.c_float * 5)()
+        bp = mdn.default_bparams(0)
+        t = L.mdn_autotune_level
+        assert t(None, C.byref(bp), mdn.F16, mdn.F16, 1, 64, 64, 3, C.byref(best), ms, None) == 1
+        assert t(C.byref(g), C.byref(bp), 7, mdn.F16, 1, 64, 64, 3, C.byref(best), ms, None) == 1
+        assert t(C.byref(g), C.byref(bp), mdn.F16, mdn.F16, 1, 64, 64, 0, C.byref(best), ms, None) == 1
+        assert t(C.byref(g), C.byref(bp), mdn.F16, 9, 1, 64, 64, 3, C.byref(best), ms, None) == 1
+        assert t(C.byref(g), C.byref(bp), mdn.F16, mdn.F16, 1, 0, 64, 3, C.byref(best), ms, None) == 2
+        assert t(C.byref(mdn.Geometry(1, -1)), C.byref(bp), mdn.F16, mdn.F16, 1, 64, 64, 3, C.byref(best), ms,
+                 None) == 2
+    finally:
+        L.mdn_autotune_clear()
