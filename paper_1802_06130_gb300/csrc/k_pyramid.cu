@@ -7,11 +7,18 @@
 // then out = b0*H_0, fma(b1,H_1) ... fma(b4,H_4); finally rounded to the
 // storage type (RN-even for FP16).  b = [1 4 6 4 1]/16 is exact in FP32.
 //
-// Tiling: a CTA makes a 64x16 output tile of one channel; the 131x35 input
-// window (clamped coordinates) is staged in shared memory with coalesced,
-// register-batched loads, the horizontal pass writes 35x64 row sums to shared
-// memory and the vertical pass produces the outputs.  HBM-bound: each input
-// element is read once from DRAM (neighbouring tiles' halos hit L2).
+// Tiling: 64x32 output tiles of one channel.  Images whose rows start on
+// 16-byte boundaries (W a multiple of 8 for FP16, 4 for FP32, aligned base)
+// go to the persistent kernel k_pyramid_fast: each CTA walks its tiles with
+// the next tile's window already loading into registers (16-byte vectors,
+// rows clamped, vectors outside a row replaced by its edge element) while
+// the current one is computed from shared memory (even / odd column rows,
+// per-thread output columns with the vertical window in registers; see
+// pyramid.cuh), so DRAM latency overlaps the arithmetic.  Other images go to
+// k_pyramid_down, which stages the clamped 131x35 windows of the two 64x16
+// halves with scalar loads.  Both give the same FP32 chains on the same
+// clamped values, so every tile is bit-identical to the oracle's order.  Each input element is read once from DRAM (neighbouring
+// tiles' halos hit L2).
 #include "common.cuh"
 #include "internal.h"
 #include "pyramid.cuh"
@@ -19,29 +26,93 @@
 namespace mdn {
 namespace {
 
+// Every tile of every plane (ntx x nty per plane), persistent CTAs, one
+// tile's window prefetched into registers.
 template <typename TS>
-__global__ void __launch_bounds__(pyr::PNT) k_pyramid_down(const TS* __restrict__ in, TS* __restrict__ out, int H,
+__global__ void __launch_bounds__(pyr::FNT, sizeof(TS) == 2 ? 4 : 3)
+    k_pyramid_fast(const TS* __restrict__ in, TS* __restrict__ out, int H, int W, int Ho, int Wo, int nplanes,
+                   int ntx, int nty) {
+    using F = pyr::Fast<TS>;
+    __shared__ __align__(16) float sm[F::SMEM_FLOATS];
+    const int64_t per_plane = (int64_t)ntx * nty, ntiles = per_plane * nplanes;
+    // ix0 = 128 tx - 2 and xa = floor(ix0 / VE) VE = 128 tx - VE, so (ix0 - xa) / 2 is the same for all tiles
+    constexpr int O2 = (F::VE - 2) / 2;
+    auto where = [&](int64_t t, const TS*& src, TS*& dst, int& ox0, int& oy0) {
+        const int plane = (int)(t / per_plane), rem = (int)(t - (int64_t)plane * per_plane);
+        const int tx = rem % ntx, ty = rem / ntx;
+        src = in + (int64_t)plane * H * W;
+        dst = out + (int64_t)plane * Ho * Wo;
+        ox0 = tx * pyr::PTX;
+        oy0 = ty * pyr::FTY;
+    };
+    uint4 v[F::NLD];
+    int64_t t = blockIdx.x;
+    if (t < ntiles) {
+        const TS* src; TS* dst; int ox0, oy0;
+        where(t, src, dst, ox0, oy0);
+        pyr::fast_fetch<TS>(src, H, W, 2 * oy0 - 2, 2 * ox0 - F::VE, v);
+    }
+    for (; t < ntiles; t += gridDim.x) {
+        const TS* src; TS* dst; int ox0, oy0;
+        where(t, src, dst, ox0, oy0);
+        __syncthreads();              // the previous tile's outputs are made: the stage is free
+        pyr::fast_stage<TS>(v, sm);
+        __syncthreads();
+        if (t + gridDim.x < ntiles) {   // the next tile's window loads while this one is computed
+            const TS* s2; TS* d2; int x2, y2;
+            where(t + gridDim.x, s2, d2, x2, y2);
+            pyr::fast_fetch<TS>(s2, H, W, 2 * y2 - 2, 2 * x2 - F::VE, v);
+        }
+        pyr::fast_compute<TS>(sm, dst, Ho, Wo, ox0, oy0, O2);
+    }
+}
+
+// Images whose rows are not 16-byte aligned: two scalar 64x16 halves per tile.
+template <typename TS>
+__global__ void __launch_bounds__(pyr::FNT) k_pyramid_down(const TS* __restrict__ in, TS* __restrict__ out, int H,
                                                            int W, int Ho, int Wo) {
     __shared__ float tile[pyr::PIH][pyr::PIW];
     __shared__ float hs[pyr::PIH][pyr::PTX + 1];
+    const int tx = blockIdx.x, ty = blockIdx.y;
     const int img = blockIdx.z / 3, ch = blockIdx.z % 3;
-    pyr::tile_down(in + ((int64_t)img * 3 + ch) * (int64_t)H * W, out + ((int64_t)img * 3 + ch) * (int64_t)Ho * Wo, H,
-                   W, Ho, Wo, blockIdx.x * pyr::PTX, blockIdx.y * pyr::PTY, tile, hs);
+    const TS* src = in + ((int64_t)img * 3 + ch) * (int64_t)H * W;
+    TS* dst = out + ((int64_t)img * 3 + ch) * (int64_t)Ho * Wo;
+    for (int half = 0; half < pyr::FTY / pyr::PTY; ++half) {
+        if (half) __syncthreads();   // the previous half is done with the buffers
+        pyr::tile_down<TS, pyr::FNT>(src, dst, H, W, Ho, Wo, tx * pyr::PTX, ty * pyr::FTY + half * pyr::PTY, tile,
+                                     hs);
+    }
+}
+
+template <typename TS>
+int launch_typed(const TS* in, TS* out, int64_t n, int64_t h, int64_t w, cudaStream_t s) {
+    using F = pyr::Fast<TS>;
+    const int64_t ho = (h + 1) / 2, wo = (w + 1) / 2;
+    const int64_t ntx_all = (wo + pyr::PTX - 1) / pyr::PTX, nty_all = (ho + pyr::FTY - 1) / pyr::FTY;
+    if (nty_all > 65535 || n * 3 > 65535) return fail(MDN_ESHAPE, "pyramid: image too large");
+    if (w % F::VE == 0 && (reinterpret_cast<uintptr_t>(in) & 15) == 0) {
+        auto kern = k_pyramid_fast<TS>;
+        int occ = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, pyr::FNT, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "k_pyramid_fast: occupancy");
+        const int64_t ntiles = ntx_all * nty_all * n * 3;
+        int64_t grid = (int64_t)num_sms() * (occ > 0 ? occ : 1);
+        if (grid > ntiles) grid = ntiles;
+        kern<<<(unsigned)grid, pyr::FNT, 0, s>>>(in, out, (int)h, (int)w, (int)ho, (int)wo, (int)(n * 3),
+                                                 (int)ntx_all, (int)nty_all);
+        return check_launch("k_pyramid_fast");
+    }
+    dim3 grid((unsigned)ntx_all, (unsigned)nty_all, (unsigned)(n * 3));
+    k_pyramid_down<TS><<<grid, pyr::FNT, 0, s>>>(in, out, (int)h, (int)w, (int)ho, (int)wo);
+    return check_launch("k_pyramid_down");
 }
 
 }  // namespace
 
 int launch_pyramid_down(const void* in, void* out, int dtype, int64_t n, int64_t h, int64_t w,
                         cudaStream_t s) {
-    int64_t ho = (h + 1) / 2, wo = (w + 1) / 2;
-    dim3 block(pyr::PNT);
-    dim3 grid((unsigned)((wo + pyr::PTX - 1) / pyr::PTX), (unsigned)((ho + pyr::PTY - 1) / pyr::PTY), (unsigned)(n * 3));
-    if (grid.y > 65535 || grid.z > 65535) return fail(MDN_ESHAPE, "pyramid: image too large");
-    if (dtype == MDN_F32)
-        k_pyramid_down<float><<<grid, block, 0, s>>>((const float*)in, (float*)out, (int)h, (int)w, (int)ho, (int)wo);
-    else
-        k_pyramid_down<__half><<<grid, block, 0, s>>>((const __half*)in, (__half*)out, (int)h, (int)w, (int)ho, (int)wo);
-    return check_launch("k_pyramid_down");
+    if (dtype == MDN_F32) return launch_typed<float>((const float*)in, (float*)out, n, h, w, s);
+    return launch_typed<__half>((const __half*)in, (__half*)out, n, h, w, s);
 }
 
 }  // namespace mdn

@@ -66,7 +66,7 @@ def _close(a, b, dt):
 
 @pytest.mark.parametrize("dt", [torch.float32, torch.float16])
 def test_checked_pyramid_and_selection(mdn, dt):
-    for i, (h, w) in enumerate(ODD + [(300, 200)]):
+    for i, (h, w) in enumerate(ODD + [(300, 200), (260, 640)]):
         x = _img(h, w, 900 + i, dt)
         ref, got = _both(mdn, lambda: mdn.build_pyramid(x, 4))
         assert all(torch.equal(a, b) for a, b in zip(ref, got))

@@ -74,6 +74,25 @@ def test_pyramid_bit_exact(mdn, storage, hw):
         assert max_abs(g, ex) <= (1e-6 if storage == "f32" else 2e-3)
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("hw", [(300, 640), (517, 1024), (301, 644), (96, 528), (1, 8), (5, 16), (3, 1032), (70, 136)])
+def test_pyramid_vector_path_bit_exact(mdn, storage, hw):
+    """Frames whose rows start on 16-byte boundaries (W a multiple of 8, or of
+    4 only: FP16 then takes the scalar path) take the vector-loaded,
+    persistent pyramid kernel, with clamped rows and edge-filled vectors at
+    every border (down to 1 x 8 and 3 x 1032 frames): bit for bit the
+    oracle's FP32-order pyramid."""
+    h, w = hw
+    z, _ = synth.noisy_pair(h, w, 150 + h)
+    zs = O.round_storage(z, storage)
+    ref = O.pyramid(zs, 3, storage, mirror32=True)
+    got = mdn.build_pyramid(_tt(zs, storage)[None].repeat(2, 1, 1, 1).contiguous(), 3)
+    for l in range(1, 3):
+        for i in range(2):
+            g = _np(got[l - 1][i])
+            assert np.array_equal(g, ref[l]), (l, i, np.abs(g - ref[l]).max())
+
+
 # ------------------------------------------------------------ A2/A3
 
 @pytest.mark.parametrize("storage", ["f32", "f16"])
