@@ -31,7 +31,7 @@ METRIC = "Mpix/s 3-level denoise at 12MP"
 # DRAM bytes (read + write) of one level-0 k_level3 launch per 4032x3024 FP16
 # frame, from the ncu capture in profiles/k_level3_12mp_level0_fp16.md; set to
 # None whenever that kernel changes until it is captured again.
-LEVEL0_TRAFFIC_PER_FRAME = (91.644672 + 37.800192) * 1e6
+LEVEL0_TRAFFIC_PER_FRAME = (91.645184 + 38.008576) * 1e6
 
 
 def _gen_frame(seed):

@@ -17,8 +17,9 @@
 // pyramid.cuh), so DRAM latency overlaps the arithmetic.  Other images go to
 // k_pyramid_down, which stages the clamped 131x35 windows of the two 64x16
 // halves with scalar loads.  Both give the same FP32 chains on the same
-// clamped values, so every tile is bit-identical to the oracle's order.  Each input element is read once from DRAM (neighbouring
-// tiles' halos hit L2).
+// clamped values, so every tile follows the fixed FP32 order above bit for
+// bit.  Each input element is read once from DRAM (neighbouring tiles'
+// halos hit L2).
 #include "common.cuh"
 #include "internal.h"
 #include "pyramid.cuh"
