@@ -292,6 +292,46 @@ int mdn_denoise_multiscale_static(const void* noisy, int32_t dtype, int64_t n, i
                                   const mdn_geometry* geom, const mdn_bucket_params* bparams,
                                   void* out, void* const* bucket_maps, void* stream);
 
+/* Tensor-descriptor forms.  The entry points above take plain pointers and
+ * sizes; these take every array as an mdn_tensor and check it against the
+ * shapes the operation implies before calling the pointer form, returning
+ * MDN_ESHAPE (the argument named in mdn_last_error) for a wrong dtype, rank,
+ * extent or stride, MDN_EINVAL for a null tensor or data pointer.  Strides
+ * are in elements and must be the dense row-major ones (extents of 1 may
+ * have any stride): the kernels read dense buffers, so a strided view must
+ * be made contiguous by the caller.  Images are [N][3][H][W] MDN_F32 or
+ * MDN_F16 (all of one call alike); coarse inputs [N][3][(H+1)/2][(W+1)/2];
+ * banks [K][3][D] MDN_F32 / MDN_F16 (D = mdn_regressor_len, K from the
+ * bucket parameters) or, prepared, a 1-D tensor of mdn_bank_rows_bytes
+ * elements of dtype MDN_F16_ROWS / MDN_F32_ROWS; bucket maps [N][H][W]
+ * MDN_U8 (K <= 256) or MDN_U16; the Gram state [K][G][Dp][Dp] MDN_F64 and
+ * counts [K] MDN_I64 (see mdn_gram_state_bytes); bank_out [K][3][D] MDN_F32.
+ * Arrays of tensors (pyramid levels, banks, bucket maps) are HOST arrays;
+ * a bucket-map entry with null data is skipped.  Ownership, streams and
+ * asynchrony as for the pointer forms. */
+#define MDN_U8 8       /* tensor dtypes beyond MDN_F32 / MDN_F16 / the row-slot banks */
+#define MDN_U16 9
+#define MDN_F64 10
+#define MDN_I64 11
+typedef struct {
+    int32_t dtype;
+    int32_t ndim;          /* 1..4 */
+    int64_t shape[4];
+    int64_t strides[4];    /* elements */
+    void* data;            /* device */
+} mdn_tensor;
+int mdn_t_build_pyramid(const mdn_tensor* img, int32_t levels, mdn_tensor* out, void* stream);
+int mdn_t_filter_level(const mdn_tensor* z, const mdn_tensor* coarse, const mdn_tensor* bank,
+                       const mdn_geometry* geom, const mdn_bucket_params* bp, mdn_tensor* out,
+                       mdn_tensor* buckets_out, void* stream);
+int mdn_t_denoise_multiscale(const mdn_tensor* noisy, int32_t levels, const mdn_tensor* banks,
+                             const mdn_geometry* geom, const mdn_bucket_params* bparams, mdn_tensor* out,
+                             mdn_tensor* bucket_maps, void* ws, size_t ws_bytes, void* stream);
+int mdn_t_train_level_filters(const mdn_tensor* noisy_lvl, const mdn_tensor* coarse_out,
+                              const mdn_tensor* clean_lvl, const mdn_geometry* geom, const mdn_bucket_params* bp,
+                              int32_t gram_precision, int32_t accumulate, mdn_tensor* gram, mdn_tensor* counts,
+                              double lambda, mdn_tensor* bank_out, void* ws, size_t ws_bytes, void* stream);
+
 /* ------------------------------------------------------------------ */
 /* Training (Eqs. 5-6: per-bucket least squares; Section 4 cascade)    */
 /* ------------------------------------------------------------------ */

@@ -21,7 +21,8 @@ __all__ = ["build", "lib", "Geometry", "BucketParams", "default_bparams", "MdnEr
            "save_banks", "load_banks", "save_gram_state", "load_gram_state", "paper_grid_bparams",
            "bucket_map_dtype", "MAX_K", "levels_for_sigma", "denoise_multiscale_pipelined", "use_checked_build",
            "PreparedBank", "prepare_bank", "F16_ROWS", "F32_ROWS", "LEVEL_VARIANTS", "autotune_level",
-           "autotune_lookup", "autotune_save", "autotune_load", "autotune_clear",
+           "autotune_lookup", "autotune_save", "autotune_load", "autotune_clear", "Tensor", "as_tensor",
+           "t_build_pyramid", "t_filter_level", "t_denoise_multiscale", "t_train_level_filters",
            "check_status", "pyramid_noise_factor", "set_gram_wait_limit",
            "gram_expire_next_wait"]
 
@@ -110,6 +111,15 @@ def bucket_map_dtype(K: int):
     return torch.uint8 if K <= 256 else torch.int16
 
 
+class Tensor(C.Structure):
+    """mdn_tensor: dtype code, rank, shape, strides (elements), device data."""
+    _fields_ = [("dtype", C.c_int32), ("ndim", C.c_int32), ("shape", C.c_int64 * 4), ("strides", C.c_int64 * 4),
+                ("data", C.c_void_p)]
+
+
+U8, U16, F64, I64 = 8, 9, 10, 11
+
+
 class ServerCfg(C.Structure):
     _fields_ = [("device", C.c_int32), ("hbm_budget_bytes", C.c_size_t), ("max_active", C.c_int32),
                 ("autotune", C.c_int32), ("tile_variant", C.c_int32), ("geom", Geometry)]
@@ -190,6 +200,14 @@ def lib():
             "mdn_autotune_save": (C.c_int, [C.c_char_p]),
             "mdn_autotune_load": (C.c_int, [C.c_char_p]),
             "mdn_autotune_clear": (None, []),
+            "mdn_t_build_pyramid": (C.c_int, [C.POINTER(Tensor), i32, C.POINTER(Tensor), vp]),
+            "mdn_t_filter_level": (C.c_int, [C.POINTER(Tensor), C.POINTER(Tensor), C.POINTER(Tensor), G, B,
+                                             C.POINTER(Tensor), C.POINTER(Tensor), vp]),
+            "mdn_t_denoise_multiscale": (C.c_int, [C.POINTER(Tensor), i32, C.POINTER(Tensor), G, B,
+                                                   C.POINTER(Tensor), C.POINTER(Tensor), vp, sz, vp]),
+            "mdn_t_train_level_filters": (C.c_int, [C.POINTER(Tensor), C.POINTER(Tensor), C.POINTER(Tensor), G, B,
+                                                    i32, i32, C.POINTER(Tensor), C.POINTER(Tensor), C.c_double,
+                                                    C.POINTER(Tensor), vp, sz, vp]),
             "mdn_prepare_bank_rows": (C.c_int, [vp, i32, G, i32, vp, sz, vp]),
             "mdn_train_workspace_bytes": (sz, [i64, i64, i64, G, i32, i32]),
             "mdn_train_level_filters": (C.c_int, [vp, vp, vp, i32, i64, i64, i64, G, B, i32, i32, vp, vp,
@@ -281,6 +299,85 @@ def _check_banks(banks, geom: Geometry, bparams):
         if isinstance(b, PreparedBank) and (b.geom != g or b.K != bp.K):
             raise ValueError(f"prepared bank is for geometry {b.geom} with K={b.K}, "
                              f"call has {g} with K={bp.K}")
+
+
+def as_tensor(t):
+    """An mdn_tensor describing a CUDA torch tensor (its own shape and strides;
+    the library checks them), or a PreparedBank (1-D row-slot bytes)."""
+    torch = _torch()
+    if t is None:
+        return None
+    if isinstance(t, PreparedBank):
+        d = Tensor(t.code, 1)
+        d.shape[0], d.strides[0], d.data = t.rows.numel(), 1, t.rows.data_ptr()
+        return d
+    codes = {torch.float32: F32, torch.float16: F16, torch.uint8: U8, torch.int16: U16, torch.float64: F64,
+             torch.int64: I64}
+    if t.dtype not in codes:
+        raise ValueError(f"no mdn_tensor dtype for {t.dtype}")
+    if t.dim() > 4:
+        raise ValueError("mdn_tensor has at most 4 dimensions")
+    d = Tensor(codes[t.dtype], t.dim())
+    for i in range(t.dim()):
+        d.shape[i], d.strides[i] = t.shape[i], t.stride(i)
+    d.data = t.data_ptr()
+    return d
+
+
+def _tarr(ts):
+    arr = (Tensor * max(len(ts), 1))()
+    for i, t in enumerate(ts):
+        if t is not None:
+            arr[i] = as_tensor(t)
+    return arr
+
+
+def t_build_pyramid(img, levels: int, outs, stream=None):
+    """mdn_t_build_pyramid: img [N][3][H][W], outs the levels-1 output tensors."""
+    _check(lib().mdn_t_build_pyramid(C.byref(as_tensor(img)), levels, _tarr(outs), _stream(stream)))
+
+
+def t_filter_level(z, coarse, bank, geom: Geometry, bp: BucketParams, out, buckets_out=None, stream=None):
+    """mdn_t_filter_level with tensor descriptors (shapes and strides checked by the library)."""
+    c = as_tensor(coarse)
+    m = as_tensor(buckets_out)
+    _check(lib().mdn_t_filter_level(C.byref(as_tensor(z)), C.byref(c) if c is not None else None,
+                                    C.byref(as_tensor(bank)), C.byref(geom), C.byref(bp), C.byref(as_tensor(out)),
+                                    C.byref(m) if m is not None else None, _stream(stream)))
+
+
+def t_denoise_multiscale(noisy, banks, geom: Geometry, bparams, out, bucket_maps=None, ws=None, stream=None):
+    """mdn_t_denoise_multiscale with tensor descriptors; ws a CUDA uint8 tensor
+    of at least denoise_workspace_bytes (allocated here when None)."""
+    torch = _torch()
+    n, _, h, w = noisy.shape
+    levels = 1 if geom.r_coarse < 0 else len(banks) + 1
+    need = denoise_workspace_bytes(n, h, w, levels, _dtype_code(noisy))
+    if ws is None:
+        ws = torch.empty(max(need, 1), dtype=torch.uint8, device=noisy.device)
+    parr = (BucketParams * len(bparams))(*bparams)
+    _check(lib().mdn_t_denoise_multiscale(C.byref(as_tensor(noisy)), levels, _tarr(banks), C.byref(geom), parr,
+                                          C.byref(as_tensor(out)), _tarr(bucket_maps) if bucket_maps else None,
+                                          C.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+    return out
+
+
+def t_train_level_filters(noisy, coarse, clean, geom: Geometry, bp: BucketParams, gram_precision: int, gram, counts,
+                          lam: float = 1e-3, bank_out=None, accumulate: bool = False, ws=None, stream=None):
+    """mdn_t_train_level_filters with tensor descriptors; gram [K][G][Dp][Dp]
+    float64, counts [K] int64, bank_out [K][3][D] float32 or None."""
+    torch = _torch()
+    n, _, h, w = noisy.shape
+    need = lib().mdn_train_workspace_bytes(n, h, w, C.byref(geom), bp.K, gram_precision)
+    if ws is None:
+        ws = torch.empty(max(need, 1), dtype=torch.uint8, device=noisy.device)
+    c = as_tensor(coarse)
+    b = as_tensor(bank_out)
+    _check(lib().mdn_t_train_level_filters(C.byref(as_tensor(noisy)), C.byref(c) if c is not None else None,
+                                           C.byref(as_tensor(clean)), C.byref(geom), C.byref(bp), gram_precision,
+                                           int(accumulate), C.byref(as_tensor(gram)), C.byref(as_tensor(counts)),
+                                           lam, C.byref(b) if b is not None else None, C.c_void_p(ws.data_ptr()),
+                                           ws.numel(), _stream(stream)))
 
 
 LEVEL_VARIANTS = ("fused_smem", "fused_l2", "strip", "tile_smem", "tile_l2")

@@ -335,3 +335,65 @@ def test_autotune_table_host(L, tmp_path):
                  None) == 2
     finally:
         L.mdn_autotune_clear()
+
+
+def _desc(dtype, shape, strides=None, data=256):
+    t = mdn.Tensor(dtype, len(shape))
+    dense = []
+    acc = 1
+    for e in reversed(shape):
+        dense.append(acc)
+        acc *= e
+    dense = list(reversed(dense))
+    for i, e in enumerate(shape):
+        t.shape[i] = e
+        t.strides[i] = (strides or dense)[i]
+    t.data = data
+    return t
+
+
+def test_tensor_descriptors_are_checked_without_device(L):
+    """The mdn_t_* forms refuse a wrong dtype, rank, extent or stride with
+    MDN_ESHAPE and name the argument, and a null tensor with MDN_EINVAL,
+    before any device work."""
+    def err():
+        return L.mdn_last_error().decode()
+    img = _desc(mdn.F16, [2, 3, 64, 48])
+    lv = (mdn.Tensor * 2)(_desc(mdn.F16, [2, 3, 32, 24]), _desc(mdn.F16, [2, 3, 16, 12]))
+    f = L.mdn_t_build_pyramid
+    for bad, word in [(_desc(mdn.U8, [2, 3, 64, 48]), "dtype"), (_desc(mdn.F16, [2, 3, 64]), "rank"),
+                      (_desc(mdn.F16, [2, 4, 64, 48]), "extent"),
+                      (_desc(mdn.F16, [2, 3, 64, 48], [9216, 3072, 48, 2]), "stride")]:
+        assert f(C.byref(bad), 3, lv, None) == 2 and "img" in err() and word in err(), err()
+    bad_lv = (mdn.Tensor * 2)(_desc(mdn.F16, [2, 3, 32, 24]), _desc(mdn.F16, [2, 3, 16, 13]))
+    assert f(C.byref(img), 3, bad_lv, None) == 2 and "out[1]" in err()
+    assert f(C.byref(_desc(mdn.F16, [2, 3, 64, 48], data=None)), 3, lv, None) == 1
+    assert f(None, 3, lv, None) == 1
+    # a dimension of extent 1 may carry any stride
+    one = _desc(mdn.F16, [1, 3, 64, 48], [12345, 3072, 48, 1])
+    lv1 = (mdn.Tensor * 1)(_desc(mdn.F32, [1, 3, 32, 24]))
+    assert f(C.byref(one), 2, lv1, None) == 2 and "out[0]" in err() and "dtype" in err()
+
+    g, bp = mdn.Geometry(3, 3), mdn.default_bparams(0)
+    z, c, out = _desc(mdn.F32, [1, 3, 33, 17]), _desc(mdn.F32, [1, 3, 17, 9]), _desc(mdn.F32, [1, 3, 33, 17])
+    t = L.mdn_t_filter_level
+    assert t(C.byref(z), C.byref(c), C.byref(_desc(mdn.F16, [216, 3, 74])), C.byref(g), C.byref(bp), C.byref(out),
+             None, None) == 2 and "bank" in err()
+    assert t(C.byref(z), C.byref(_desc(mdn.F32, [1, 3, 16, 9])), C.byref(_desc(mdn.F16, [216, 3, 98])), C.byref(g),
+             C.byref(bp), C.byref(out), None, None) == 2 and "coarse" in err()
+    assert t(C.byref(z), C.byref(c), C.byref(_desc(mdn.F16, [216, 3, 98])), C.byref(g), C.byref(bp), C.byref(out),
+             C.byref(_desc(mdn.U16, [1, 33, 17])), None) == 2 and "buckets_out" in err()
+    rows = L.mdn_bank_rows_bytes(C.byref(g), 216, mdn.F16)
+    assert t(C.byref(z), C.byref(c), C.byref(_desc(mdn.F16_ROWS, [rows - 16])), C.byref(g), C.byref(bp),
+             C.byref(out), None, None) == 2 and "bank" in err()
+
+    gx = mdn.Geometry(3, -1, 1)   # cross-channel: gram [K][1][D+3][D+3]
+    n, cl = _desc(mdn.F32, [1, 3, 33, 17]), _desc(mdn.F32, [1, 3, 33, 17])
+    tr = L.mdn_t_train_level_filters
+    good_g, good_c = _desc(mdn.F64, [216, 1, 150, 150]), _desc(mdn.I64, [216])
+    assert tr(C.byref(n), None, C.byref(cl), C.byref(gx), C.byref(bp), 1, 0, C.byref(_desc(mdn.F64, [216, 3, 150, 150])),
+              C.byref(good_c), 1e-3, None, None, 0, None) == 2 and "gram" in err()
+    assert tr(C.byref(n), None, C.byref(cl), C.byref(gx), C.byref(bp), 1, 0, C.byref(good_g),
+              C.byref(_desc(mdn.F64, [216])), 1e-3, None, None, 0, None) == 2 and "counts" in err()
+    assert tr(C.byref(n), None, C.byref(_desc(mdn.F16, [1, 3, 33, 17])), C.byref(gx), C.byref(bp), 1, 0,
+              C.byref(good_g), C.byref(good_c), 1e-3, None, None, 0, None) == 2 and "clean_lvl" in err()
