@@ -10,11 +10,11 @@
 // Tiling: 64x32 output tiles of one channel.  Images whose rows start on
 // 16-byte boundaries (W a multiple of 8 for FP16, 4 for FP32, aligned base)
 // go to the persistent kernel k_pyramid_fast: each CTA walks its tiles with
-// the next tile's window already loading into registers (16-byte vectors,
-// rows clamped, vectors outside a row replaced by its edge element) while
-// the current one is computed from shared memory (even / odd column rows,
-// per-thread output columns with the vertical window in registers; see
-// pyramid.cuh), so DRAM latency overlaps the arithmetic.  Other images go to
+// the next tile's window copying (cp.async, 16-byte vectors, rows clamped,
+// vectors outside a row filled with its edge element) into one of two
+// shared-memory stages while the current one is computed from the other
+// (per-thread output columns reading element pairs, the vertical window in
+// registers; see pyramid.cuh), so DRAM latency overlaps the arithmetic.  Other images go to
 // k_pyramid_down, which stages the clamped 131x35 windows of the two 64x16
 // halves with scalar loads.  Both give the same FP32 chains on the same
 // clamped values, so every tile follows the fixed FP32 order above bit for
@@ -27,14 +27,15 @@
 namespace mdn {
 namespace {
 
-// Every tile of every plane (ntx x nty per plane), persistent CTAs, one
-// tile's window prefetched into registers.
+// Every tile of every plane (ntx x nty per plane), persistent CTAs, the
+// next tile's window copying into the other shared-memory stage while the
+// current one is computed.
 template <typename TS>
-__global__ void __launch_bounds__(pyr::FNT, sizeof(TS) == 2 ? 4 : 3)
-    k_pyramid_fast(const TS* __restrict__ in, TS* __restrict__ out, int H, int W, int Ho, int Wo, int nplanes,
-                   int ntx, int nty) {
+__global__ void __launch_bounds__(pyr::FNT) k_pyramid_fast(const TS* __restrict__ in, TS* __restrict__ out, int H,
+                                                           int W, int Ho, int Wo, int nplanes, int ntx, int nty) {
     using F = pyr::Fast<TS>;
-    __shared__ __align__(16) float sm[F::SMEM_FLOATS];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto stage = [&](int k) { return reinterpret_cast<TS*>(smem_raw + (k & 1) * F::STAGE_BYTES); };
     const int64_t per_plane = (int64_t)ntx * nty, ntiles = per_plane * nplanes;
     // ix0 = 128 tx - 2 and xa = floor(ix0 / VE) VE = 128 tx - VE, so (ix0 - xa) / 2 is the same for all tiles
     constexpr int O2 = (F::VE - 2) / 2;
@@ -46,25 +47,26 @@ __global__ void __launch_bounds__(pyr::FNT, sizeof(TS) == 2 ? 4 : 3)
         ox0 = tx * pyr::PTX;
         oy0 = ty * pyr::FTY;
     };
-    uint4 v[F::NLD];
     int64_t t = blockIdx.x;
     if (t < ntiles) {
         const TS* src; TS* dst; int ox0, oy0;
         where(t, src, dst, ox0, oy0);
-        pyr::fast_fetch<TS>(src, H, W, 2 * oy0 - 2, 2 * ox0 - F::VE, v);
+        pyr::raw_issue<TS>(src, H, W, 2 * oy0 - 2, 2 * ox0 - F::VE, stage(0));
     }
-    for (; t < ntiles; t += gridDim.x) {
+    for (int i = 0; t < ntiles; t += gridDim.x, ++i) {
         const TS* src; TS* dst; int ox0, oy0;
         where(t, src, dst, ox0, oy0);
-        __syncthreads();              // the previous tile's outputs are made: the stage is free
-        pyr::fast_stage<TS>(v, sm);
-        __syncthreads();
-        if (t + gridDim.x < ntiles) {   // the next tile's window loads while this one is computed
+        if (t + gridDim.x < ntiles) {   // the next tile into the other stage (read two iterations ago)
             const TS* s2; TS* d2; int x2, y2;
             where(t + gridDim.x, s2, d2, x2, y2);
-            pyr::fast_fetch<TS>(s2, H, W, 2 * y2 - 2, 2 * x2 - F::VE, v);
+            pyr::raw_issue<TS>(s2, H, W, 2 * y2 - 2, 2 * x2 - F::VE, stage(i + 1));
+            asm volatile("cp.async.wait_group 1;" ::: "memory");   // this tile's copies landed
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
-        pyr::fast_compute<TS>(sm, dst, Ho, Wo, ox0, oy0, O2);
+        __syncthreads();   // every thread's copies and edge stores of this tile are visible
+        pyr::raw_compute<TS>(stage(i), dst, Ho, Wo, ox0, oy0, O2);
+        __syncthreads();   // the stage is read before it is refilled
     }
 }
 
@@ -93,13 +95,16 @@ int launch_typed(const TS* in, TS* out, int64_t n, int64_t h, int64_t w, cudaStr
     if (nty_all > 65535 || n * 3 > 65535) return fail(MDN_ESHAPE, "pyramid: image too large");
     if (w % F::VE == 0 && (reinterpret_cast<uintptr_t>(in) & 15) == 0) {
         auto kern = k_pyramid_fast<TS>;
+        const int bytes = (int)F::SMEM_BYTES;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "k_pyramid_fast: smem attribute");
         int occ = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, pyr::FNT, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, pyr::FNT, bytes);
         if (e != cudaSuccess) return cuda_fail(e, "k_pyramid_fast: occupancy");
         const int64_t ntiles = ntx_all * nty_all * n * 3;
         int64_t grid = (int64_t)num_sms() * (occ > 0 ? occ : 1);
         if (grid > ntiles) grid = ntiles;
-        kern<<<(unsigned)grid, pyr::FNT, 0, s>>>(in, out, (int)h, (int)w, (int)ho, (int)wo, (int)(n * 3),
+        kern<<<(unsigned)grid, pyr::FNT, bytes, s>>>(in, out, (int)h, (int)w, (int)ho, (int)wo, (int)(n * 3),
                                                  (int)ntx_all, (int)nty_all);
         return check_launch("k_pyramid_fast");
     }

@@ -68,113 +68,87 @@ __device__ __forceinline__ void tile_down(const TS* __restrict__ src, TS* __rest
 }
 
 // Per-image fast path (k_pyramid_fast): 64 x 32 output tiles of images whose
-// rows start on 16-byte boundaries, 256 threads.  The 131 x 67 input
-// window is loaded as an aligned superset of whole 16-byte vectors (VE
-// elements each, columns xa .. xa + NV*VE - 1 with xa = ix0 rounded down to
-// VE) and staged with its even and odd columns in separate rows E and O, so
-// that output column c's horizontal taps E[o2+c], O[o2+c], E[o2+c+1],
-// O[o2+c+1], E[o2+c+2] are consecutive across the lanes (no bank
-// conflicts).  Thread (c, seg) then makes output column c of the FRY = 8
-// rows FRY seg .. FRY seg + FRY - 1: the 2 FRY + 3 horizontal sums of its
-// input rows in turn, with the vertical 5-tap window held in registers.  The values and the two
-// FP32 chains are those of tile_down, so the outputs are bit-identical.
+// rows start on 16-byte boundaries, 256 threads.  The 131 x 67 input window
+// of a tile is copied raw (storage type) into one of two shared-memory
+// stages as an aligned superset of whole 16-byte vectors (VE elements each:
+// columns xa .. xa + NV*VE - 1 with xa = ix0 rounded down to VE), by
+// cp.async so that the next tile's copies are in flight while the current
+// tile is computed; rows are clamped to the image, and with W and xa
+// multiples of VE a vector lies wholly inside its row or wholly outside it,
+// one outside being filled with the row's edge element (the clamped columns
+// of tile_down).  Output column c's horizontal taps p[2c .. 2c + 4] are the
+// staged elements off + 2c .. off + 2c + 4 (off = ix0 - xa is even), i.e.
+// three consecutive element pairs starting at pair o2 + c (o2 = off / 2):
+// one 32-bit word of two FP16 values or one 8-byte pair of FP32 values each,
+// consecutive across the lanes.  Thread (c, seg) makes output column c of
+// the FRY = 8 rows FRY seg .. FRY seg + FRY - 1: the 2 FRY + 3 horizontal
+// sums of its input rows in turn, with the vertical 5-tap window in
+// registers.  The values and the two FP32 chains are those of tile_down, so
+// the outputs are bit-identical.
 constexpr int FTY = 32, FNT = 256, FSEG = FNT / PTX, FRY = FTY / FSEG;   // FRY output rows per thread
 constexpr int FIH = 2 * FTY + 3;                                   // staged input rows
 template <typename TS> struct Fast {
     static constexpr int VE = 16 / (int)sizeof(TS);              // elements per 16-byte vector
     static constexpr int NV = (PIW + VE - 1 + VE - 1) / VE;       // vectors per window row (any ix0 - xa < VE)
-    static constexpr int PITCH = NV * VE;                          // staged columns per row
-    static constexpr int HP = PITCH / 2;                           // floats per E or O row
-    static constexpr int NLD = (FIH * NV + FNT - 1) / FNT;        // vector loads per thread
-    static constexpr int SMEM_FLOATS = 2 * FIH * HP;
+    static constexpr int PITCH = NV * VE;                          // staged elements per row
+    static constexpr size_t STAGE_BYTES = (size_t)FIH * PITCH * sizeof(TS);
+    static constexpr size_t SMEM_BYTES = 2 * STAGE_BYTES;
 };
 
-// Staged window of one tile: FIH input rows of NV 16-byte vectors from
-// (iy0, xa), rows clamped to the image.  With W a multiple of VE and xa a
-// multiple of VE, a vector lies wholly inside its row or wholly outside it;
-// one outside holds the row's edge element VE times (the clamped columns of
-// tile_down).  Thread tid's share is vectors tid, tid + FNT, ...
+// Starts the copies of one tile's window into `stage` (cp.async, then one
+// commit group per call); vectors outside a row are stored directly.
 template <typename TS>
-__device__ __forceinline__ void fast_fetch(const TS* __restrict__ src, int H, int W, int iy0, int xa,
-                                           uint4 (&v)[Fast<TS>::NLD]) {
+__device__ __forceinline__ void raw_issue(const TS* __restrict__ src, int H, int W, int iy0, int xa,
+                                          TS* __restrict__ stage) {
     using F = Fast<TS>;
-#pragma unroll
-    for (int j = 0; j < F::NLD; ++j) {
-        const int i = threadIdx.x + j * FNT;
-        if (i < FIH * F::NV) {
-            const int r = i / F::NV, q = i - r * F::NV;
-            const int gy = clampi(iy0 + r, 0, H - 1), x = xa + q * F::VE;
-            if (x >= 0 && x + F::VE <= W) {
-                const int64_t o = (int64_t)gy * W + x;
-                v[j] = mdn_in(o + F::VE - 1, (int64_t)H * W, 304) ? __ldg(reinterpret_cast<const uint4*>(src + o))
-                                                                  : make_uint4(0, 0, 0, 0);
-            } else {
-                const int64_t o = (int64_t)gy * W + (x < 0 ? 0 : W - 1);
-                const TS e = src[mdn_in(o, (int64_t)H * W, 306) ? o : 0];
-                uint32_t b;
-                if constexpr (sizeof(TS) == 2) {
-                    const uint32_t h = __half_as_ushort(e);
-                    b = h | (h << 16);
-                } else {
-                    b = __float_as_uint(e);
-                }
-                v[j] = make_uint4(b, b, b, b);
-            }
-        }
-    }
-}
-
-// The fetched vectors into the E (even staged columns) and O (odd) rows.
-template <typename TS>
-__device__ __forceinline__ void fast_stage(const uint4 (&v)[Fast<TS>::NLD], float* __restrict__ sm) {
-    using F = Fast<TS>;
-    float* E = sm;
-    float* O = sm + FIH * F::HP;
-#pragma unroll
-    for (int j = 0; j < F::NLD; ++j) {
-        const int i = threadIdx.x + j * FNT;
-        if (i < FIH * F::NV) {
-            const int r = i / F::NV, q = i - r * F::NV;
+    for (int i = threadIdx.x; i < FIH * F::NV; i += FNT) {
+        const int r = i / F::NV, q = i - r * F::NV;
+        const int gy = clampi(iy0 + r, 0, H - 1), x = xa + q * F::VE;
+        TS* dst = stage + r * F::PITCH + q * F::VE;
+        if (x >= 0 && x + F::VE <= W) {
+            const int64_t o = (int64_t)gy * W + x;
+            const TS* g = src + (mdn_in(o + F::VE - 1, (int64_t)H * W, 304) ? o : 0);
+            const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(g) : "memory");
+        } else {
+            const int64_t o = (int64_t)gy * W + (x < 0 ? 0 : W - 1);
+            const TS e = src[mdn_in(o, (int64_t)H * W, 306) ? o : 0];
+            uint32_t b;
             if constexpr (sizeof(TS) == 2) {
-                const uint32_t w4[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
-                float f[8];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const float2 p2 = __half22float2(*reinterpret_cast<const __half2*>(&w4[k]));
-                    f[2 * k] = p2.x;
-                    f[2 * k + 1] = p2.y;
-                }
-                *reinterpret_cast<float4*>(E + r * F::HP + 4 * q) = make_float4(f[0], f[2], f[4], f[6]);
-                *reinterpret_cast<float4*>(O + r * F::HP + 4 * q) = make_float4(f[1], f[3], f[5], f[7]);
+                const uint32_t h = __half_as_ushort(e);
+                b = h | (h << 16);
             } else {
-                *reinterpret_cast<float2*>(E + r * F::HP + 2 * q) =
-                    make_float2(__uint_as_float(v[j].x), __uint_as_float(v[j].z));
-                *reinterpret_cast<float2*>(O + r * F::HP + 2 * q) =
-                    make_float2(__uint_as_float(v[j].y), __uint_as_float(v[j].w));
+                b = __float_as_uint(e);
             }
+            *reinterpret_cast<uint4*>(dst) = make_uint4(b, b, b, b);
         }
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-// Outputs of one staged interior tile: thread (c, seg) makes column c of
-// rows FRY seg .. FRY seg + FRY - 1; o2 = (ix0 - xa) / 2.
+// element pair k of a staged row as two floats
+template <typename TS> __device__ __forceinline__ float2 pair_at(const TS* row, int k) {
+    if constexpr (sizeof(TS) == 2) return __half22float2(reinterpret_cast<const __half2*>(row)[k]);
+    else return reinterpret_cast<const float2*>(row)[k];
+}
+
+// Outputs of one staged tile: thread (c, seg) makes column c of rows
+// FRY seg .. FRY seg + FRY - 1; o2 = (ix0 - xa) / 2.
 template <typename TS>
-__device__ __forceinline__ void fast_compute(const float* __restrict__ sm, TS* __restrict__ dst, int Ho, int Wo,
-                                             int ox0, int oy0, int o2) {
+__device__ __forceinline__ void raw_compute(const TS* __restrict__ stage, TS* __restrict__ dst, int Ho, int Wo,
+                                            int ox0, int oy0, int o2) {
     using F = Fast<TS>;
     const float b0 = 0.0625f, b1 = 0.25f, b2 = 0.375f;
-    const float* E = sm;
-    const float* O = sm + FIH * F::HP;
     const int c = threadIdx.x % PTX, seg = threadIdx.x / PTX;
-    const int k0 = mdn_in(o2 + c + 2, F::HP, 305) ? o2 + c : 0;
+    const int k0 = mdn_in(2 * (o2 + c + 2) + 1, F::PITCH, 305) ? o2 + c : 0;
     auto hrow = [&](int r) {   // horizontal sum of staged input row r at output column c
-        const float* e = E + r * F::HP + k0;
-        const float* od = O + r * F::HP + k0;
-        float acc = __fmul_rn(b0, e[0]);
-        acc = __fmaf_rn(b1, od[0], acc);
-        acc = __fmaf_rn(b2, e[1], acc);
-        acc = __fmaf_rn(b1, od[1], acc);
-        acc = __fmaf_rn(b0, e[2], acc);
+        const TS* row = stage + r * F::PITCH;
+        const float2 p0 = pair_at<TS>(row, k0), p1 = pair_at<TS>(row, k0 + 1), p2 = pair_at<TS>(row, k0 + 2);
+        float acc = __fmul_rn(b0, p0.x);
+        acc = __fmaf_rn(b1, p0.y, acc);
+        acc = __fmaf_rn(b2, p1.x, acc);
+        acc = __fmaf_rn(b1, p1.y, acc);
+        acc = __fmaf_rn(b0, p2.x, acc);
         return acc;
     };
     const int r0 = 2 * FRY * seg;   // first staged row of this segment's window
