@@ -71,6 +71,8 @@ constexpr bool CROSS = false;
 constexpr int NVAR = 4;             // level-kernel variants: 0-2 tile kernels, 3 the fused kernel
 constexpr int COPY_SMS = 8;         // SMs the level and pyramid kernels leave to the host copies
 constexpr int COPY_NT = 256, COPY_BLOCKS = 4 * COPY_SMS;
+// SMs the server's compute kernels are sized for (all but COPY_SMS, at least one)
+inline int compute_sms() { return num_sms() > COPY_SMS ? num_sms() - COPY_SMS : 1; }
 
 struct PyrItem {
     const __half* in;
@@ -217,7 +219,7 @@ template <class SH> int launch_level(const WorkList* wl, const Tables* tb, int K
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, SH::NT, bytes);
     if (e != cudaSuccess || occ < 1) return fail(MDN_ESHAPE, "server: level kernel does not fit");
-    kern<<<(num_sms() - COPY_SMS) * occ, SH::NT, bytes, s>>>(wl, tb, stage);
+    kern<<<compute_sms() * occ, SH::NT, bytes, s>>>(wl, tb, stage);
     return check_launch("k_serve_level");
 }
 
@@ -272,7 +274,7 @@ int launch_fused(const WorkList* wl, const Tables* tb, int stage, cudaStream_t s
     SRC src{wl, tb, stage};
     float w[5];
     gauss5_weights(w);
-    kern<<<(num_sms() - COPY_SMS) * occ, lvl::v3::NT, bytes, s>>>(src, nullptr, w[0], w[1], w[2], 1);
+    kern<<<compute_sms() * occ, lvl::v3::NT, bytes, s>>>(src, nullptr, w[0], w[1], w[2], 1);
     return check_launch("k_level3 (server)");
 }
 
@@ -743,7 +745,7 @@ static int capture_graph(mdn_server* s, TickCtx& c) {
     cudaError_t e = cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "server: begin capture");
     int rc = MDN_OK;
-    for (int l = 1; l < s->max_levels; ++l) k_serve_pyr<<<(num_sms() - COPY_SMS) * 4, pyr::PNT, 0, c.stream>>>(c.d_wl, l);
+    for (int l = 1; l < s->max_levels; ++l) k_serve_pyr<<<compute_sms() * 4, pyr::PNT, 0, c.stream>>>(c.d_wl, l);
     for (int l = s->max_levels - 2; l >= 0 && rc == MDN_OK; --l)
         rc = launch_variant(s->variant, s->geom, c.d_wl, s->d_tb, s->Kmax, l, c.stream);
     cudaGraph_t g = nullptr;
