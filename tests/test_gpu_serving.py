@@ -260,3 +260,35 @@ def test_host_buffer_kinds(mdn, copy_engines, monkeypatch):
             assert torch.equal(y, ref), (tuple(x.shape), x.is_pinned(), x.data_ptr() % 16, y.data_ptr() % 16)
     finally:
         srv.close()
+
+
+def test_per_tick_trace(mdn, tmp_path, monkeypatch):
+    """MDN_SERVER_TRACE at create: at destroy the server writes one CSV line
+    per tick (requests, pixels, host launch / retire times, device phase
+    times, request ids) covering every completed request exactly once."""
+    path = tmp_path / "trace.csv"
+    monkeypatch.setenv("MDN_SERVER_TRACE", str(path))
+    sets = [_bank_set(mdn, 3, 17)]
+    srv = mdn.Server(sets, budget_bytes=256 << 20, max_active=8, autotune=False)
+    monkeypatch.delenv("MDN_SERVER_TRACE")
+    try:
+        frames = [_frame(h, w, 67000 + i) for i, (h, w) in enumerate([(64, 80), (131, 97), (240, 320), (33, 17)])]
+        outs = [torch.empty_like(f).pin_memory() for f in frames]
+        ids = [srv.submit(f, o, 0) for f, o in zip(frames, outs)]
+        _drain(srv, len(ids))
+    finally:
+        srv.close()
+    lines = path.read_text().strip().splitlines()
+    head = lines[0].split(",")
+    assert head[:3] == ["tick", "requests", "pixels"] and head[-1] == "ids"
+    seen, pix = [], 0
+    for ln in lines[1:]:
+        f = ln.split(",")
+        got = [int(x) for x in f[-1].split(";")]
+        assert int(f[1]) == len(got)
+        seen += got
+        pix += int(f[2])
+        launch, retire = float(f[3]), float(f[4])
+        assert retire >= launch and all(float(x) >= 0 for x in f[5:10])
+    assert sorted(seen) == sorted(ids)
+    assert pix == sum(f.shape[1] * f.shape[2] for f in frames)
