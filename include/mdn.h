@@ -205,7 +205,8 @@ int mdn_prepare_bank_rows(const void* bank, int32_t bank_dtype, const mdn_geomet
 #define MDN_LV_STRIP 2          /* strip kernel, bank in shared memory */
 #define MDN_LV_TILE_SMEM 3      /* one pixel per thread, bank in shared memory */
 #define MDN_LV_TILE_L2 4        /* one pixel per thread, taps read through L2 */
-#define MDN_LEVEL_VARIANTS 5
+#define MDN_LV_FUSED_CLUSTER 5  /* fused kernel on clusters of two CTAs, FP32 bank split between them */
+#define MDN_LEVEL_VARIANTS 6
 int mdn_autotune_level(const mdn_geometry* geom, const mdn_bucket_params* bp, int32_t dtype, int32_t bank_dtype,
                        int64_t n, int64_t h, int64_t w, int32_t reps, int32_t* best, float* ms, void* stream);
 int mdn_autotune_lookup(const mdn_geometry* geom, int32_t K, int32_t dtype, int32_t bank_dtype, int64_t n,

@@ -380,7 +380,7 @@ def t_train_level_filters(noisy, coarse, clean, geom: Geometry, bp: BucketParams
                                            ws.numel(), _stream(stream)))
 
 
-LEVEL_VARIANTS = ("fused_smem", "fused_l2", "strip", "tile_smem", "tile_l2")
+LEVEL_VARIANTS = ("fused_smem", "fused_l2", "strip", "tile_smem", "tile_l2", "fused_cluster")
 
 
 def autotune_level(geom: Geometry, bp: BucketParams, dtype: int, bank_dtype: int, n: int, h: int, w: int,

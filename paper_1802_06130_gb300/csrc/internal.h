@@ -72,7 +72,8 @@ enum LevelVariant {
     LV_STRIP = 2,        // strip kernel, bank in shared memory (K <= 256, if it fits)
     LV_TILE_SMEM = 3,    // one pixel per thread, bank in shared memory (if it fits)
     LV_TILE_L2 = 4,      // one pixel per thread, taps read through L2
-    LV_COUNT = 5
+    LV_FUSED_CLUSTER = 5,   // fused kernel on CTA pairs, FP32 bank split between their shared memories
+    LV_COUNT = 6
 };
 // Autotune table (tune.cu): the variant recorded for this call's geometry,
 // storage / bank types, K and image-size class, or -1.  Thread-safe.

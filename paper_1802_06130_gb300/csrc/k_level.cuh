@@ -560,11 +560,11 @@ __device__ __forceinline__ void build_bucket_placement(const SelParams& sp, int 
 
 }  // namespace v2
 namespace v3 {
-template <int RF, int RC, bool CROSS, typename TB, bool GLOBAL = false>
+template <int RF, int RC, bool CROSS, typename TB, bool GLOBAL = false, bool CL = false>
 __device__ __forceinline__ void filter_group(const float* __restrict__ zb, int zpl, int zst,
                                              const float* __restrict__ ub, int upl, int ust,
                                              const unsigned char* __restrict__ bank_s, const int (&kb)[8], int j,
-                                             float o[3]);
+                                             float o[3], uint32_t cb0 = 0, uint32_t cb1 = 0, int ckh = 0);
 }  // namespace v3
 namespace v2 {
 
@@ -952,18 +952,38 @@ template <typename TB, bool GLOBAL> __device__ __forceinline__ void group_slot(c
     }
 }
 
-template <int RF, int RC, bool CROSS, typename TB, bool GLOBAL>
+// An FP32 slot (8 floats, 32 bytes) of a bank held in the shared memory of
+// a CTA of this cluster, by its shared::cluster address.
+__device__ __forceinline__ void cluster_slot(uint32_t a, float h[8]) {
+    uint32_t v[8];
+    asm("ld.shared::cluster.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]) : "r"(a));
+    asm("ld.shared::cluster.v4.u32 {%0, %1, %2, %3}, [%4];"
+        : "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+        : "r"(a + 16));
+#pragma unroll
+    for (int e = 0; e < 8; ++e) h[e] = __uint_as_float(v[e]);
+}
+
+// CL: the bank is split over the two CTAs of a cluster by bucket (buckets
+// below ckh in CTA 0, the rest in CTA 1, each at the start of its bank
+// area), cb0 / cb1 the shared::cluster addresses of the two areas.
+template <int RF, int RC, bool CROSS, typename TB, bool GLOBAL, bool CL>
 __device__ __forceinline__ void filter_group(const float* __restrict__ zb, int zpl, int zst,
                                              const float* __restrict__ ub, int upl, int ust,
                                              const unsigned char* __restrict__ bank_s, const int (&kb)[8], int j,
-                                             float o[3]) {
+                                             float o[3], uint32_t cb0, uint32_t cb1, int ckh) {
     using SL = RowSlots<RF, RC, CROSS>;
     constexpr int SB = v2::SlotBytes<TB>::B;
     constexpr int BSTRIDE = bucket_bytes_rows<RF, RC, CROSS, TB>();
+    static_assert(!CL || (sizeof(TB) == 4 && !GLOBAL), "cluster banks: FP32 slots in shared memory");
     const unsigned FULL = 0xffffffffu;
     const unsigned char* hb[PX];
+    uint32_t hc[PX];
 #pragma unroll
-    for (int p = 0; p < PX; ++p) hb[p] = bank_s + (size_t)kb[p] * BSTRIDE;
+    for (int p = 0; p < PX; ++p) {
+        if constexpr (CL) hc[p] = kb[p] < ckh ? cb0 + kb[p] * BSTRIDE : cb1 + (kb[p] - ckh) * BSTRIDE;
+        else hb[p] = bank_s + (size_t)kb[p] * BSTRIDE;
+    }
     float acc[3][PX];
 #pragma unroll
     for (int oc = 0; oc < 3; ++oc)
@@ -986,7 +1006,8 @@ __device__ __forceinline__ void filter_group(const float* __restrict__ zb, int z
 #pragma unroll
                     for (int p = 0; p < PX; ++p) {
                         float h[8];
-                        group_slot<TB, GLOBAL>(hb[p] + (slot + j) * SB, h);
+                        if constexpr (CL) cluster_slot(hc[p] + (slot + j) * SB, h);
+                        else group_slot<TB, GLOBAL>(hb[p] + (slot + j) * SB, h);
 #pragma unroll
                         for (int d = 0; d < SL::NCR; ++d) acc[oc][p] = fmaf(h[d], col[p / 2 + d], acc[oc][p]);
                     }
@@ -1006,7 +1027,8 @@ __device__ __forceinline__ void filter_group(const float* __restrict__ zb, int z
 #pragma unroll
                 for (int p = 0; p < PX; ++p) {
                     float h[8];
-                    group_slot<TB, GLOBAL>(hb[p] + (slot + j) * SB, h);
+                    if constexpr (CL) cluster_slot(hc[p] + (slot + j) * SB, h);
+                    else group_slot<TB, GLOBAL>(hb[p] + (slot + j) * SB, h);
 #pragma unroll
                     for (int d = 0; d < SL::NFR; ++d) acc[oc][p] = fmaf(h[d], col[p + d], acc[oc][p]);
                 }
@@ -1101,7 +1123,15 @@ template <typename TS, typename BT> struct BatchTiles {
     __device__ __forceinline__ const SelParams& sel(int) const { return sp; }
 };
 
-template <int RF, int RC, bool CROSS, typename TS, typename TB, bool GB, typename BT, class SRC>
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// CL: launched in clusters of two CTAs, the (FP32) bank split between them
+// by bucket; each CTA loads its half, and the consumers read every slot by
+// its shared::cluster address.  Every CTA passes the same two cluster
+// barriers (after the load, before exit), whatever its tile count.
+template <int RF, int RC, bool CROSS, typename TS, typename TB, bool GB, typename BT, class SRC, bool CL = false>
 __global__ void __launch_bounds__(NT, 1) k_level3(const __grid_constant__ SRC src, const TB* __restrict__ bank,
                                                   float w0, float w1, float w2, int rows_in) {
     using SL = RowSlots<RF, RC, CROSS>;
@@ -1116,15 +1146,34 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const __grid_constant__ SRC sr
     const int tid = threadIdx.x;
 
     if constexpr (!GB) {
-        const int K = src.K;   // shared-memory banks: batch sources only
+        int K = src.K;   // shared-memory banks: batch sources only
+        const TB* b = bank;
+        int skip = 0;    // buckets before this CTA's part (CL: the other CTA's half)
+        if constexpr (CL) {
+            uint32_t rank;
+            asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+            const int kh = (K + 1) / 2;
+            skip = rank ? kh : 0;
+            K = rank ? K - kh : kh;
+            b = bank + (size_t)skip * 3 * Geo<RF, RC, CROSS>::D;
+        }
         if (rows_in) {   // prepared row slots: a straight 16-byte copy
-            for (int i = tid; i < K * BSTRIDE / 16; i += NT)
-                reinterpret_cast<uint4*>(bank_sm)[i] = __ldg(reinterpret_cast<const uint4*>(bank) + i);
+            const uint4* r = reinterpret_cast<const uint4*>(bank) + (size_t)skip * BSTRIDE / 16;
+            for (int i = tid; i < K * BSTRIDE / 16; i += NT) reinterpret_cast<uint4*>(bank_sm)[i] = __ldg(r + i);
         } else {
-            load_bank_rows<RF, RC, CROSS, TB>(bank, K, bank_sm, tid, NT);
+            load_bank_rows<RF, RC, CROSS, TB>(b, K, bank_sm, tid, NT);
         }
     }   // once per persistent CTA
     __syncthreads();
+    uint32_t cb0 = 0, cb1 = 0;
+    int ckh = 0;
+    if constexpr (CL) {
+        cluster_sync_all();   // both halves are loaded before any CTA reads the other's
+        const uint32_t local = (uint32_t)__cvta_generic_to_shared(bank_sm);
+        asm volatile("mapa.shared::cluster.u32 %0, %1, 0;" : "=r"(cb0) : "r"(local));
+        asm volatile("mapa.shared::cluster.u32 %0, %1, 1;" : "=r"(cb1) : "r"(local));
+        ckh = (src.K + 1) / 2;
+    }
 
     const int64_t ntiles = src.count();
     const int64_t T = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
@@ -1413,8 +1462,9 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const __grid_constant__ SRC sr
                 const int rr_ = r, cc_ = c0;
 #endif
                 float o[3];
-                filter_group<RF, RC, CROSS, TB, GB>(zs + (rr_ + HZ - RF) * ZW + cc_ + HZ - RF, ZH * ZW, ZW,
-                                                 us + (rr_ / 2) * UW + cc_ / 2, UH * UW, UW, bank_s, kb, j, o);
+                filter_group<RF, RC, CROSS, TB, GB, CL>(zs + (rr_ + HZ - RF) * ZW + cc_ + HZ - RF, ZH * ZW, ZW,
+                                                     us + (rr_ / 2) * UW + cc_ / 2, UH * UW, UW, bank_s, kb, j, o,
+                                                     cb0, cb1, ckh);
                 if (pass == TH / 8 - 1 && i + 2 < T) bar_arrive(BAR_EMPTY0 + s, NT);   // stage s no longer read
                 const int gy = y0 + r, gx = x0 + c0 + j;
                 if (gy < H && gx < W && mdn_in((int64_t)gy * W + gx, (int64_t)H * W, 126)) {
@@ -1428,6 +1478,7 @@ __global__ void __launch_bounds__(NT, 1) k_level3(const __grid_constant__ SRC sr
             }
         }
     }
+    if constexpr (CL) cluster_sync_all();   // no CTA leaves while its partner may still read its half
 }
 
 template <int RF, int RC, bool CROSS, typename TS, typename TB, bool GB = false, typename BT = uint8_t>
@@ -1461,6 +1512,57 @@ int run3(const LevelArgs& a, cudaStream_t s) {
     return check_launch("k_level3");
 }
 
+// Shared memory of the cluster form: the stages plus half the FP32 bank (rounded up).
+template <int RF, int RC, bool CROSS> size_t smem_need_cluster(int K) {
+    return front_bytes<RC, 1>() + (size_t)((K + 1) / 2) * bucket_bytes_rows<RF, RC, CROSS, float>();
+}
+
+// The fused kernel in clusters of two CTAs with an FP32 bank split between them.
+template <int RF, int RC, bool CROSS, typename TS>
+int run3_cluster(const LevelArgs& a, cudaStream_t s) {
+    using SRC = BatchTiles<TS, uint8_t>;
+    auto kern = k_level3<RF, RC, CROSS, TS, float, false, uint8_t, SRC, true>;
+    const size_t bytes = smem_need_cluster<RF, RC, CROSS>(a.K);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "k_level3 (cluster): set smem attribute");
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = bytes;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(2 * (unsigned)num_sms());
+    int nclusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
+    if (e != cudaSuccess) return cuda_fail(e, "k_level3 (cluster): occupancy");
+    if (nclusters < 1) return fail(MDN_ESHAPE, "k_level3 (cluster): no cluster of two fits");
+    const int64_t tiles = ((a.w + TW - 1) / TW) * ((a.h + TH - 1) / TH) * a.n;
+    int64_t grid = 2 * (int64_t)nclusters;
+    if (grid > tiles + (tiles & 1)) grid = tiles + (tiles & 1);   // whole clusters; a CTA may get no tile
+    cfg.gridDim = dim3((unsigned)grid);
+    float w[5];
+    gauss5_weights(w);
+    SRC src;
+    src.z = (const TS*)a.z;
+    src.coarse = (const TS*)a.coarse;
+    src.out = (TS*)a.out;
+    src.bmap = (uint8_t*)a.buckets;
+    src.bank = (const unsigned char*)a.bank;
+    src.H = (int)a.h; src.W = (int)a.w; src.Hc = (int)a.hc; src.Wc = (int)a.wc;
+    src.nimg = (int)a.n; src.K = a.K; src.color = a.geom.color;
+    src.tiles_x = (int)((a.w + TW - 1) / TW);
+    src.tiles_y = (int)((a.h + TH - 1) / TH);
+    src.sp = a.sel;
+    e = cudaLaunchKernelEx(&cfg, kern, src, (const float*)a.bank, w[0], w[1], w[2], a.bank_rows ? 1 : 0);
+    if (e != cudaSuccess) return cuda_fail(e, "k_level3 (cluster): launch");
+    return check_launch("k_level3 (cluster)");
+}
+
 }  // namespace v3
 
 
@@ -1477,6 +1579,8 @@ template <int RF, int RC, bool CROSS, typename TB> bool variant_ok(const LevelAr
         case LV_STRIP: return !a.bank_rows && small && v2::smem_need<RF, RC, CROSS, TB>(a.K) <= SMEM_LIMIT;
         case LV_TILE_SMEM: return !a.bank_rows && smem_need<RF, RC, CROSS, TB>(a.K) <= SMEM_LIMIT;
         case LV_TILE_L2: return !a.bank_rows;
+        case LV_FUSED_CLUSTER:
+            return sizeof(TB) == 4 && a.K >= 2 && small && v3::smem_need_cluster<RF, RC, CROSS>(a.K) <= SMEM_LIMIT;
         default: return false;
     }
 }
@@ -1490,6 +1594,9 @@ int run_variant(const LevelArgs& a, int v, cudaStream_t s) {
                               : v3::run3<RF, RC, CROSS, TS, TB, true, uint16_t>(a, s);
         case LV_STRIP: return v2::run2<RF, RC, CROSS, TS, TB>(a, s);
         case LV_TILE_SMEM: return run<RF, RC, CROSS, TS, TB, true, true>(a, s);
+        case LV_FUSED_CLUSTER:
+            if constexpr (sizeof(TB) == 4) return v3::run3_cluster<RF, RC, CROSS, TS>(a, s);
+            return fail(MDN_ESHAPE, "filter_level: cluster banks are FP32");
         default: return run<RF, RC, CROSS, TS, TB, false, true>(a, s);
     }
 }
@@ -1499,7 +1606,8 @@ int run_variant(const LevelArgs& a, int v, cudaStream_t s) {
 // kernel with the bank in shared memory when it fits, else the strip or tile
 // kernels.  Prepared banks (row slots, mdn_prepare_bank_rows): the fused
 // kernel, with the bank copied to shared memory when it fits and read
-// through L2 otherwise.
+// through L2 otherwise.  The cluster form (an FP32 bank split over two CTAs)
+// runs only when forced or chosen by the autotuner.
 template <int RF, int RC, bool CROSS, typename TS, typename TB>
 int dispatch_geo(const LevelArgs& a, cudaStream_t s) {
     if (a.variant >= 0) {
@@ -1509,6 +1617,8 @@ int dispatch_geo(const LevelArgs& a, cudaStream_t s) {
     }
     const int t = tune_lookup(a);
     if (t >= 0 && variant_ok<RF, RC, CROSS, TB>(a, t)) return run_variant<RF, RC, CROSS, TS, TB>(a, t, s);
+    // (the cluster form of FP32 banks is the tuner's to choose: reading every
+    // slot across the pair, it measured 4x slower than the L2 form)
     if (a.bank_rows)
         return run_variant<RF, RC, CROSS, TS, TB>(
             a, variant_ok<RF, RC, CROSS, TB>(a, LV_FUSED_SMEM) ? LV_FUSED_SMEM : LV_FUSED_L2, s);

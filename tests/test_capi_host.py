@@ -323,7 +323,7 @@ def test_autotune_table_host(L, tmp_path):
         assert L.mdn_autotune_load(str(bad).encode()) == 1
         assert L.mdn_autotune_load(str(tmp_path / "missing.txt").encode()) == 1
         best = C.c_int32()
-        ms = (C.c_float * 5)()
+        ms = (C.c_float * 6)()
         bp = mdn.default_bparams(0)
         t = L.mdn_autotune_level
         assert t(None, C.byref(bp), mdn.F16, mdn.F16, 1, 64, 64, 3, C.byref(best), ms, None) == 1

@@ -115,3 +115,39 @@ def test_server_stores_and_reads_its_entry(mdn, tmp_path):
         assert torch.equal(y, ref)
     finally:
         srv.close()
+
+
+@pytest.mark.parametrize("geom_args", [(3, 3), (3, 2)], ids=["7x7+7x7", "7x7+5x5"])
+def test_cluster_bank_equals_l2_bank(mdn, geom_args, tmp_path):
+    """An FP32 bank too large for one CTA's shared memory: split over a
+    cluster of two CTAs (variant 5) it gives, bit for bit, the results of
+    the same prepared bank read through L2 (variant 1), and meets the FP32
+    parity bar of the oracle."""
+    geom_o = O.Geometry(*geom_args)
+    geom = mdn.Geometry(*geom_args)
+    h, w = 197, 131
+    sc = int(np.floor(np.log2(h * w)))
+    rng = np.random.default_rng(95)
+    D = geom_o.D()
+    bank = rng.standard_normal((216, 3, D)) * 0.05
+    bank += (1.0 - bank.sum(axis=2, keepdims=True)) / D
+    bank = bank.astype(np.float32).astype(np.float64)
+    zs = O.round_storage(synth.noisy_pair(h, w, 9400)[0], "f32")
+    uc = O.round_storage(synth.clean_image((h + 1) // 2, (w + 1) // 2, 9401), "f32")
+    bpo = O.default_bparams(0)
+    prepared = mdn.prepare_bank(_tt(bank, "f32"), geom)
+    outs = {}
+    for v in (1, 5):
+        p = tmp_path / f"t{v}.txt"
+        p.write_text(f"level {geom_args[0]} {geom_args[1]} 0 {mdn.F32} {mdn.F32} 1 216 {sc} {v} 0.1\n")
+        mdn.autotune_clear()
+        mdn.autotune_load(p)
+        m = torch.empty((1, h, w), dtype=torch.uint8, device="cuda")
+        outs[v] = (mdn.filter_level(_tt(zs, "f32")[None], _tt(uc, "f32")[None], prepared, geom, _gbp(mdn, bpo),
+                                    buckets_out=m), m)
+    assert torch.equal(outs[1][0], outs[5][0]) and torch.equal(outs[1][1], outs[5][1])
+    ref_b, band, _ = O.select(zs, bpo, mirror32=True)
+    ref = O.filter_level(zs, uc, ref_b, bank, geom_o)
+    mism = outs[5][1][0].cpu().numpy() != ref_b
+    assert not (mism & ~band).any()
+    assert max_abs(outs[5][0][0].cpu().numpy().astype(np.float64), ref, ~mism) <= TOL["f32"]
