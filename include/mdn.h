@@ -151,9 +151,13 @@ int mdn_select_buckets(const void* z, int32_t dtype, int64_t n, int64_t h, int64
  * z, out: [n][3][h][w]; coarse: [n][3][ceil(h/2)][ceil(w/2)] or NULL when
  * geom->r_coarse < 0; bank: [K][3][D] of bank_dtype, K = bucket count of bp;
  * buckets_out: optional [n][h][w] copy of s(i) (u8 or u16 by K).  out must
- * not alias z or coarse.  Banks of up to ~220 KB (e.g. 216 buckets of 7x7 +
- * 7x7 taps in FP16) are held in shared memory; larger ones (the paper's
- * 4096-bucket grid) are read through L2 by a slower kernel. */
+ * not alias z or coarse.  Banks of up to ~145 KB in row-slot form (e.g. 216
+ * buckets of 7x7 + 7x7 taps in FP16) are held in shared memory by the fused
+ * kernel; larger plain banks (the paper's 4096-bucket grid, FP32 banks of
+ * 7x7 + 7x7 taps) run a slower kernel that reads taps through L2, and larger
+ * prepared banks (mdn_prepare_bank_rows) run the fused kernel reading row
+ * slots through L2.  The kernel used can be tuned per configuration
+ * (mdn_autotune_level). */
 int mdn_filter_level(const void* z, const void* coarse, int32_t dtype, int64_t n, int64_t h,
                      int64_t w, const void* bank, int32_t bank_dtype, const mdn_geometry* geom,
                      const mdn_bucket_params* bp, void* out, void* buckets_out, void* stream);
