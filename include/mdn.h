@@ -173,8 +173,8 @@ int mdn_filter_level(const void* z, const void* coarse, int32_t dtype, int64_t n
  * there whole; a larger one (the paper's 4096-bucket grid, FP32 banks of 216
  * buckets of 7x7 + 7x7 taps) is read from this layout through L2 with 16-byte
  * loads instead of tap by tap.  Results equal those of the plain bank where
- * both run the same kernel; geometries: 5x5, 7x7 + 7x7, 7x7 + 5x5 per
- * channel and 7x7x3 cross-channel.  mdn_bank_rows_bytes returns 0 for
+ * both run the same kernel; geometries: 5x5, 7x7 + 7x7, 7x7 + 5x5, 5x5 + 3x3
+ * per channel and 7x7x3 cross-channel.  mdn_bank_rows_bytes returns 0 for
  * another geometry or bad arguments.  The layout carries no header: a
  * prepared bank must be passed with the geometry and bucket count it was
  * prepared for (the caller's contract, like the size of any buffer; the

@@ -35,6 +35,7 @@ int bucket_row_bytes(const mdn_geometry& g, int elem_dtype) {
     MDN_GEO(3, 3, false)
     MDN_GEO(3, 2, false)
     MDN_GEO(3, -1, true)
+    MDN_GEO(2, 1, false)
 #undef MDN_GEO
     return 0;
 }
@@ -70,6 +71,7 @@ extern "C" int mdn_prepare_bank_rows(const void* bank, int32_t bank_dtype, const
     MDN_GEO(3, 3, false)
     MDN_GEO(3, 2, false)
     MDN_GEO(3, -1, true)
+    MDN_GEO(2, 1, false)
 #undef MDN_GEO
     return fail(MDN_ESHAPE, "prepare_bank_rows: geometry not compiled");
 }

@@ -1638,9 +1638,10 @@ template <typename TS, typename TB> int dispatch(const LevelArgs& a, cudaStream_
     MDN_GEO(3, 3, false)
     MDN_GEO(3, 2, false)
     MDN_GEO(3, -1, true)
+    MDN_GEO(2, 1, false)
 #undef MDN_GEO
     return fail(MDN_ESHAPE, "filter_level: geometry not compiled (supported: r_fine/r_coarse/cross = "
-                            "2/-1/0, 3/3/0, 3/2/0, 3/-1/1)");
+                            "2/-1/0, 3/3/0, 3/2/0, 3/-1/1, 2/1/0)");
 }
 
 }  // namespace lvl

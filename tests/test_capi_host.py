@@ -38,6 +38,7 @@ def test_regressor_lengths(L):
     assert mdn.regressor_len(mdn.Geometry(3, 3)) == 98
     assert mdn.regressor_len(mdn.Geometry(3, 2)) == 74
     assert mdn.regressor_len(mdn.Geometry(3, -1, 1)) == 147
+    assert mdn.regressor_len(mdn.Geometry(2, 1)) == 34   # the paper's low-noise 5x5 + 3x3
     assert L.mdn_regressor_len(None) == -1
 
 
@@ -267,7 +268,8 @@ def test_prepared_bank_layout_sizes_and_checks(L):
     bucket, output channel, tap block and filter row (2r+1 rows per block; a
     7x7x3 cross-channel filter has three fine blocks per output channel);
     mdn_prepare_bank_rows rejects bad arguments before any device work."""
-    cases = [((2, -1), 3 * 5), ((3, 3), 3 * (7 + 7)), ((3, 2), 3 * (7 + 5)), ((3, -1, 1), 3 * 3 * 7)]
+    cases = [((2, -1), 3 * 5), ((3, 3), 3 * (7 + 7)), ((3, 2), 3 * (7 + 5)), ((3, -1, 1), 3 * 3 * 7),
+             ((2, 1), 3 * (3 + 5))]
     for args, slots in cases:
         g = C.byref(mdn.Geometry(*args))
         assert L.mdn_bank_rows_bytes(g, 216, mdn.F16) == 216 * slots * 16

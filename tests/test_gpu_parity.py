@@ -128,7 +128,7 @@ def test_constant_image_bucket(mdn):
 # ------------------------------------------------------------ A4
 
 GEOMS = [O.Geometry(2, -1), O.Geometry(3, 3), O.Geometry(3, 2), O.Geometry(3, -1, cross=1),
-         O.Geometry(3, 3, color=1)]
+         O.Geometry(3, 3, color=1), O.Geometry(2, 1)]   # the last: the paper's low-noise 5x5 + 3x3
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16"])
@@ -168,7 +168,8 @@ def _trained_banks(geom, levels, n=2, size=96, seed=1000):
 @pytest.mark.parametrize("case", [("cfg1", O.Geometry(2, -1), 1, (256, 256)),
                                   ("cfg2", O.Geometry(3, 3), 3, (135, 240)),
                                   ("paper", O.Geometry(3, 2), 3, (101, 77)),
-                                  ("cfg4", O.Geometry(3, 3), 4, (189, 252))], ids=lambda c: c[0])
+                                  ("cfg4", O.Geometry(3, 3), 4, (189, 252)),
+                                  ("lownoise", O.Geometry(2, 1), 3, (120, 161))], ids=lambda c: c[0])
 def test_denoise_multiscale(mdn, storage, case):
     _, geom, levels, (h, w) = case
     banks = _trained_banks(geom, levels)
@@ -276,6 +277,7 @@ def _train_case(name):
     if name not in _TRAIN_CACHE:
         geom, n, (h, w) = {"cfg1": (O.Geometry(2, -1), 2, (128, 128)),
                            "cfg2": (O.Geometry(3, 3), 2, (96, 80)),
+                           "lownoise": (O.Geometry(2, 1), 2, (96, 80)),
                            "cfg3": (O.Geometry(3, -1, cross=1), 2, (96, 96)),
                            "cfg3_256x4": (O.Geometry(3, -1, cross=1), 4, (256, 256)),
                            # two 1 MP pairs: more than one pixel group of the tensor-core Gram
@@ -285,7 +287,7 @@ def _train_case(name):
 
 
 @pytest.mark.parametrize("prec", [0, 1, 2, 3], ids=lambda p: PREC_IDS[p])
-@pytest.mark.parametrize("case", ["cfg1", "cfg2", "cfg3", "cfg3_256x4", "cfg3_1024x2"])
+@pytest.mark.parametrize("case", ["cfg1", "cfg2", "lownoise", "cfg3", "cfg3_256x4", "cfg3_1024x2"])
 def test_train_level_gram_and_bank(mdn, case, prec):
     """Counts exact; Gram sums and the solved bank vs the FP64 oracle.  The
     bank bar (1e-3 relative Frobenius, BF16 1e-2) applies to the whole bank
